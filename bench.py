@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: the 2D leapfrog wave stencil, FP32, 8192 x 8192,
+200 steps, split into 4 row chunks with a radius-1 neighbourhood halo, every
+chunk launch timed by its own event pair (and energy-attributed).
+
+One bench "step" = one whole simulation: the Taylor start plus 200 leapfrog
+steps over the 4 chunks (804 kernel launches), from the initial field already
+resident in HBM.  Units: grid-point updates (200 * 8192^2 per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sy|reference]
+
+Prints ONE JSON line (rank 0).  With N > 1 (torchrun), every rank runs an
+independent replica on its own GPU (the single-GPU chunk split keeps the
+paper's semantics; the cross-GPU halo exchange is not exercised here), and
+`value` is the updates of all ranks / the slowest rank's time ("weak" scaling).
+
+`--impl reference` times the CPU oracle (the FP32 precision mirror, the same
+arithmetic as the GPU path) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NY = NX = 8192
+STEPS = 200
+CHUNKS = 4
+RADIUS = 1
+HALO = 1
+C2 = 0.25
+SIGMA = 64.0
+BYTES_PER_UPDATE = 12  # read u^n and u^{n-1}, write u^{n+1} (FP32)
+METRIC = "stencil GB/s & updates/s (fraction of HBM peak), J/update; learned/batched vs plain"
+WORKLOAD = ("wave2d leapfrog 5-point FP32, 8192x8192, c*dt/dx=0.5, 200 steps, Dirichlet-zero, "
+            "Gaussian sigma=64 at centre, 4 row chunks, halo radius 1")
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_median": statistics.median(power)}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("wave_kernel.cuh", "wave.cu", "wave_f32.cu"):
+        with open(os.path.join(ROOT, "paper_2505_06022_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic() -> float | None:
+    """Per-launch DRAM bytes of the wave kernel from the committed ncu summary, if
+    it was captured from the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "wave_f32_8192_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_sha") == kernel_source_sha():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(seconds: float = 10.0) -> dict:
+    """FP32 mirror of the oracle on full-width row bands of the same field, steps
+    repeated until about `seconds` of CPU work; returns updates/s."""
+    import numpy as np
+
+    import oracle
+    from paper_2505_06022_gb300 import inputs
+
+    rows = 512
+    u = inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA)[NY // 2 - rows // 2: NY // 2 + rows // 2], "f32")
+    prev = oracle.wave_start_mirror(oracle.F32, u, RADIUS, C2)
+    cur = u
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        nxt = oracle.wave_step_mirror(oracle.F32, prev, cur, RADIUS, C2)
+        prev, cur = cur, nxt
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    upd = steps * rows * NX
+    return {"value": upd / el, "unit": "updates/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"FP32 mirror oracle, {rows}x{NX} rows of the 8192^2 Gaussian field, {steps} steps "
+                      f"({upd:.3g} updates, {el:.1f} s)", "seconds": el, "updates": upd}
+
+
+def run_reference(args) -> None:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    per = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(per / 4)
+    vals = [oracle_sample(per) for _ in range(args.steps)]
+    tot_upd = sum(v["updates"] for v in vals)
+    tot_s = sum(v["seconds"] for v in vals)
+    value = tot_upd / tot_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": vals[0]["sample"]},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"each step: {vals[0]['sample']}"},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def run_gpu(args) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    stream = torch.cuda.current_stream()
+    q = sy.Queue(local, stream)
+    p = sy.stencil_params(NY, NX, RADIUS, C2, "f32")
+    chunks = sy.sy_split_rows(NY, CHUNKS)
+
+    u0_host = inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), "f32")
+    u0 = torch.from_numpy(u0_host).cuda()  # resident initial field (never overwritten)
+    A = torch.empty_like(u0)
+    B = torch.empty_like(u0)
+    events: list[int] = []
+
+    def simulate(u_init, collect: bool):
+        """Start + STEPS leapfrog steps from u_init (read only); returns (prev, cur)."""
+        evs = sy.sy_stencil_start(q.handle, p, u_init, A, chunks, HALO, want_events=collect)
+        # step 1: u^1 into A (u_prev = A = u^{-1}, in place)
+        e = sy.sy_stencil_step(q.handle, p, A, u_init, A, chunks, HALO, want_events=collect)
+        if collect:
+            events.extend(e)
+        # step 2: u^2 into B (out of place, keeps u_init pristine)
+        e = sy.sy_stencil_step(q.handle, p, u_init, A, B, chunks, HALO, want_events=collect)
+        if collect:
+            events.extend(e)
+        prev, cur = A, B
+        for _ in range(STEPS - 2):
+            e = sy.sy_stencil_step(q.handle, p, prev, cur, prev, chunks, HALO, want_events=collect)
+            if collect:
+                events.extend(e)
+            prev, cur = cur, prev
+        return prev, cur
+
+    for _ in range(args.warmup):
+        simulate(u0, False)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K whole simulations, device-timed on the launching stream ----
+    launches0 = q.launches
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    have_energy = True
+    try:
+        sy.sy_meter_begin(q.handle)
+    except sy.SyError:
+        have_energy = False
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        simulate(u0, True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    joules = seconds = None
+    if have_energy:
+        try:
+            joules, seconds = sy.sy_meter_end(q.handle)
+        except sy.SyError:
+            have_energy = False
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    launches = q.launches - launches0
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+
+    updates_per_step = STEPS * NY * NX
+    value = world * args.steps * updates_per_step / (ms_total * 1e-3)
+
+    # roofline of the dominant kernel: every leapfrog chunk launch, event-timed
+    durs = [sy.sy_event_elapsed(q.handle, e) for e in events]
+    avg_ms = statistics.mean(durs)
+    rows_per_chunk = NY // CHUNKS
+    alg_bytes = BYTES_PER_UPDATE * rows_per_chunk * NX
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    peaks = measured_peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(),
+                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
+                else "fallback 6.8 TB/s",
+                "kernel": "wave_vec_kernel<float,1,RY,false> (one chunk of 2048x8192)",
+                "avg_launch_ms": avg_ms, "launches_timed": len(durs),
+                "frac_of_nominal_8000": achieved / 8000.0}
+    energy = None
+    if have_energy and joules is not None and joules > 0:
+        kern_j = [sy.sy_kernel_energy(q.handle, e) for e in events[: 4 * CHUNKS]]
+        energy = {"joules": joules, "window_s": seconds, "j_per_update": joules / (args.steps * updates_per_step),
+                  "avg_power_w": joules / seconds, "chunk_kernel_j": statistics.mean(kern_j)}
+
+    # ---- e2e: host (pinned) initial field in, final field out, through the same API ----
+    e2e = None
+    if True:
+        h_in = torch.from_numpy(u0_host).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        d_in = torch.empty_like(u0)
+        for _ in range(1):
+            d_in.copy_(h_in, non_blocking=True)
+            _, cur = simulate(d_in, False)
+            h_out.copy_(cur, non_blocking=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k_e2e = max(1, min(args.steps, 5))
+        for _ in range(k_e2e):
+            d_in.copy_(h_in, non_blocking=True)
+            _, cur = simulate(d_in, False)
+            h_out.copy_(cur, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1)
+        e2e = {"value": world * k_e2e * updates_per_step / (ms_e2e * 1e-3), "unit": "updates/s",
+               "h2d_bytes_per_step": h_in.numel() * 4, "d2h_bytes_per_step": h_out.numel() * 4,
+               "ms_per_step": ms_e2e / k_e2e}
+        # the result must be the physics, not garbage: energy of the final state is finite
+        E = sy.sy_wave_energy(q.handle, p, cur, A if cur is B else B)[0]
+        assert np.isfinite(E) and E > 0
+
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        cpu = oracle_sample(args.cpu_seconds) if (world == 1 and args.cpu_seconds > 0) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "updates_per_step": updates_per_step,
+                       "launches_per_step": launches // max(1, args.steps),
+                       "l2": "inputs larger than L2 (three 256 MiB fields per step, 161 GB moved per step)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "gb_per_s": value * BYTES_PER_UPDATE / 1e9,
+            "frac_hbm_measured": value * BYTES_PER_UPDATE / 1e9 / peaks["hbm_gbs"],
+            "roofline": roofline,
+            "energy": energy,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
+                                                                          "sample")},
+        }
+        print(json.dumps(line), flush=True)
+    q.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sy", choices=["sy", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "sy":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

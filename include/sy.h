@@ -1,0 +1,244 @@
+/*
+ * sy.h -- C ABI of libsy: range-mapped data-parallel kernels for one GB300
+ * (sm_103a) GPU, with per-kernel timing and energy metering.
+ *
+ * The programming model follows the paper's SYCL extensions:
+ *   - a queue stands for one device and one in-order stream (paper §2, Listing 1:
+ *     kernels are submitted to a queue bound to a device);
+ *   - a submission is a parallel_for over an index range whose accessors state
+ *     which buffers it reads and writes (paper §2, Listing 1);
+ *   - a range mapper ties a chunk of the execution range to the data the chunk
+ *     touches, and the runtime splits a kernel into chunks (paper §3, Listing 2);
+ *   - each submission yields an event whose kernel energy can be queried, and the
+ *     device energy can be queried as a whole (paper §4, Listing 3).
+ *
+ * General rules (every entry point):
+ *   - Every call returns sy_status; SY_OK is 0.  No C++ exception crosses the ABI.
+ *     On failure, sy_last_error() returns a thread-local message.
+ *   - "device pointer" arguments are CUDA global-memory addresses on the queue's
+ *     device, owned by the caller; the library never frees them.  "host pointer"
+ *     arguments are ordinary host memory.
+ *   - Launches are asynchronous on the queue's stream unless a call says it
+ *     synchronises.  Inputs must stay valid until the work has completed.
+ *   - Argument checks (null pointers, sizes, aliasing, chunk lists) happen on the
+ *     host before anything is launched; a rejected call launches nothing.
+ *   - All kernels are hand-written CUDA for sm_103a; there is no CPU fallback.
+ *     SY_ERR_CUDA reports a CUDA runtime error (message in sy_last_error()).
+ */
+#ifndef SY_H
+#define SY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+#define SY_ABI_VERSION 1
+
+typedef enum sy_status {
+    SY_OK = 0,
+    SY_ERR_INVALID_ARGUMENT = 1, /* a size, radius, dtype or option is out of range */
+    SY_ERR_NULL_POINTER = 2,     /* a required pointer is NULL */
+    SY_ERR_ALIAS = 3,            /* buffers overlap in a way the call forbids */
+    SY_ERR_BAD_CHUNKS = 4,       /* chunk list does not tile the range in order */
+    SY_ERR_HALO_TOO_SMALL = 5,   /* declared halo radius < stencil radius */
+    SY_ERR_UNSUPPORTED = 6,      /* feature unavailable on this device / system */
+    SY_ERR_CUDA = 7,             /* CUDA runtime error */
+    SY_ERR_NVML_UNAVAILABLE = 8, /* NVML missing or energy counter unsupported */
+    SY_ERR_TIMEOUT = 9,          /* a bounded device-side wait gave up */
+    SY_ERR_OUT_OF_MEMORY = 10,   /* library-internal allocation failed */
+    SY_ERR_NOT_READY = 11,       /* queried work has not completed */
+    SY_ERR_IO = 12               /* file read/write failed */
+} sy_status;
+
+/* Storage type of a field.  Arithmetic is always FP32 (energy: FP64). */
+typedef enum sy_dtype { SY_F32 = 0, SY_BF16 = 1, SY_F16 = 2 } sy_dtype;
+
+typedef struct sy_queue_s* sy_queue_t;
+
+/* Event id of one submitted kernel (0 = none).  Valid for the queue that issued
+ * it until 65536 newer events have been issued on that queue. */
+typedef uint64_t sy_event;
+
+/* A half-open sub-range [begin, end) of an execution range (rows for 2D). */
+typedef struct sy_chunk {
+    int64_t begin;
+    int64_t end;
+} sy_chunk;
+
+/* ------------------------------------------------------------------------- */
+/* Status and errors                                                          */
+/* ------------------------------------------------------------------------- */
+
+const char* sy_status_string(sy_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char* sy_last_error(void);
+int sy_abi_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Queue (paper §2, Listing 1: `queue q(gpu_selector)`)                       */
+/* ------------------------------------------------------------------------- */
+
+/* Create a queue on CUDA device `device`.  `cuda_stream` is a cudaStream_t to
+ * borrow (never destroyed by the library), or NULL to create an owned
+ * non-blocking stream.  The queue remembers the device energy counter at
+ * creation (for sy_device_energy) when NVML is available. */
+sy_status sy_queue_create(int device, void* cuda_stream, sy_queue_t* out);
+sy_status sy_queue_destroy(sy_queue_t q);
+/* Block until all work submitted to the queue has completed. */
+sy_status sy_queue_sync(sy_queue_t q);
+/* The cudaStream_t the queue submits to. */
+sy_status sy_queue_stream(sy_queue_t q, void** cuda_stream);
+/* Number of kernel launches this queue has issued so far. */
+sy_status sy_queue_launch_count(sy_queue_t q, uint64_t* launches);
+
+/* ------------------------------------------------------------------------- */
+/* Events: per-kernel time and energy (paper §4, Listing 3)                   */
+/* ------------------------------------------------------------------------- */
+
+/* Device time of an event's kernel in milliseconds (CUDA events around the
+ * launch).  Returns SY_ERR_NOT_READY if the kernel has not completed. */
+sy_status sy_event_elapsed(sy_queue_t q, sy_event ev, double* ms);
+
+/* Raw NVML total-energy counter of the queue's device, in millijoules
+ * (nvmlDeviceGetTotalEnergyConsumption).  SY_ERR_NVML_UNAVAILABLE if NVML cannot
+ * be loaded or the counter is unsupported. */
+sy_status sy_energy_read(sy_queue_t q, uint64_t* millijoules);
+
+/* Device energy in joules since the queue was created (paper §4, Listing 3:
+ * `q.device_energy_consumption()`).  Includes every process's work on the GPU. */
+sy_status sy_device_energy(sy_queue_t q, double* joules);
+
+/* Metering window.  sy_meter_begin synchronises the queue and samples the energy
+ * counter and the host clock; sy_meter_end synchronises again and samples them
+ * again, returning the energy (J) and wall time (s) of the window.  Kernels
+ * issued inside a closed window get an energy attribution (below).  The counter
+ * updates at a coarse period, so windows should last well beyond it (about
+ * 100 ms or more on current drivers). */
+sy_status sy_meter_begin(sy_queue_t q);
+sy_status sy_meter_end(sy_queue_t q, double* joules, double* seconds);
+
+/* Energy of one kernel (paper §4, Listing 3: `q.kernel_energy_consumption(e)`):
+ * the average device power of the closed metering window the kernel ran in,
+ * times the kernel's device time.  SY_ERR_NOT_READY if the kernel was not
+ * issued inside a window that has since been closed. */
+sy_status sy_kernel_energy(sy_queue_t q, sy_event ev, double* joules);
+
+/* ------------------------------------------------------------------------- */
+/* SAXPY (paper §2 Listing 1; §3 Listing 2 with one_to_one range mappers)     */
+/* ------------------------------------------------------------------------- */
+
+/* z[i] = alpha * x[i] + y[i] for i in [0, n), evaluated as two FP32 roundings
+ * fl(fl(alpha * x[i]) + y[i]) (no fused multiply-add).  x, y, z: device
+ * pointers to n floats.  z may be exactly x or exactly y (in place) but must not
+ * partially overlap either.  Any alignment is accepted (16-byte aligned
+ * pointers take the vector path).  n == 0 is a no-op.  `ev` (nullable) receives
+ * the event of the launch. */
+sy_status sy_saxpy(sy_queue_t q, int64_t n, float alpha, const float* x, const float* y, float* z, sy_event* ev);
+
+/* The same kernel split into chunks (paper §3, Listing 2): chunk c covers
+ * [chunks[c].begin, chunks[c].end) with one_to_one range mappers, one launch per
+ * chunk.  The chunks must tile [0, n) in order; events (nullable) receives
+ * n_chunks event ids. */
+sy_status sy_saxpy_split(sy_queue_t q, int64_t n, float alpha, const float* x, const float* y, float* z,
+                         const sy_chunk* chunks, int n_chunks, sy_event* events);
+
+/* ------------------------------------------------------------------------- */
+/* Range mappers and splitting (paper §3)                                     */
+/* ------------------------------------------------------------------------- */
+
+/* Even split of [0, n) into k chunks; the first n % k chunks are one longer.
+ * out: host array of k chunks.  k >= 1, n >= 0. */
+sy_status sy_split_rows(int64_t n, int k, sy_chunk* out);
+
+/* one_to_one range mapper: chunk [begin, end) touches exactly [begin, end). */
+sy_status sy_rm_one_to_one(sy_chunk chunk, sy_chunk* region);
+
+/* neighbourhood range mapper of radius r: chunk [begin, end) of a domain of n
+ * rows reads [begin - r, end + r) clipped to [0, n). */
+sy_status sy_rm_neighbourhood(sy_chunk chunk, int radius, int64_t n, sy_chunk* region);
+
+/* SY_OK when chunks tile [0, n) in order with no empty chunk, else
+ * SY_ERR_BAD_CHUNKS. */
+sy_status sy_chunks_validate(int64_t n, const sy_chunk* chunks, int n_chunks);
+
+/* ------------------------------------------------------------------------- */
+/* 2D leapfrog wave stencil (range-split, neighbourhood range mappers)        */
+/* ------------------------------------------------------------------------- */
+/* The field is row-major: element (i, j), 0 <= i < ny, 0 <= j < nx, lives at
+ * index i * pitch + j; a field buffer holds ny * pitch elements of its dtype.
+ * Points outside the grid are zero (Dirichlet-zero ghosts).
+ *
+ *   L u_ij  = 2 w_0 u_ij + sum_{k=1..r} w_k ((u_{i-k,j} + u_{i+k,j}) + (u_{i,j-k} + u_{i,j+k}))
+ *   u^{n+1} = (2 u^n - u^{n-1}) + c2 * L u^n
+ *
+ * with w the order-2r central second-difference weights (r = 1: 1, -2, 1;
+ * r = 2: -1/12, 4/3, -5/2, ...; Fornberg 1988) rounded once to FP32, evaluated
+ * in FP32 in exactly this order, and the result rounded once to the storage
+ * type (round to nearest even).  16-bit values are widened exactly to FP32. */
+
+typedef struct sy_stencil_params {
+    int64_t ny;      /* rows (>= 0) */
+    int64_t nx;      /* columns (>= 0) */
+    int64_t pitch;   /* elements between row starts (>= nx) */
+    int32_t radius;  /* stencil radius r, 1..4 */
+    int32_t dtype;   /* sy_dtype of all three fields */
+    float c2;        /* (c dt / dx)^2 */
+    int32_t variant; /* kernel tile variant, 0 = library default (see sy_stencil_variant_count) */
+} sy_stencil_params;
+
+/* One leapfrog step, split into row chunks with a neighbourhood range mapper of
+ * radius halo_radius: chunk c writes rows [begin, end) of u_next and reads rows
+ * [begin - r, end + r) (clipped) of u_cur and rows [begin, end) of u_prev; one
+ * launch per chunk, in list order, on the queue's stream.
+ *   u_prev, u_cur: device pointers (read); u_next: device pointer (written).
+ *   u_next may be exactly u_prev (in place) but must not overlap u_cur, nor
+ *   partially overlap u_prev.
+ *   chunks: host array tiling [0, ny) in order (SY_ERR_BAD_CHUNKS otherwise).
+ *   halo_radius < radius gives SY_ERR_HALO_TOO_SMALL.
+ *   chunk_events (nullable): n_chunks event ids, one per chunk launch.
+ * Results do not depend on the chunking: any valid chunk list gives the same
+ * bits. */
+sy_status sy_stencil_step(sy_queue_t q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
+                          void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                          sy_event* chunk_events);
+
+/* Taylor start for zero initial velocity: u_m1 = u0 + (c2 / 2) * L u0, evaluated
+ * as fl(u0 + fl((c2/2) * L u0)) with L as above (bit-identical to a step with c2
+ * halved and u_prev = u_cur = u0).  u_m1 must not overlap u0.  Same chunk rules
+ * as sy_stencil_step. */
+sy_status sy_stencil_start(sy_queue_t q, const sy_stencil_params* p, const void* u0, void* u_m1,
+                           const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* chunk_events);
+
+/* Number of tile variants for a (radius, dtype); variant ids are 1..count
+ * (0 always means the default).  tile_rows / tile_cols / threads (nullable)
+ * describe variant `variant`. */
+sy_status sy_stencil_variant_count(int radius, int dtype, int* count);
+sy_status sy_stencil_variant_info(int radius, int dtype, int variant, int* tile_rows, int* tile_cols,
+                                  int* threads);
+
+/* Discrete energy of the leapfrog scheme, conserved exactly when L is symmetric:
+ *   E^{n+1/2} = sum (u_new - u_old)^2 - c2 * sum u_new * (L u_old)
+ * summed over the whole grid in FP64 (fields widened exactly; L with FP64
+ * weights).  The reduction has a fixed shape, so repeated calls give identical
+ * bits.  Synchronises the queue; energy, kinetic (sum of squares) and potential
+ * (sum u_new * L u_old) are host pointers, the last two nullable.  Uses a
+ * scratch buffer the queue allocates on first use. */
+sy_status sy_wave_energy(sy_queue_t q, const sy_stencil_params* p, const void* u_new, const void* u_old,
+                         double* energy, double* kinetic, double* potential);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SY_H */

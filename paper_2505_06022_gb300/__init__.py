@@ -1,7 +1,324 @@
 """GB300-native range-mapped data-parallel kernels with energy metering.
 
-The compute path is libsy.so (hand-written sm_103a CUDA behind a C ABI, declared
-in include/sy.h); this package is its thin Python binding.  The library is
-loaded on first use, not at import, so `paper_2505_06022_gb300.inputs` can be
-imported on hosts without the built library.
+The compute path is libsy.so: hand-written sm_103a CUDA behind the C ABI declared
+in include/sy.h.  This package is its thin Python binding: every function named
+`sy_*` here marshals its arguments (torch tensors -> device pointers, Python
+lists -> C arrays) and calls the C entry point of the same name; no step of the
+computation runs in Python or PyTorch.  PyTorch provides device memory and
+streams only.
+
+The library is loaded on first use, not at import, so `inputs` can be imported
+on hosts without a GPU.  If libsy.so is missing or older than its sources it is
+built with nvcc; if that is impossible the call raises -- there is no fallback.
 """
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+__all__ = [
+    "SyError", "lib", "lib_path", "Queue", "Chunk", "StencilParams",
+    "SY_F32", "SY_BF16", "SY_F16", "DTYPE_CODES",
+]
+
+SY_F32, SY_BF16, SY_F16 = 0, 1, 2
+DTYPE_CODES = {"f32": SY_F32, "bf16": SY_BF16, "f16": SY_F16}
+
+STATUS = {
+    0: "SY_OK", 1: "SY_ERR_INVALID_ARGUMENT", 2: "SY_ERR_NULL_POINTER", 3: "SY_ERR_ALIAS",
+    4: "SY_ERR_BAD_CHUNKS", 5: "SY_ERR_HALO_TOO_SMALL", 6: "SY_ERR_UNSUPPORTED", 7: "SY_ERR_CUDA",
+    8: "SY_ERR_NVML_UNAVAILABLE", 9: "SY_ERR_TIMEOUT", 10: "SY_ERR_OUT_OF_MEMORY", 11: "SY_ERR_NOT_READY",
+    12: "SY_ERR_IO",
+}
+
+
+class SyError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Chunk(C.Structure):
+    _fields_ = [("begin", C.c_int64), ("end", C.c_int64)]
+
+
+class StencilParams(C.Structure):
+    _fields_ = [("ny", C.c_int64), ("nx", C.c_int64), ("pitch", C.c_int64), ("radius", C.c_int32),
+                ("dtype", C.c_int32), ("c2", C.c_float), ("variant", C.c_int32)]
+
+
+_p = C.c_void_p
+_i64 = C.c_int64
+_u64 = C.c_uint64
+_st = C.c_int
+_lock = threading.Lock()
+_lib = None
+
+# name: (argtypes) -- every entry returns sy_status unless listed in _RESTYPE
+_SIGS = {
+    "sy_status_string": [_st],
+    "sy_last_error": [],
+    "sy_abi_version": [],
+    "sy_queue_create": [C.c_int, _p, _p],
+    "sy_queue_destroy": [_p],
+    "sy_queue_sync": [_p],
+    "sy_queue_stream": [_p, _p],
+    "sy_queue_launch_count": [_p, _p],
+    "sy_event_elapsed": [_p, _u64, _p],
+    "sy_energy_read": [_p, _p],
+    "sy_device_energy": [_p, _p],
+    "sy_meter_begin": [_p],
+    "sy_meter_end": [_p, _p, _p],
+    "sy_kernel_energy": [_p, _u64, _p],
+    "sy_saxpy": [_p, _i64, C.c_float, _p, _p, _p, _p],
+    "sy_saxpy_split": [_p, _i64, C.c_float, _p, _p, _p, _p, C.c_int, _p],
+    "sy_split_rows": [_i64, C.c_int, _p],
+    "sy_rm_one_to_one": [Chunk, _p],
+    "sy_rm_neighbourhood": [Chunk, C.c_int, _i64, _p],
+    "sy_chunks_validate": [_i64, _p, C.c_int],
+    "sy_stencil_step": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
+    "sy_stencil_start": [_p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
+    "sy_stencil_variant_count": [C.c_int, C.c_int, _p],
+    "sy_stencil_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p, _p],
+    "sy_wave_energy": [_p, _p, _p, _p, _p, _p, _p],
+}
+_RESTYPE = {"sy_status_string": C.c_char_p, "sy_last_error": C.c_char_p, "sy_abi_version": C.c_int}
+
+
+def lib_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsy.so")
+
+
+def lib() -> C.CDLL:
+    """Load libsy.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import _build
+
+            path = _build.build()
+            L = C.CDLL(path)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.argtypes = args
+                fn.restype = _RESTYPE.get(name, _st)
+            _lib = L
+    return _lib
+
+
+def _call(name: str, *args) -> None:
+    L = lib()
+    rc = getattr(L, name)(*args)
+    if rc != 0:
+        raise SyError(rc, L.sy_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> int | None:
+    """Device (or host) address of a tensor / integer address / None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _chunks(chunks) -> tuple[C.Array, int]:
+    chunks = list(chunks)
+    arr = (Chunk * max(1, len(chunks)))(*[Chunk(int(a), int(b)) for a, b in chunks])
+    return arr, len(chunks)
+
+
+# ---------------------------------------------------------------------------
+# C entry points, one wrapper per name
+# ---------------------------------------------------------------------------
+
+def sy_abi_version() -> int:
+    return lib().sy_abi_version()
+
+
+def sy_status_string(status: int) -> str:
+    return lib().sy_status_string(status).decode()
+
+
+def sy_queue_create(device: int = 0, stream: int | None = None) -> int:
+    h = C.c_void_p()
+    _call("sy_queue_create", device, stream, C.byref(h))
+    return h.value
+
+
+def sy_queue_destroy(q: int) -> None:
+    _call("sy_queue_destroy", q)
+
+
+def sy_queue_sync(q: int) -> None:
+    _call("sy_queue_sync", q)
+
+
+def sy_queue_stream(q: int) -> int:
+    s = C.c_void_p()
+    _call("sy_queue_stream", q, C.byref(s))
+    return s.value or 0
+
+
+def sy_queue_launch_count(q: int) -> int:
+    n = C.c_uint64()
+    _call("sy_queue_launch_count", q, C.byref(n))
+    return n.value
+
+
+def sy_event_elapsed(q: int, ev: int) -> float:
+    ms = C.c_double()
+    _call("sy_event_elapsed", q, ev, C.byref(ms))
+    return ms.value
+
+
+def sy_energy_read(q: int) -> int:
+    mj = C.c_uint64()
+    _call("sy_energy_read", q, C.byref(mj))
+    return mj.value
+
+
+def sy_device_energy(q: int) -> float:
+    j = C.c_double()
+    _call("sy_device_energy", q, C.byref(j))
+    return j.value
+
+
+def sy_meter_begin(q: int) -> None:
+    _call("sy_meter_begin", q)
+
+
+def sy_meter_end(q: int) -> tuple[float, float]:
+    j, s = C.c_double(), C.c_double()
+    _call("sy_meter_end", q, C.byref(j), C.byref(s))
+    return j.value, s.value
+
+
+def sy_kernel_energy(q: int, ev: int) -> float:
+    j = C.c_double()
+    _call("sy_kernel_energy", q, ev, C.byref(j))
+    return j.value
+
+
+def sy_saxpy(q: int, n: int, alpha: float, x, y, z, want_event: bool = False) -> int:
+    ev = C.c_uint64()
+    _call("sy_saxpy", q, n, alpha, _ptr(x), _ptr(y), _ptr(z), C.byref(ev) if want_event else None)
+    return ev.value
+
+
+def sy_saxpy_split(q: int, n: int, alpha: float, x, y, z, chunks, want_events: bool = False) -> list[int]:
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))()
+    _call("sy_saxpy_split", q, n, alpha, _ptr(x), _ptr(y), _ptr(z), arr, k, evs if want_events else None)
+    return list(evs[:k]) if want_events else []
+
+
+def sy_split_rows(n: int, k: int) -> list[tuple[int, int]]:
+    arr = (Chunk * max(1, k))()
+    _call("sy_split_rows", n, k, arr)
+    return [(arr[i].begin, arr[i].end) for i in range(k)]
+
+
+def sy_rm_one_to_one(chunk) -> tuple[int, int]:
+    out = Chunk()
+    _call("sy_rm_one_to_one", Chunk(*chunk), C.byref(out))
+    return out.begin, out.end
+
+
+def sy_rm_neighbourhood(chunk, radius: int, n: int) -> tuple[int, int]:
+    out = Chunk()
+    _call("sy_rm_neighbourhood", Chunk(*chunk), radius, n, C.byref(out))
+    return out.begin, out.end
+
+
+def sy_chunks_validate(n: int, chunks) -> None:
+    arr, k = _chunks(chunks)
+    _call("sy_chunks_validate", n, arr, k)
+
+
+def stencil_params(ny: int, nx: int, radius: int = 1, c2: float = 0.25, dtype: str | int = "f32",
+                   pitch: int | None = None, variant: int = 0) -> StencilParams:
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    return StencilParams(ny, nx, nx if pitch is None else pitch, radius, code, c2, variant)
+
+
+def sy_stencil_step(q: int, p: StencilParams, u_prev, u_cur, u_next, chunks, halo_radius: int,
+                    want_events: bool = False) -> list[int]:
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))()
+    _call("sy_stencil_step", q, C.byref(p), _ptr(u_prev), _ptr(u_cur), _ptr(u_next), arr, k, halo_radius,
+          evs if want_events else None)
+    return list(evs[:k]) if want_events else []
+
+
+def sy_stencil_start(q: int, p: StencilParams, u0, u_m1, chunks, halo_radius: int,
+                     want_events: bool = False) -> list[int]:
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))()
+    _call("sy_stencil_start", q, C.byref(p), _ptr(u0), _ptr(u_m1), arr, k, halo_radius,
+          evs if want_events else None)
+    return list(evs[:k]) if want_events else []
+
+
+def sy_stencil_variant_count(radius: int, dtype: int) -> int:
+    n = C.c_int()
+    _call("sy_stencil_variant_count", radius, dtype, C.byref(n))
+    return n.value
+
+
+def sy_stencil_variant_info(radius: int, dtype: int, variant: int) -> tuple[int, int, int]:
+    r, c, t = C.c_int(), C.c_int(), C.c_int()
+    _call("sy_stencil_variant_info", radius, dtype, variant, C.byref(r), C.byref(c), C.byref(t))
+    return r.value, c.value, t.value
+
+
+def sy_wave_energy(q: int, p: StencilParams, u_new, u_old) -> tuple[float, float, float]:
+    e, k, pot = C.c_double(), C.c_double(), C.c_double()
+    _call("sy_wave_energy", q, C.byref(p), _ptr(u_new), _ptr(u_old), C.byref(e), C.byref(k), C.byref(pot))
+    return e.value, k.value, pot.value
+
+
+# ---------------------------------------------------------------------------
+# Convenience: a queue object bound to torch's current stream
+# ---------------------------------------------------------------------------
+
+class Queue:
+    """sy_queue on a CUDA device; borrows `stream` (a torch.cuda.Stream or raw
+    cudaStream_t) or torch's current stream when None."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.handle = sy_queue_create(device, raw or None)
+        self.device = device
+
+    def close(self) -> None:
+        if self.handle:
+            sy_queue_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self) -> None:
+        sy_queue_sync(self.handle)
+
+    @property
+    def launches(self) -> int:
+        return sy_queue_launch_count(self.handle)

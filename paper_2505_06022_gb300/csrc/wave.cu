@@ -1,0 +1,238 @@
+// Wave-step launch logic (grid sizing, variant table, layout checks) and the
+// FP64 discrete-energy reduction.
+//
+// Discrete energy of the leapfrog scheme (conserved exactly when L = L^T):
+//   E^{n+1/2} = sum (u_new - u_old)^2 - c2 * sum u_new * (L u_old)
+// Reduction shape is fixed (kEnergyBlocks blocks x 256 threads, each thread a
+// fixed arithmetic progression of points, a fixed shared-memory tree per block,
+// then one block summing the partials in a fixed tree), so the result does not
+// depend on scheduling: repeated calls give identical bits.
+#include <mutex>
+#include <unordered_map>
+
+#include "wave_kernel.cuh"
+
+namespace sy {
+namespace wave {
+
+namespace {
+std::mutex g_occ_mu;
+std::unordered_map<uint64_t, int> g_occ;
+
+int occupancy(KernelFn fn, int threads) {
+    const uint64_t key = reinterpret_cast<uint64_t>(fn) ^ (static_cast<uint64_t>(threads) << 56);
+    {
+        std::lock_guard<std::mutex> lock(g_occ_mu);
+        auto it = g_occ.find(key);
+        if (it != g_occ.end()) return it->second;
+    }
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, 0) != cudaSuccess || blocks < 1)
+        blocks = 1;
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    g_occ[key] = blocks;
+    return blocks;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+}  // namespace
+
+sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn scalar_fn, int tile_rows,
+                       int threads, int V, size_t esize) {
+    const int64_t rows = w.row_end - w.row_begin;
+    if (rows <= 0 || w.nx == 0) return SY_OK;
+    Args a;
+    a.u_prev = static_cast<const char*>(w.u_prev);
+    a.u_cur = static_cast<const char*>(w.u_cur);
+    a.u_next = static_cast<char*>(w.u_next);
+    a.ny = w.ny;
+    a.nx = w.nx;
+    a.pitch_bytes = w.pitch * static_cast<int64_t>(esize);
+    a.row_begin = w.row_begin;
+    a.row_end = w.row_end;
+    a.c2 = w.c2;
+    if (!aligned(w.u_cur, esize) || !aligned(w.u_next, esize) || (!w.start && !aligned(w.u_prev, esize)))
+        return fail(SY_ERR_INVALID_ARGUMENT, "field pointers must be aligned to the element size (%zu bytes)", esize);
+    const bool vec_ok = aligned(w.u_cur, 16) && aligned(w.u_next, 16) && (w.start || aligned(w.u_prev, 16)) &&
+                        (a.pitch_bytes % 16) == 0;
+    if (vec_ok) {
+        const int64_t span = 32 * static_cast<int64_t>(V);
+        a.tiles_x = (w.nx + span - 1) / span;
+        a.tiles = a.tiles_x * ((rows + tile_rows - 1) / tile_rows);
+        const int64_t wpb = threads / 32;
+        int64_t blocks = (a.tiles + wpb - 1) / wpb;
+        const int64_t cap = static_cast<int64_t>(occupancy(vec_fn, threads)) * q->sm_count;
+        if (blocks > cap) blocks = cap;
+        vec_fn<<<static_cast<unsigned>(blocks), threads, 0, q->stream>>>(a);
+    } else {
+        a.tiles_x = 0;
+        a.tiles = 0;
+        const int64_t total = rows * w.nx;
+        int64_t blocks = (total + 255) / 256;
+        const int64_t cap = static_cast<int64_t>(q->sm_count) * 8;
+        if (blocks > cap) blocks = cap;
+        scalar_fn<<<static_cast<unsigned>(blocks), 256, 0, q->stream>>>(a);
+    }
+    SY_CUDA(cudaGetLastError());
+    ++q->launches;
+    return SY_OK;
+}
+
+}  // namespace wave
+
+int wave_variant_count(int, int) { return wave::kVariants; }
+
+bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* tile_cols, int* threads) {
+    if (radius < 1 || radius > 4 || dtype_size(dtype) == 0 || variant < 0 || variant > wave::kVariants)
+        return false;
+    int rows, thr;
+    if (variant == 0) {
+        rows = 8;
+        thr = 256;
+    } else {
+        rows = wave::kTileRows[(variant - 1) % 4];
+        thr = wave::kBlockThreads[(variant - 1) / 4];
+    }
+    if (tile_rows) *tile_rows = rows;
+    if (threads) *threads = thr;
+    if (tile_cols) *tile_cols = 32 * static_cast<int>(16 / dtype_size(dtype));
+    return true;
+}
+
+sy_status launch_wave(Queue* q, const WaveLaunch& w) {
+    int tile_rows = 0, threads = 0;
+    if (!wave_variant_info(w.radius, w.dtype, w.variant, &tile_rows, nullptr, &threads))
+        return fail(SY_ERR_INVALID_ARGUMENT, "bad stencil variant %d", w.variant);
+    switch (w.dtype) {
+        case SY_F32: return wave::launch_f32(q, w, tile_rows, threads);
+        case SY_BF16: return wave::launch_bf16(q, w, tile_rows, threads);
+        case SY_F16: return wave::launch_f16(q, w, tile_rows, threads);
+    }
+    return fail(SY_ERR_INVALID_ARGUMENT, "unknown dtype %d", w.dtype);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 discrete energy
+// ---------------------------------------------------------------------------
+namespace energy {
+
+constexpr int kThreads = 256;
+
+// FP64 weights of the order-2r second difference (exact rationals rounded once).
+template <int R>
+__device__ __forceinline__ double c0x2_64() {
+    return R == 1 ? -4.0 : R == 2 ? -5.0 : R == 3 ? -49.0 / 9.0 : -205.0 / 36.0;
+}
+template <int R>
+__device__ __forceinline__ double wk64(int k) {
+    if (R == 1) return 1.0;
+    if (R == 2) return k == 1 ? 4.0 / 3.0 : -1.0 / 12.0;
+    if (R == 3) return k == 1 ? 1.5 : k == 2 ? -3.0 / 20.0 : 1.0 / 90.0;
+    return k == 1 ? 8.0 / 5.0 : k == 2 ? -1.0 / 5.0 : k == 3 ? 8.0 / 315.0 : -1.0 / 560.0;
+}
+
+struct EArgs {
+    const char* u_new;
+    const char* u_old;
+    int64_t ny, nx, pitch_bytes;
+};
+
+template <typename S, int R>
+__global__ void __launch_bounds__(kThreads) energy_partials_kernel(EArgs a, double* partials) {
+    using T = wave::Traits<S>;
+    auto at = [&](const char* base, int64_t i, int64_t j) -> double {
+        if (i < 0 || i >= a.ny || j < 0 || j >= a.nx) return 0.0;
+        return static_cast<double>(T::load1(base + i * a.pitch_bytes + j * static_cast<int64_t>(sizeof(S))));
+    };
+    double kin = 0.0, pot = 0.0;
+    const int64_t total = a.ny * a.nx;
+    const int64_t stride = static_cast<int64_t>(kEnergyBlocks) * kThreads;
+    for (int64_t p = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; p < total; p += stride) {
+        const int64_t i = p / a.nx, j = p - (p / a.nx) * a.nx;
+        const double un = at(a.u_new, i, j), uo = at(a.u_old, i, j);
+        double lap = __dmul_rn(c0x2_64<R>(), uo);
+#pragma unroll
+        for (int k = 1; k <= R; ++k) {
+            double vert = __dadd_rn(at(a.u_old, i - k, j), at(a.u_old, i + k, j));
+            double horz = __dadd_rn(at(a.u_old, i, j - k), at(a.u_old, i, j + k));
+            lap = __dadd_rn(lap, __dmul_rn(wk64<R>(k), __dadd_rn(vert, horz)));
+        }
+        const double d = __dsub_rn(un, uo);
+        kin = __dadd_rn(kin, __dmul_rn(d, d));
+        pot = __dadd_rn(pot, __dmul_rn(un, lap));
+    }
+    __shared__ double sk[kThreads], sp[kThreads];
+    sk[threadIdx.x] = kin;
+    sp[threadIdx.x] = pot;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sk[threadIdx.x] = __dadd_rn(sk[threadIdx.x], sk[threadIdx.x + s]);
+            sp[threadIdx.x] = __dadd_rn(sp[threadIdx.x], sp[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = sk[0];
+        partials[2 * blockIdx.x + 1] = sp[0];
+    }
+}
+
+// One block of kEnergyBlocks threads; partials holds 2 * kEnergyBlocks doubles.
+__global__ void __launch_bounds__(kEnergyBlocks) energy_final_kernel(const double* partials, double c2,
+                                                                     double* out3) {
+    __shared__ double sk[kEnergyBlocks], sp[kEnergyBlocks];
+    sk[threadIdx.x] = partials[2 * threadIdx.x];
+    sp[threadIdx.x] = partials[2 * threadIdx.x + 1];
+    __syncthreads();
+    for (int s = kEnergyBlocks / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sk[threadIdx.x] = __dadd_rn(sk[threadIdx.x], sk[threadIdx.x + s]);
+            sp[threadIdx.x] = __dadd_rn(sp[threadIdx.x], sp[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out3[0] = __dsub_rn(sk[0], __dmul_rn(c2, sp[0]));
+        out3[1] = sk[0];
+        out3[2] = sp[0];
+    }
+}
+
+template <typename S>
+void launch_partials(int radius, EArgs a, double* partials, cudaStream_t s) {
+    switch (radius) {
+        case 1: energy_partials_kernel<S, 1><<<kEnergyBlocks, kThreads, 0, s>>>(a, partials); break;
+        case 2: energy_partials_kernel<S, 2><<<kEnergyBlocks, kThreads, 0, s>>>(a, partials); break;
+        case 3: energy_partials_kernel<S, 3><<<kEnergyBlocks, kThreads, 0, s>>>(a, partials); break;
+        default: energy_partials_kernel<S, 4><<<kEnergyBlocks, kThreads, 0, s>>>(a, partials); break;
+    }
+}
+
+}  // namespace energy
+
+sy_status launch_wave_energy(Queue* q, const sy_stencil_params* p, const void* u_new, const void* u_old,
+                             double* partials, int n_partials, double* out3_device) {
+    if (n_partials != kEnergyBlocks) return fail(SY_ERR_INVALID_ARGUMENT, "energy partials must be %d", kEnergyBlocks);
+    const size_t esize = dtype_size(p->dtype);
+    if ((reinterpret_cast<uintptr_t>(u_new) % esize) || (reinterpret_cast<uintptr_t>(u_old) % esize))
+        return fail(SY_ERR_INVALID_ARGUMENT, "field pointers must be aligned to the element size");
+    energy::EArgs a;
+    a.u_new = static_cast<const char*>(u_new);
+    a.u_old = static_cast<const char*>(u_old);
+    a.ny = p->ny;
+    a.nx = p->nx;
+    a.pitch_bytes = p->pitch * static_cast<int64_t>(esize);
+    switch (p->dtype) {
+        case SY_F32: energy::launch_partials<float>(p->radius, a, partials, q->stream); break;
+        case SY_BF16: energy::launch_partials<__nv_bfloat16>(p->radius, a, partials, q->stream); break;
+        default: energy::launch_partials<__half>(p->radius, a, partials, q->stream); break;
+    }
+    SY_CUDA(cudaGetLastError());
+    energy::energy_final_kernel<<<1, kEnergyBlocks, 0, q->stream>>>(partials, static_cast<double>(p->c2), out3_device);
+    SY_CUDA(cudaGetLastError());
+    q->launches += 2;
+    return SY_OK;
+}
+
+}  // namespace sy

@@ -1,0 +1,13 @@
+// Wave-step kernel instantiations for bf16 storage (all radii, tile heights,
+// step and start forms).  The kernels themselves are in wave_kernel.cuh.
+#include "wave_kernel.cuh"
+
+namespace sy {
+namespace wave {
+
+sy_status launch_bf16(Queue* q, const WaveLaunch& w, int tile_rows, int threads) {
+    return launch_dtype<__nv_bfloat16>(q, w, tile_rows, threads);
+}
+
+}  // namespace wave
+}  // namespace sy

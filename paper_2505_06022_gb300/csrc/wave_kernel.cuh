@@ -1,0 +1,360 @@
+// Leapfrog wave step kernels (radius-r star stencil, Dirichlet-zero ghosts) for
+// one row chunk of a row-major field.  Included by wave_f32.cu, wave_bf16.cu and
+// wave_f16.cu, one storage type each.
+//
+//   L u_ij  = 2 w_0 u_ij + sum_{k=1..r} w_k ((u_{i-k,j} + u_{i+k,j}) + (u_{i,j-k} + u_{i,j+k}))
+//   u^{n+1} = (2 u^n - u^{n-1}) + c2 * L u^n          (start: u^{-1} = u^0 + (c2/2) L u^0)
+//
+// Every operation is an explicit round-to-nearest FP32 intrinsic in exactly this
+// order, so no FMA contraction can change a bit; 16-bit storage is widened
+// exactly and the result rounded once (round to nearest even).
+//
+// Vector kernel (16-byte aligned rows): HBM-bound, 3 x sizeof(S) bytes per point.
+//   * A warp owns a tile of 32*V columns x RY rows (V = 16 / sizeof(S)); lane l
+//     owns the V columns [x0, x0+V) and marches down the RY rows.
+//   * All loads of a tile are issued before any arithmetic: RY+2r rows of u_cur
+//     (halo rows included, read through the non-coherent path: u_cur is never
+//     written during the step), RY rows of u_prev and the two warp-edge vectors
+//     per row, each a single 128-bit access.  u_prev/u_next are streamed
+//     (ld.global.cs / st.global.cs: touched once), u_cur keeps default caching
+//     so that the halo rows re-read by the tile below hit in L2.
+//   * Horizontal neighbours come from the adjacent lanes by warp shuffles; only
+//     lanes 0 and 31 load the r columns beyond the warp's span.
+//   * Warps stride over the tiles of the chunk in row-major tile order, so the
+//     tiles in flight at any moment form a narrow band of rows and the halo rows
+//     are still in L2 when they are read again.
+// Scalar kernel: any layout whose rows are not 16-byte aligned; one point per
+// thread, same arithmetic.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "sy_internal.h"
+
+namespace sy {
+namespace wave {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- weights: the order-2r central second difference, rounded once to FP32 ----
+// r = 1: 1, -2, 1;  r = 2: -1/12, 4/3, -5/2;  r = 3: 1/90, -3/20, 3/2, -49/18;
+// r = 4: -1/560, 8/315, -1/5, 8/5, -205/72 (Fornberg 1988).  c0x2 = 2 w_0 (the
+// centre weight of the 2D star counts once per axis).
+template <int R>
+__device__ __forceinline__ float c0x2();
+template <>
+__device__ __forceinline__ float c0x2<1>() { return -4.0f; }
+template <>
+__device__ __forceinline__ float c0x2<2>() { return -5.0f; }
+template <>
+__device__ __forceinline__ float c0x2<3>() { return static_cast<float>(-49.0 / 9.0); }
+template <>
+__device__ __forceinline__ float c0x2<4>() { return static_cast<float>(-205.0 / 36.0); }
+
+template <int R>
+__device__ __forceinline__ float wk(int k);
+template <>
+__device__ __forceinline__ float wk<1>(int) { return 1.0f; }
+template <>
+__device__ __forceinline__ float wk<2>(int k) {
+    return k == 1 ? static_cast<float>(4.0 / 3.0) : static_cast<float>(-1.0 / 12.0);
+}
+template <>
+__device__ __forceinline__ float wk<3>(int k) {
+    return k == 1 ? 1.5f : (k == 2 ? static_cast<float>(-3.0 / 20.0) : static_cast<float>(1.0 / 90.0));
+}
+template <>
+__device__ __forceinline__ float wk<4>(int k) {
+    return k == 1   ? static_cast<float>(8.0 / 5.0)
+           : k == 2 ? static_cast<float>(-1.0 / 5.0)
+           : k == 3 ? static_cast<float>(8.0 / 315.0)
+                    : static_cast<float>(-1.0 / 560.0);
+}
+
+// ---- storage traits: a 16-byte unit holds V elements -----------------------------
+template <typename S>
+struct Traits;
+
+__device__ __forceinline__ uint32_t word(const uint4& r, int i) {
+    return i == 0 ? r.x : (i == 1 ? r.y : (i == 2 ? r.z : r.w));
+}
+__device__ __forceinline__ void set_word(uint4& r, int i, uint32_t v) {
+    if (i == 0) r.x = v;
+    else if (i == 1) r.y = v;
+    else if (i == 2) r.z = v;
+    else r.w = v;
+}
+
+template <>
+struct Traits<float> {
+    static constexpr int V = 4;
+    __device__ static __forceinline__ float elem(const uint4& r, int e) { return __uint_as_float(word(r, e)); }
+    // zero elements e >= nvalid
+    __device__ static __forceinline__ void mask(uint4& r, int nvalid) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            if (e >= nvalid) set_word(r, e, 0u);
+    }
+    __device__ static __forceinline__ uint4 pack(const float (&v)[V]) {
+        return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]),
+                          __float_as_uint(v[3]));
+    }
+    __device__ static __forceinline__ float load1(const char* p) { return __ldg(reinterpret_cast<const float*>(p)); }
+    __device__ static __forceinline__ float load1_cs(const char* p) {
+        return __ldcs(reinterpret_cast<const float*>(p));
+    }
+    __device__ static __forceinline__ void store1(char* p, float v) { *reinterpret_cast<float*>(p) = v; }
+};
+
+template <>
+struct Traits<__nv_bfloat16> {
+    static constexpr int V = 8;
+    __device__ static __forceinline__ float elem(const uint4& r, int e) {
+        uint32_t w = word(r, e >> 1);
+        return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
+    }
+    __device__ static __forceinline__ void mask(uint4& r, int nvalid) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            if (e >= nvalid) set_word(r, e >> 1, word(r, e >> 1) & ((e & 1) ? 0x0000ffffu : 0xffff0000u));
+    }
+    __device__ static __forceinline__ uint32_t bits(float v) {
+        return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
+    }
+    __device__ static __forceinline__ uint4 pack(const float (&v)[V]) {
+        return make_uint4(bits(v[0]) | (bits(v[1]) << 16), bits(v[2]) | (bits(v[3]) << 16),
+                          bits(v[4]) | (bits(v[5]) << 16), bits(v[6]) | (bits(v[7]) << 16));
+    }
+    __device__ static __forceinline__ float load1(const char* p) {
+        return __uint_as_float(static_cast<uint32_t>(__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
+    }
+    __device__ static __forceinline__ float load1_cs(const char* p) {
+        return __uint_as_float(static_cast<uint32_t>(__ldcs(reinterpret_cast<const unsigned short*>(p))) << 16);
+    }
+    __device__ static __forceinline__ void store1(char* p, float v) {
+        *reinterpret_cast<unsigned short*>(p) = static_cast<unsigned short>(bits(v));
+    }
+};
+
+template <>
+struct Traits<__half> {
+    static constexpr int V = 8;
+    __device__ static __forceinline__ float elem(const uint4& r, int e) {
+        uint32_t w = word(r, e >> 1);
+        unsigned short h = static_cast<unsigned short>((e & 1) ? (w >> 16) : (w & 0xffffu));
+        return __half2float(__ushort_as_half(h));
+    }
+    __device__ static __forceinline__ void mask(uint4& r, int nvalid) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            if (e >= nvalid) set_word(r, e >> 1, word(r, e >> 1) & ((e & 1) ? 0x0000ffffu : 0xffff0000u));
+    }
+    __device__ static __forceinline__ uint32_t bits(float v) {
+        return static_cast<uint32_t>(__half_as_ushort(__float2half_rn(v)));
+    }
+    __device__ static __forceinline__ uint4 pack(const float (&v)[V]) {
+        return make_uint4(bits(v[0]) | (bits(v[1]) << 16), bits(v[2]) | (bits(v[3]) << 16),
+                          bits(v[4]) | (bits(v[5]) << 16), bits(v[6]) | (bits(v[7]) << 16));
+    }
+    __device__ static __forceinline__ float load1(const char* p) {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+    }
+    __device__ static __forceinline__ float load1_cs(const char* p) {
+        return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p))));
+    }
+    __device__ static __forceinline__ void store1(char* p, float v) {
+        *reinterpret_cast<unsigned short*>(p) = static_cast<unsigned short>(bits(v));
+    }
+};
+
+struct Args {
+    const char* u_prev;  // unused by the start kernel
+    const char* u_cur;
+    char* u_next;
+    int64_t ny, nx, pitch_bytes;
+    int64_t row_begin, row_end;
+    int64_t tiles_x, tiles;  // vector kernel: tiles per row band, total tiles
+    float c2;                // coefficient of L u
+};
+
+// One output point from its neighbourhood, in the canonical operation order.
+template <int R, bool START>
+__device__ __forceinline__ float update(float u, float up, const float (&vert)[R], const float (&horz)[R], float c2) {
+    float acc = __fmul_rn(c0x2<R>(), u);
+#pragma unroll
+    for (int d = 1; d <= R; ++d) acc = __fadd_rn(acc, __fmul_rn(wk<R>(d), __fadd_rn(vert[d - 1], horz[d - 1])));
+    if (START) return __fadd_rn(u, __fmul_rn(c2, acc));
+    return __fadd_rn(__fsub_rn(__fmul_rn(2.0f, u), up), __fmul_rn(c2, acc));
+}
+
+template <typename S, int R, int RY, bool START>
+__global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
+    using T = Traits<S>;
+    constexpr int V = T::V;
+    static_assert(R <= V, "radius must not exceed the vector width");
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_per_block = blockDim.x >> 5;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * warps_per_block;
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); t < a.tiles;
+         t += nwarps) {
+        const int64_t ty = t / a.tiles_x;
+        const int64_t tx = t - ty * a.tiles_x;
+        const int64_t x0 = (tx * 32 + lane) * V;
+        const int64_t y0 = a.row_begin + ty * RY;
+        const bool col_in = x0 < a.nx;
+        const int nvalid = col_in ? static_cast<int>(a.nx - x0 < V ? a.nx - x0 : V) : 0;
+
+        // ---- loads: everything for the tile is in flight before any arithmetic ----
+        uint4 cur[RY + 2 * R];
+#pragma unroll
+        for (int k = 0; k < RY + 2 * R; ++k) {
+            const int64_t row = y0 - R + k;
+            cur[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (col_in && row >= 0 && row < a.ny && row < a.row_end + R)
+                cur[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + x0 * sizeof(S)));
+        }
+        uint4 prev[START ? 1 : RY];
+        if (!START) {
+#pragma unroll
+            for (int k = 0; k < RY; ++k) {
+                const int64_t row = y0 + k;
+                prev[k] = make_uint4(0u, 0u, 0u, 0u);
+                if (col_in && row < a.row_end)
+                    prev[k] =
+                        __ldcs(reinterpret_cast<const uint4*>(a.u_prev + row * a.pitch_bytes + x0 * sizeof(S)));
+            }
+        }
+        // warp edges: lane 0 fetches the vector left of the warp, lane 31 the one right of it
+        uint4 edge[RY];
+        const int64_t xe = lane == 0 ? x0 - V : x0 + V;
+        const bool edge_lane = (lane == 0 && xe >= 0) || (lane == 31 && xe < a.nx);
+        const int edge_valid = lane == 0 ? V : static_cast<int>(a.nx - xe < V ? a.nx - xe : V);
+#pragma unroll
+        for (int k = 0; k < RY; ++k) {
+            const int64_t row = y0 + k;
+            edge[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (edge_lane && row < a.row_end)
+                edge[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + xe * sizeof(S)));
+        }
+#pragma unroll
+        for (int k = 0; k < RY + 2 * R; ++k) T::mask(cur[k], nvalid);
+        if (lane == 31) {
+#pragma unroll
+            for (int k = 0; k < RY; ++k) T::mask(edge[k], edge_valid);
+        }
+
+        // ---- arithmetic and stores, row by row ----
+#pragma unroll
+        for (int k = 0; k < RY; ++k) {
+            const int64_t row = y0 + k;
+            // ext[m] holds column x0 - R + m
+            float ext[V + 2 * R];
+#pragma unroll
+            for (int e = 0; e < V; ++e) ext[R + e] = T::elem(cur[k + R], e);
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                float from_left = __shfl_up_sync(kFull, ext[R + V - d], 1);
+                float from_right = __shfl_down_sync(kFull, ext[R + d - 1], 1);
+                ext[R - d] = lane == 0 ? T::elem(edge[k], V - d) : from_left;
+                ext[R + V - 1 + d] = lane == 31 ? T::elem(edge[k], d - 1) : from_right;
+            }
+            float out[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                float vert[R], horz[R];
+#pragma unroll
+                for (int d = 1; d <= R; ++d) {
+                    vert[d - 1] = __fadd_rn(T::elem(cur[k + R - d], e), T::elem(cur[k + R + d], e));
+                    horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                }
+                const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
+                out[e] = update<R, START>(ext[R + e], up, vert, horz, a.c2);
+            }
+            if (col_in && row < a.row_end) {
+                char* dst = a.u_next + row * a.pitch_bytes + x0 * sizeof(S);
+                if (nvalid == V) {
+                    __stcs(reinterpret_cast<uint4*>(dst), T::pack(out));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (e < nvalid) T::store1(dst + e * sizeof(S), out[e]);
+                }
+            }
+        }
+    }
+}
+
+// One point per thread; any element-aligned layout.
+template <typename S, int R, bool START>
+__global__ void __launch_bounds__(256) wave_scalar_kernel(Args a) {
+    using T = Traits<S>;
+    const int64_t rows = a.row_end - a.row_begin;
+    const int64_t total = rows * a.nx;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < total; p += stride) {
+        const int64_t i = a.row_begin + p / a.nx;
+        const int64_t j = p - (i - a.row_begin) * a.nx;
+        auto at = [&](int64_t ii, int64_t jj) -> float {
+            if (ii < 0 || ii >= a.ny || jj < 0 || jj >= a.nx) return 0.0f;
+            return T::load1(a.u_cur + ii * a.pitch_bytes + jj * static_cast<int64_t>(sizeof(S)));
+        };
+        float vert[R], horz[R];
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+            vert[d - 1] = __fadd_rn(at(i - d, j), at(i + d, j));
+            horz[d - 1] = __fadd_rn(at(i, j - d), at(i, j + d));
+        }
+        const int64_t off = i * a.pitch_bytes + j * static_cast<int64_t>(sizeof(S));
+        const float up = START ? 0.0f : T::load1_cs(a.u_prev + off);
+        T::store1(a.u_next + off, update<R, START>(at(i, j), up, vert, horz, a.c2));
+    }
+}
+
+// Row heights of the vector kernel's tiles; variant v (1-based) = (kTileRows[(v-1) % 4],
+// kBlockThreads[(v-1) / 4]).
+constexpr int kTileRows[4] = {2, 4, 8, 16};
+constexpr int kBlockThreads[2] = {128, 256};
+constexpr int kVariants = 8;
+
+using KernelFn = void (*)(Args);
+
+// Launch helper shared by the per-dtype translation units.
+sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn scalar_fn, int tile_rows,
+                       int threads, int V, size_t esize);
+
+template <typename S, int R, bool START>
+KernelFn pick_vec(int tile_rows) {
+    switch (tile_rows) {
+        case 2: return wave_vec_kernel<S, R, 2, START>;
+        case 4: return wave_vec_kernel<S, R, 4, START>;
+        case 8: return wave_vec_kernel<S, R, 8, START>;
+        default: return wave_vec_kernel<S, R, 16, START>;
+    }
+}
+
+template <typename S, int R>
+sy_status launch_r(Queue* q, const WaveLaunch& w, int tile_rows, int threads) {
+    KernelFn vec = w.start ? pick_vec<S, R, true>(tile_rows) : pick_vec<S, R, false>(tile_rows);
+    KernelFn sca = w.start ? wave_scalar_kernel<S, R, true> : wave_scalar_kernel<S, R, false>;
+    return launch_typed(q, w, vec, sca, tile_rows, threads, Traits<S>::V, sizeof(S));
+}
+
+template <typename S>
+sy_status launch_dtype(Queue* q, const WaveLaunch& w, int tile_rows, int threads) {
+    switch (w.radius) {
+        case 1: return launch_r<S, 1>(q, w, tile_rows, threads);
+        case 2: return launch_r<S, 2>(q, w, tile_rows, threads);
+        case 3: return launch_r<S, 3>(q, w, tile_rows, threads);
+        default: return launch_r<S, 4>(q, w, tile_rows, threads);
+    }
+}
+
+sy_status launch_f32(Queue* q, const WaveLaunch& w, int tile_rows, int threads);
+sy_status launch_bf16(Queue* q, const WaveLaunch& w, int tile_rows, int threads);
+sy_status launch_f16(Queue* q, const WaveLaunch& w, int tile_rows, int threads);
+
+}  // namespace wave
+}  // namespace sy

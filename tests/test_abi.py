@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads and exports every symbol include/sy.h declares;
+host-only entry points (no GPU needed) agree with the oracle bit for bit."""
+import ctypes as C
+import re
+import subprocess
+
+import pytest
+
+import oracle
+import paper_2505_06022_gb300 as sy
+
+ROOT = __file__.rsplit("/tests/", 1)[0]
+
+
+def declared_symbols():
+    text = open(ROOT + "/include/sy.h").read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(sy_[a-z0-9_]+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ["sy_queue_create", "sy_saxpy", "sy_stencil_step", "sy_split_rows", "sy_energy_read",
+                 "sy_kernel_energy", "sy_device_energy", "sy_wave_energy", "sy_status_string", "sy_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = sy.lib().__dict__.get("_name") or sy.lib_path()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(sy_[a-z0-9_]+)", out))
+    missing = [n for n in declared_symbols() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    # and nothing C++ leaks: every exported symbol is a C name from the header
+    assert exported <= set(declared_symbols())
+
+
+def test_status_strings_and_version():
+    L = sy.lib()
+    assert sy.sy_abi_version() == 1
+    for code, name in sy.STATUS.items():
+        assert L.sy_status_string(code).decode() == name
+
+
+@pytest.mark.parametrize("n,k", [(8192, 4), (10, 3), (7, 7), (5, 1), (100, 9), (0, 1), (3, 5)])
+def test_split_rows_matches_oracle(n, k):
+    assert sy.sy_split_rows(n, k) == oracle.split_rows(n, k)
+
+
+def test_range_mappers_match_oracle():
+    for ny in (1, 6, 19):
+        for r in (0, 1, 2, 4):
+            for a in range(ny):
+                for b in range(a + 1, ny + 1):
+                    assert sy.sy_rm_neighbourhood((a, b), r, ny) == oracle.rm_neighbourhood(a, b, r, ny)
+                    assert sy.sy_rm_one_to_one((a, b)) == oracle.rm_one_to_one(a, b)
+
+
+@pytest.mark.parametrize("chunks,n", [([(0, 5), (6, 10)], 10), ([(0, 6), (5, 10)], 10), ([(0, 5), (5, 9)], 10),
+                                      ([(0, 0), (0, 10)], 10), ([(5, 10), (0, 5)], 10), ([(0, 1), (1, 10)], 10),
+                                      ([(0, 10)], 10), ([], 0)])
+def test_chunk_validation_matches_oracle(chunks, n):
+    ok = oracle.chunks_valid(n, chunks) if chunks else False
+    if ok:
+        sy.sy_chunks_validate(n, chunks)
+    else:
+        with pytest.raises(sy.SyError) as e:
+            sy.sy_chunks_validate(n, chunks)
+        assert e.value.name == "SY_ERR_BAD_CHUNKS"
+
+
+def test_errors_are_reported_not_raised_across_the_abi():
+    with pytest.raises(sy.SyError) as e:
+        sy.sy_split_rows(10, 0)
+    assert e.value.name == "SY_ERR_INVALID_ARGUMENT" and "chunks" in str(e.value)
+    L = sy.lib()
+    assert L.sy_split_rows(5, 2, None) == 2  # SY_ERR_NULL_POINTER
+    assert L.sy_saxpy(None, 4, C.c_float(1.0), None, None, None, None) == 2
+
+
+def test_no_oracle_in_the_product_library():
+    out = subprocess.run(["nm", "-D", sy.lib_path()], capture_output=True, text=True, check=True).stdout
+    assert "oracle" not in out
+    deps = subprocess.run(["ldd", sy.lib_path()], capture_output=True, text=True).stdout
+    assert "liboracle" not in deps

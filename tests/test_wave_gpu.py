@@ -1,0 +1,304 @@
+"""Leapfrog wave stencil on the GPU (row chunks with neighbourhood range mappers,
+paper §3) against the oracle.
+
+Bar: bit-exact against the precision mirror (same FP32 operation order, same
+storage rounding) for every radius, storage type, chunking, tile variant and
+layout; and, for FP32 at the 8192 x 8192 / 200-step workload, max|u - u64| /
+max|u64| <= 1e-5 against the FP64 oracle on light-cone samples."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2505_06022_gb300 as sy
+from paper_2505_06022_gb300 import inputs
+
+from gpu_helpers import bits, to_device, to_host, torch_cuda, wave_run
+
+pytestmark = pytest.mark.gpu
+
+DT = {"f32": oracle.F32, "bf16": oracle.BF16, "f16": oracle.F16}
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch_cuda()
+    with sy.Queue(0) as queue:
+        yield queue.handle
+
+
+def field(ny, nx, dtype, seed=1, smooth=True):
+    if smooth:
+        a = inputs.gaussian_pulse(ny, nx, max(2.0, min(ny, nx) / 6.0)) + 0.05 * inputs.random_field(seed, ny, nx)
+    else:
+        a = inputs.random_field(seed, ny, nx).astype(np.float64)
+    return inputs.to_storage(a, dtype)
+
+
+SHAPES = [(8, 8), (1, 1), (1, 200), (300, 1), (33, 131), (64, 128), (17, 257), (70, 1030), (129, 64)]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_bit_exact_vs_mirror(q, dtype, r, shape):
+    ny, nx = shape
+    u0 = field(ny, nx, dtype, seed=r)
+    steps = 7
+    chunks = sy.sy_split_rows(ny, min(3, ny))
+    gp, gc = wave_run(q, u0, steps, r, 0.25, dtype, chunks)
+    op, oc = oracle.wave_run_mirror(DT[dtype], u0, steps, r, 0.25)
+    assert np.array_equal(bits(gc), bits(oc)) and np.array_equal(bits(gp), bits(op))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_start_bit_exact(q, dtype, r):
+    torch = torch_cuda()
+    ny, nx = 45, 300
+    u0 = field(ny, nx, dtype, smooth=False)
+    d0 = to_device(u0)
+    dm1 = torch.empty_like(d0)
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype)
+    sy.sy_stencil_start(q, p, d0, dm1, [(0, ny)], r)
+    torch.cuda.synchronize()
+    want = oracle.wave_start_mirror(DT[dtype], u0, r, 0.25)
+    st = np.float32 if dtype == "f32" else np.uint16
+    assert np.array_equal(bits(to_host(dm1, None, st)), bits(want))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("r", [1, 4])
+def test_chunk_invariance(q, dtype, r):
+    # The paper's split across devices must not change results: any chunking, same bits.
+    ny, nx = 97, 520
+    u0 = field(ny, nx, dtype)
+    ref = None
+    for chunks in [[(0, ny)], sy.sy_split_rows(ny, 2), sy.sy_split_rows(ny, 4), sy.sy_split_rows(ny, 7),
+                   [(0, 1), (1, 2), (2, 50), (50, 96), (96, 97)], [(i, i + 1) for i in range(ny)]]:
+        _, c = wave_run(q, u0, 9, r, 0.25, dtype, chunks)
+        if ref is None:
+            ref = c
+        assert np.array_equal(bits(c), bits(ref))
+    _, oc = oracle.wave_run_mirror(DT[dtype], u0, 9, r, 0.25)
+    assert np.array_equal(bits(ref), bits(oc))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_every_variant_identical(q, dtype, r):
+    ny, nx = 75, 700
+    u0 = field(ny, nx, dtype)
+    _, oc = oracle.wave_run_mirror(DT[dtype], u0, 5, r, 0.25)
+    for v in range(0, sy.sy_stencil_variant_count(r, DT[dtype]) + 1):
+        _, c = wave_run(q, u0, 5, r, 0.25, dtype, sy.sy_split_rows(ny, 4), variant=v)
+        assert np.array_equal(bits(c), bits(oc)), f"variant {v}"
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("pitch_extra", [4, 8, 3, 1])
+def test_padded_and_unaligned_pitch(q, dtype, pitch_extra):
+    # pitch_extra 4/8 keeps rows 16-byte aligned (vector kernel); 1/3 forces the scalar kernel.
+    # Padding holds NaN: it must be neither read as data nor written.
+    torch = torch_cuda()
+    ny, nx, r = 40, 250, 2
+    pitch = nx + pitch_extra
+    u0 = field(ny, nx, dtype)
+    st = np.float32 if dtype == "f32" else np.uint16
+    fill = float("nan") if dtype == "f32" else -1
+    cur = to_device(u0, pitch, fill=fill)
+    prev = torch.empty_like(cur)
+    prev.copy_(cur)
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype, pitch=pitch)
+    sy.sy_stencil_start(q, p, cur, prev, [(0, 13), (13, ny)], r)
+    for _ in range(6):
+        sy.sy_stencil_step(q, p, prev, cur, prev, [(0, 13), (13, ny)], r)
+        prev, cur = cur, prev
+    torch.cuda.synchronize()
+    full = to_host(cur, None, st)
+    _, oc = oracle.wave_run_mirror(DT[dtype], u0, 6, r, 0.25)
+    assert np.array_equal(bits(np.ascontiguousarray(full[:, :nx])), bits(oc))
+    pad = full[:, nx:]
+    assert (np.isnan(pad).all() if dtype == "f32" else (pad.view(np.int16) == -1).all())
+
+
+def test_unaligned_base_pointer_uses_scalar_path(q):
+    torch = torch_cuda()
+    ny, nx, r = 21, 64, 1
+    u0 = field(ny, nx, "f32")
+    big = torch.zeros(3 * (ny * nx + 4), device="cuda")
+    a = big[1: 1 + ny * nx]
+    b = big[ny * nx + 6: 2 * ny * nx + 6]
+    a.copy_(torch.from_numpy(u0.reshape(-1)))
+    p = sy.stencil_params(ny, nx, r, 0.25, "f32")
+    sy.sy_stencil_start(q, p, a, b, [(0, ny)], r)
+    sy.sy_stencil_step(q, p, b, a, b, [(0, ny)], r)
+    torch.cuda.synchronize()
+    op, oc = oracle.wave_run_mirror(oracle.F32, u0, 1, r, 0.25)
+    assert np.array_equal(b.cpu().numpy().reshape(ny, nx).view(np.uint32), oc.view(np.uint32))
+
+
+def test_out_of_place_equals_in_place(q):
+    torch = torch_cuda()
+    ny, nx, r = 50, 333, 3
+    u0 = field(ny, nx, "f32")
+    cur = to_device(u0)
+    prev = torch.empty_like(cur)
+    p = sy.stencil_params(ny, nx, r, 0.25, "f32")
+    sy.sy_stencil_start(q, p, cur, prev, [(0, ny)], r)
+    nxt = torch.empty_like(cur)
+    sy.sy_stencil_step(q, p, prev, cur, nxt, [(0, ny)], r)
+    sy.sy_stencil_step(q, p, prev, cur, prev, [(0, ny)], r)
+    torch.cuda.synchronize()
+    assert torch.equal(nxt.view(torch.int32), prev.view(torch.int32))
+
+
+def test_f32_close_to_f64_small(q):
+    ny, nx = 256, 256
+    u64 = inputs.gaussian_pulse(ny, nx, 16.0)
+    u0 = inputs.to_storage(u64, "f32")
+    _, gc = wave_run(q, u0, 200, 1, 0.25, "f32", sy.sy_split_rows(ny, 4))
+    _, c64 = oracle.wave_run_f64(u0.astype(np.float64), 200, 1, 0.25)
+    assert np.max(np.abs(gc - c64)) / np.max(np.abs(c64)) <= 1e-5
+
+
+def test_standing_mode_closed_form_small(q):
+    ny, nx, mx, my, steps = 120, 200, 16, 32, 200
+    u0 = inputs.to_storage(inputs.sine_mode(ny, nx, mx, my), "f32")
+    _, gc = wave_run(q, u0, steps, 1, 0.25, "f32", sy.sy_split_rows(ny, 4))
+    ty, tx = math.pi * my / (ny + 1), math.pi * mx / (nx + 1)
+    om = math.acos(1 - 2 * 0.25 * (math.sin(tx / 2) ** 2 + math.sin(ty / 2) ** 2))
+    want = math.cos(steps * om) * inputs.sine_mode(ny, nx, mx, my)
+    assert np.max(np.abs(gc - want)) <= 1e-5
+
+
+def test_errors(q):
+    torch = torch_cuda()
+    ny, nx = 16, 64
+    a = torch.zeros(ny, nx, device="cuda")
+    b = torch.zeros(ny, nx, device="cuda")
+    c = torch.zeros(ny, nx, device="cuda")
+    p = sy.stencil_params(ny, nx, 2, 0.25, "f32")
+    cases = [
+        (dict(chunks=[(0, 8), (9, 16)], halo=2), "SY_ERR_BAD_CHUNKS"),
+        (dict(chunks=[(0, 16)], halo=1), "SY_ERR_HALO_TOO_SMALL"),
+        (dict(chunks=[(0, 16)], halo=2, nxt=b), "SY_ERR_ALIAS"),
+        (dict(chunks=[(0, 16)], halo=2, nxt=a.view(-1)[1:]), "SY_ERR_ALIAS"),
+    ]
+    before = sy.sy_queue_launch_count(q)
+    for kw, name in cases:
+        with pytest.raises(sy.SyError) as e:
+            sy.sy_stencil_step(q, p, a, b, kw.get("nxt", c), kw["chunks"], kw["halo"])
+        assert e.value.name == name
+    for bad in [sy.stencil_params(ny, nx, 5, 0.25, "f32"), sy.stencil_params(ny, nx, 1, 0.25, 9),
+                sy.stencil_params(ny, nx, 1, 0.25, "f32", pitch=nx - 1),
+                sy.stencil_params(ny, nx, 1, 0.25, "f32", variant=99)]:
+        with pytest.raises(sy.SyError) as e:
+            sy.sy_stencil_step(q, bad, a, b, c, [(0, ny)], 4)
+        assert e.value.name == "SY_ERR_INVALID_ARGUMENT"
+    assert sy.sy_queue_launch_count(q) == before
+    # an empty grid is a no-op with an empty chunk list
+    sy.sy_stencil_step(q, sy.stencil_params(0, 0, 1, 0.25, "f32"), a, b, c, [], 1)
+
+
+# ---- discrete energy (FP64 reduction on the GPU) --------------------------------
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_energy_matches_oracle(q, dtype, r):
+    ny, nx = 77, 301
+    u_new = field(ny, nx, dtype, seed=3, smooth=False)
+    u_old = field(ny, nx, dtype, seed=4, smooth=False)
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype)
+    E, kin, pot = sy.sy_wave_energy(q, p, to_device(u_new), to_device(u_old))
+    code = DT[dtype]
+    want = oracle.wave_energy_f64(oracle.storage_to_f64(u_new, code), oracle.storage_to_f64(u_old, code), r, 0.25)
+    # Same FP64 terms, different summation order: |difference| <= 2 * N * eps * sum|terms|
+    # (standard bound for two orders of a sum of N terms); in practice ~1e-15.
+    tol = 2 * ny * nx * 2.0 ** -53 * want["abs_sum"]
+    assert abs(E - want["E"]) <= tol and abs(kin - want["kin"]) <= tol and abs(pot - want["pot"]) <= 8 * tol
+    # fixed reduction shape: identical bits on a repeat call
+    assert sy.sy_wave_energy(q, p, to_device(u_new), to_device(u_old)) == (E, kin, pot)
+
+
+def test_energy_conserved_by_gpu_steps(q):
+    torch = torch_cuda()
+    # r = 1: the FP32 weights are exact, so only rounding of the field can drift E.
+    ny, nx, r = 256, 384, 1
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 12.0), "f32")
+    cur = to_device(u0)
+    prev = torch.empty_like(cur)
+    p = sy.stencil_params(ny, nx, r, 0.25, "f32")
+    chunks = sy.sy_split_rows(ny, 4)
+    sy.sy_stencil_start(q, p, cur, prev, chunks, r)
+    E0 = sy.sy_wave_energy(q, p, cur, prev)[0]
+    for _ in range(200):
+        sy.sy_stencil_step(q, p, prev, cur, prev, chunks, r)
+        prev, cur = cur, prev
+    E1 = sy.sy_wave_energy(q, p, cur, prev)[0]
+    assert E0 > 0 and abs(E1 - E0) / E0 < 1e-3  # FP32 storage: drift from rounding only
+
+
+# ---- the 8192 x 8192, 200-step, 4-chunk FP32 workload at full size ------------------
+
+def light_cone_box(p, shape, steps, r):
+    """Clipped box around p holding every point u^steps(p) depends on (start step included)."""
+    h = (steps + 1) * r + 1
+    (pi, pj), (ny, nx) = p, shape
+    return max(0, pi - h), min(ny, pi + h + 1), max(0, pj - h), min(nx, pj + h + 1)
+
+
+FULL_SAMPLES = [(0, 0), (0, 8191), (8191, 0), (8191, 8191), (0, 4096), (4096, 0), (8191, 4096), (4096, 8191),
+                (2047, 4096), (2048, 4096), (6143, 4100), (6144, 4100), (4095, 4096), (4096, 4096),
+                (4096, 4196), (4026, 4166), (4096, 3995), (4200, 4001), (4096, 127), (4096, 128),
+                (1000, 7000), (7777, 1234)]
+
+
+def test_config1_full_size_sampled(q):
+    ny = nx = 8192
+    steps, r = 200, 1
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 64.0), "f32")
+    gp, gc = wave_run(q, u0, steps, r, 0.25, "f32", sy.sy_split_rows(ny, 4))
+    scale = float(np.max(np.abs(gc)))
+    assert scale > 0.05
+    worst = 0.0
+    for pt in FULL_SAMPLES:
+        y0, y1, x0, x1 = light_cone_box(pt, (ny, nx), steps, r)
+        sub = np.ascontiguousarray(u0[y0:y1, x0:x1])
+        _, m32 = oracle.wave_run_mirror(oracle.F32, sub, steps, r, 0.25)
+        _, m64 = oracle.wave_run_f64(sub.astype(np.float64), steps, r, 0.25)
+        i, j = pt[0] - y0, pt[1] - x0
+        assert gc[pt].view(np.uint32) == m32[i, j].view(np.uint32), pt
+        worst = max(worst, abs(float(gc[pt]) - m64[i, j]) / scale)
+    assert worst <= 1e-5
+
+
+def test_config1_mode_closed_form_full_size(q):
+    # single sin(kx x) sin(ky y) mode on the full grid: u^n = cos(n Omega) u^0 everywhere
+    ny = nx = 8192
+    mx, my, steps = 16, 32, 200
+    mode = inputs.sine_mode(ny, nx, mx, my)
+    u0 = inputs.to_storage(mode, "f32")
+    _, gc = wave_run(q, u0, steps, 1, 0.25, "f32", sy.sy_split_rows(ny, 4))
+    ty, tx = math.pi * my / (ny + 1), math.pi * mx / (nx + 1)
+    om = math.acos(1 - 2 * 0.25 * (math.sin(tx / 2) ** 2 + math.sin(ty / 2) ** 2))
+    err = np.max(np.abs(gc - math.cos(steps * om) * mode))
+    assert err <= 1e-5
+
+
+def test_config1_energy_drift_full_size(q):
+    torch = torch_cuda()
+    ny = nx = 8192
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 64.0), "f32")
+    cur = to_device(u0)
+    prev = torch.empty_like(cur)
+    p = sy.stencil_params(ny, nx, 1, 0.25, "f32")
+    chunks = sy.sy_split_rows(ny, 4)
+    sy.sy_stencil_start(q, p, cur, prev, chunks, 1)
+    E0 = sy.sy_wave_energy(q, p, cur, prev)[0]
+    for _ in range(200):
+        sy.sy_stencil_step(q, p, prev, cur, prev, chunks, 1)
+        prev, cur = cur, prev
+    E1 = sy.sy_wave_energy(q, p, cur, prev)[0]
+    assert E0 > 0 and abs(E1 - E0) / E0 < 1e-3
