@@ -1,11 +1,11 @@
 #!/usr/bin/env python3
 """Benchmark of the hot path: the 2D leapfrog wave stencil, FP32, 8192 x 8192,
 200 steps, split into 4 row chunks with a radius-1 neighbourhood halo, every
-chunk launch timed by its own event pair (and energy-attributed).
+chunk launch timed by device-side timestamps and energy-attributed (NVML).
 
 One bench "step" = one whole simulation: the Taylor start plus 200 leapfrog
-steps over the 4 chunks (804 kernel launches), from the initial field already
-resident in HBM.  Units: grid-point updates (200 * 8192^2 per step).
+steps over the 4 chunks (804 kernel launches, one sy_wave_run call replaying its
+CUDA graph), from the initial field already resident in HBM.  Units: grid-point updates (200 * 8192^2 per step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sy|reference]
 
@@ -119,7 +119,7 @@ class ClockSampler:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for name in ("wave_kernel.cuh", "wave.cu", "wave_f32.cu"):
+    for name in ("wave_kernel.cuh", "wave.cu", "wave_f32.cu", "stamp.cuh"):
         with open(os.path.join(ROOT, "paper_2505_06022_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -222,29 +222,13 @@ def run_gpu(args) -> None:
     u0 = torch.from_numpy(u0_host).cuda()  # resident initial field (never overwritten)
     A = torch.empty_like(u0)
     B = torch.empty_like(u0)
-    events: list[int] = []
 
     def simulate(u_init, collect: bool):
-        """Start + STEPS leapfrog steps from u_init (read only); returns (prev, cur)."""
-        evs = sy.sy_stencil_start(q.handle, p, u_init, A, chunks, HALO, want_events=collect)
-        # step 1: u^1 into A (u_prev = A = u^{-1}, in place)
-        e = sy.sy_stencil_step(q.handle, p, A, u_init, A, chunks, HALO, want_events=collect)
-        if collect:
-            events.extend(e)
-        # step 2: u^2 into B (out of place, keeps u_init pristine)
-        e = sy.sy_stencil_step(q.handle, p, u_init, A, B, chunks, HALO, want_events=collect)
-        if collect:
-            events.extend(e)
-        prev, cur = A, B
-        for _ in range(STEPS - 2):
-            e = sy.sy_stencil_step(q.handle, p, prev, cur, prev, chunks, HALO, want_events=collect)
-            if collect:
-                events.extend(e)
-            prev, cur = cur, prev
-        return prev, cur
+        """Start + STEPS chunked leapfrog steps from u_init (read only), one graph replay."""
+        return sy.sy_wave_run(q.handle, p, u_init, A, B, STEPS, chunks, HALO, want_events=collect)
 
     for _ in range(args.warmup):
-        simulate(u0, False)
+        simulate(u0, True)
     torch.cuda.synchronize()
 
     # ---- timed region: K whole simulations, device-timed on the launching stream ----
@@ -263,8 +247,9 @@ def run_gpu(args) -> None:
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
+    events = []
     for _ in range(args.steps):
-        simulate(u0, True)
+        _, _, events = simulate(u0, True)  # per-chunk ids of the latest run
     t_end.record(stream)
     torch.cuda.synchronize()
     joules = seconds = None
@@ -286,25 +271,32 @@ def run_gpu(args) -> None:
     updates_per_step = STEPS * NY * NX
     value = world * args.steps * updates_per_step / (ms_total * 1e-3)
 
-    # roofline of the dominant kernel: every leapfrog chunk launch, event-timed
-    durs = [sy.sy_event_elapsed(q.handle, e) for e in events]
-    avg_ms = statistics.mean(durs)
-    rows_per_chunk = NY // CHUNKS
-    alg_bytes = BYTES_PER_UPDATE * rows_per_chunk * NX
+    # Roofline of the dominant kernel (the chunked leapfrog step, 800 of the 804
+    # launches of a step): algorithmic bytes per launch / average launch duration,
+    # both over the CUDA-event-timed region.  The start's 4 launches move 8 B/point.
+    bytes_per_sim = 8 * NY * NX + STEPS * BYTES_PER_UPDATE * NY * NX
+    launches_per_sim = (STEPS + 1) * CHUNKS
+    avg_ms = ms_total / (args.steps * launches_per_sim)
+    alg_bytes = bytes_per_sim / launches_per_sim
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    # kernel-only view from the per-chunk device timestamps of the last run
+    stamp_ms = sy.sy_events_elapsed(q.handle, events)[CHUNKS:]
+    chunk_bytes = BYTES_PER_UPDATE * (NY // CHUNKS) * NX
     peaks = measured_peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(),
-                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "wave_vec_kernel<float,1,RY,false> (one chunk of 2048x8192)",
-                "avg_launch_ms": avg_ms, "launches_timed": len(durs),
-                "frac_of_nominal_8000": achieved / 8000.0}
+                "kernel": "wave_vec_kernel<float,1,4,false>, one 2048x8192 chunk per launch",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
+                "frac_of_nominal_8000": achieved / 8000.0,
+                "stamp_avg_chunk_ms": statistics.mean(stamp_ms),
+                "stamp_chunk_gbs": chunk_bytes / (statistics.mean(stamp_ms) * 1e-3) / 1e9}
     energy = None
     if have_energy and joules is not None and joules > 0:
-        kern_j = [sy.sy_kernel_energy(q.handle, e) for e in events[: 4 * CHUNKS]]
+        kern_j = [sy.sy_kernel_energy(q.handle, e) for e in events[CHUNKS:]]
         energy = {"joules": joules, "window_s": seconds, "j_per_update": joules / (args.steps * updates_per_step),
-                  "avg_power_w": joules / seconds, "chunk_kernel_j": statistics.mean(kern_j)}
+                  "avg_power_w": joules / seconds, "chunk_kernel_j_mean": statistics.mean(kern_j)}
 
     # ---- e2e: host (pinned) initial field in, final field out, through the same API ----
     e2e = None
@@ -312,10 +304,11 @@ def run_gpu(args) -> None:
         h_in = torch.from_numpy(u0_host).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         d_in = torch.empty_like(u0)
-        for _ in range(1):
+        byptr = {A.data_ptr(): A, B.data_ptr(): B, d_in.data_ptr(): d_in}
+        for _ in range(2):
             d_in.copy_(h_in, non_blocking=True)
-            _, cur = simulate(d_in, False)
-            h_out.copy_(cur, non_blocking=True)
+            _, cv, _ = simulate(d_in, False)
+            h_out.copy_(byptr[cv], non_blocking=True)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -323,8 +316,8 @@ def run_gpu(args) -> None:
         k_e2e = max(1, min(args.steps, 5))
         for _ in range(k_e2e):
             d_in.copy_(h_in, non_blocking=True)
-            _, cur = simulate(d_in, False)
-            h_out.copy_(cur, non_blocking=True)
+            pv, cv, _ = simulate(d_in, False)
+            h_out.copy_(byptr[cv], non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1)
@@ -332,7 +325,7 @@ def run_gpu(args) -> None:
                "h2d_bytes_per_step": h_in.numel() * 4, "d2h_bytes_per_step": h_out.numel() * 4,
                "ms_per_step": ms_e2e / k_e2e}
         # the result must be the physics, not garbage: energy of the final state is finite
-        E = sy.sy_wave_energy(q.handle, p, cur, A if cur is B else B)[0]
+        E = sy.sy_wave_energy(q.handle, p, byptr[cv], byptr[pv])[0]
         assert np.isfinite(E) and E > 0
 
     if dist:

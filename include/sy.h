@@ -85,9 +85,13 @@ int sy_abi_version(void);
 /* Queue (paper §2, Listing 1: `queue q(gpu_selector)`)                       */
 /* ------------------------------------------------------------------------- */
 
+/* Borrow the legacy default stream (the runtime's cudaStreamLegacy handle); the
+ * stream handle 0 cannot be used for this because NULL requests an owned stream. */
+#define SY_STREAM_LEGACY ((void*)0x1)
+
 /* Create a queue on CUDA device `device`.  `cuda_stream` is a cudaStream_t to
- * borrow (never destroyed by the library), or NULL to create an owned
- * non-blocking stream.  The queue remembers the device energy counter at
+ * borrow (never destroyed by the library), SY_STREAM_LEGACY for the legacy
+ * default stream, or NULL to create an owned non-blocking stream.  The queue remembers the device energy counter at
  * creation (for sy_device_energy) when NVML is available. */
 sy_status sy_queue_create(int device, void* cuda_stream, sy_queue_t* out);
 sy_status sy_queue_destroy(sy_queue_t q);
@@ -102,9 +106,15 @@ sy_status sy_queue_launch_count(sy_queue_t q, uint64_t* launches);
 /* Events: per-kernel time and energy (paper §4, Listing 3)                   */
 /* ------------------------------------------------------------------------- */
 
-/* Device time of an event's kernel in milliseconds (CUDA events around the
- * launch).  Returns SY_ERR_NOT_READY if the kernel has not completed. */
+/* Device time of an event's launch in milliseconds: from the first block's start
+ * to the last block's end, read from %globaltimer stamps the kernels themselves
+ * write (no operation is added to the stream, so timing does not slow the
+ * launches down).  Returns SY_ERR_NOT_READY if the launch has not completed. */
 sy_status sy_event_elapsed(sy_queue_t q, sy_event ev, double* ms);
+
+/* Device times of n events at once (one copy of the timestamp ring); ms receives
+ * n values.  Fails with SY_ERR_NOT_READY if any of them has not completed. */
+sy_status sy_events_elapsed(sy_queue_t q, const sy_event* events, int n, double* ms);
 
 /* Raw NVML total-energy counter of the queue's device, in millijoules
  * (nvmlDeviceGetTotalEnergyConsumption).  SY_ERR_NVML_UNAVAILABLE if NVML cannot
@@ -215,6 +225,20 @@ sy_status sy_stencil_step(sy_queue_t q, const sy_stencil_params* p, const void* 
  * as sy_stencil_step. */
 sy_status sy_stencil_start(sy_queue_t q, const sy_stencil_params* p, const void* u0, void* u_m1,
                            const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* chunk_events);
+
+/* A whole simulation in one call: the Taylor start from u0, then `steps` leapfrog
+ * steps, each split into the chunks as in sy_stencil_step.  The launches are
+ * captured into a CUDA graph on the first call and the graph is replayed by later
+ * calls with identical arguments (one cached graph per queue; changing any
+ * argument re-captures).  u0 (device, read) is never written; u_a and u_b
+ * (device) are work fields that receive the results: on return *prev_out and
+ * *cur_out (nullable) name the buffers (u0, u_a or u_b) holding u^{steps-1} and
+ * u^{steps}.  u0, u_a, u_b must not overlap.  events (nullable) receives
+ * (steps + 1) * n_chunks ids -- the start's chunks, then each step's -- valid until
+ * the next sy_wave_run on this queue (at most 16384 per run; pass NULL beyond). */
+sy_status sy_wave_run(sy_queue_t q, const sy_stencil_params* p, const void* u0, void* u_a, void* u_b, int64_t steps,
+                      const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* events, const void** prev_out,
+                      const void** cur_out);
 
 /* Number of tile variants for a (radius, dtype); variant ids are 1..count
  * (0 always means the default).  tile_rows / tile_cols / threads (nullable)

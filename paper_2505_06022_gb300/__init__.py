@@ -23,6 +23,7 @@ __all__ = [
 ]
 
 SY_F32, SY_BF16, SY_F16 = 0, 1, 2
+SY_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 DTYPE_CODES = {"f32": SY_F32, "bf16": SY_BF16, "f16": SY_F16}
 
 STATUS = {
@@ -67,6 +68,7 @@ _SIGS = {
     "sy_queue_stream": [_p, _p],
     "sy_queue_launch_count": [_p, _p],
     "sy_event_elapsed": [_p, _u64, _p],
+    "sy_events_elapsed": [_p, _p, C.c_int, _p],
     "sy_energy_read": [_p, _p],
     "sy_device_energy": [_p, _p],
     "sy_meter_begin": [_p],
@@ -83,6 +85,7 @@ _SIGS = {
     "sy_stencil_variant_count": [C.c_int, C.c_int, _p],
     "sy_stencil_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p, _p],
     "sy_wave_energy": [_p, _p, _p, _p, _p, _p, _p],
+    "sy_wave_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
 }
 _RESTYPE = {"sy_status_string": C.c_char_p, "sy_last_error": C.c_char_p, "sy_abi_version": C.c_int}
 
@@ -176,6 +179,14 @@ def sy_event_elapsed(q: int, ev: int) -> float:
     return ms.value
 
 
+def sy_events_elapsed(q: int, events) -> list[float]:
+    evs = list(events)
+    arr = (C.c_uint64 * max(1, len(evs)))(*evs)
+    ms = (C.c_double * max(1, len(evs)))()
+    _call("sy_events_elapsed", q, arr, len(evs), ms)
+    return list(ms[: len(evs)])
+
+
 def sy_energy_read(q: int) -> int:
     mj = C.c_uint64()
     _call("sy_energy_read", q, C.byref(mj))
@@ -264,6 +275,20 @@ def sy_stencil_start(q: int, p: StencilParams, u0, u_m1, chunks, halo_radius: in
     return list(evs[:k]) if want_events else []
 
 
+def sy_wave_run(q: int, p: StencilParams, u0, u_a, u_b, steps: int, chunks, halo_radius: int,
+                want_events: bool = False):
+    """Start + `steps` chunked leapfrog steps (graph-captured, cached).  Returns
+    (prev_ptr, cur_ptr, events): the device addresses holding u^{steps-1} and
+    u^{steps} (each equal to one of u0, u_a, u_b) and the per-chunk event ids."""
+    arr, k = _chunks(chunks)
+    n_ev = (steps + 1) * k
+    evs = (C.c_uint64 * max(1, n_ev))() if want_events else None
+    pv, cv = C.c_void_p(), C.c_void_p()
+    _call("sy_wave_run", q, C.byref(p), _ptr(u0), _ptr(u_a), _ptr(u_b), steps, arr, k, halo_radius, evs,
+          C.byref(pv), C.byref(cv))
+    return pv.value, cv.value, (list(evs[:n_ev]) if want_events else [])
+
+
 def sy_stencil_variant_count(radius: int, dtype: int) -> int:
     n = C.c_int()
     _call("sy_stencil_variant_count", radius, dtype, C.byref(n))
@@ -296,7 +321,9 @@ class Queue:
         if stream is None:
             stream = torch.cuda.current_stream(device)
         raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        self.handle = sy_queue_create(device, raw or None)
+        # torch reports its default (legacy) stream as handle 0; NULL would ask the
+        # library for a private stream, so name the legacy stream explicitly.
+        self.handle = sy_queue_create(device, raw if raw else SY_STREAM_LEGACY)
         self.device = device
 
     def close(self) -> None:

@@ -142,25 +142,45 @@ sy_status queue_scratch(Queue* q, size_t bytes, void** out) {
 
 sy_status begin_event(Queue* q, sy_event* want, EventRecord** rec) {
     *rec = nullptr;
+    q->cur_stamp = nullptr;
+    q->cur_blocks = 0;
     if (!want) return SY_OK;
+    uint32_t slot;
+    if (q->capturing) {
+        if (q->next_graph_slot >= kGraphStampSlots)
+            return fail(SY_ERR_INVALID_ARGUMENT, "more than %u timed launches in one captured run", kGraphStampSlots);
+        slot = kStreamStampSlots + q->next_graph_slot++;
+        q->capture_expected.push_back(0);
+        q->cur_stamp = q->d_stamps + 4ull * slot;
+        *want = 0;  // ids are issued per replay
+        return SY_OK;
+    }
+    slot = q->next_stream_slot;
+    q->next_stream_slot = (q->next_stream_slot + 1) % kStreamStampSlots;
     std::lock_guard<std::mutex> lock(q->mu);
+    if (slot % kStampPage == 0) {  // zero the page this slot opens, ahead of its launches
+        SY_CUDA(cudaMemsetAsync(q->d_stamps + 4ull * slot, 0, 4ull * kStampPage * sizeof(unsigned long long),
+                                q->launch));
+        for (uint32_t i = slot; i < slot + kStampPage; ++i) q->slot_owner[i] = 0;
+    }
     uint64_t id = q->next_event++;
     EventRecord& r = q->ring[id % kEventRing];
-    if (!r.start) {
-        SY_CUDA(cudaEventCreate(&r.start));
-        SY_CUDA(cudaEventCreate(&r.stop));
-    }
     r.id = id;
+    r.slot = slot;
+    r.expected = 0;
     r.window = q->open_window;
-    SY_CUDA(cudaEventRecord(r.start, q->stream));
+    q->slot_owner[slot] = id;
+    q->cur_stamp = q->d_stamps + 4ull * slot;
     *want = id;
     *rec = &r;
     return SY_OK;
 }
 
 sy_status end_event(Queue* q, EventRecord* rec) {
-    if (!rec) return SY_OK;
-    SY_CUDA(cudaEventRecord(rec->stop, q->stream));
+    if (q->capturing && q->cur_stamp) q->capture_expected.back() = q->cur_blocks;
+    if (rec) rec->expected = q->cur_blocks;
+    q->cur_stamp = nullptr;
+    q->cur_blocks = 0;
     return SY_OK;
 }
 
@@ -169,8 +189,32 @@ static sy_status find_event(Queue* q, sy_event ev, EventRecord** out) {
         return fail(SY_ERR_INVALID_ARGUMENT, "event %llu is not a live event of this queue",
                     static_cast<unsigned long long>(ev));
     EventRecord& r = q->ring[ev % kEventRing];
-    if (r.id != ev) return fail(SY_ERR_INVALID_ARGUMENT, "event %llu was recycled", (unsigned long long)ev);
+    if (r.id != ev || q->slot_owner[r.slot] != ev)
+        return fail(SY_ERR_INVALID_ARGUMENT, "event %llu was recycled", (unsigned long long)ev);
     *out = &r;
+    return SY_OK;
+}
+
+// Copy stamp slots [lo, hi) to the host (a snapshot: launches may still run).
+static sy_status read_stamps(Queue* q, uint32_t lo, uint32_t hi, std::vector<unsigned long long>* out) {
+    out->assign(4ull * (hi - lo), 0ull);
+    if (hi <= lo) return SY_OK;
+    SY_CUDA(cudaMemcpyAsync(out->data(), q->d_stamps + 4ull * lo, out->size() * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, q->aux));
+    SY_CUDA(cudaStreamSynchronize(q->aux));
+    return SY_OK;
+}
+
+static sy_status stamp_ms(const EventRecord& r, const unsigned long long* slot, double* ms) {
+    if (r.expected == 0) {  // nothing launched (e.g. an empty range): zero time
+        *ms = 0.0;
+        return SY_OK;
+    }
+    if (slot[2] != r.expected)
+        return fail(SY_ERR_NOT_READY, "event %llu: %llu of %llu blocks finished", (unsigned long long)r.id,
+                    slot[2], (unsigned long long)r.expected);
+    unsigned long long start = ~slot[0], end = slot[1];
+    *ms = end > start ? static_cast<double>(end - start) * 1e-6 : 0.0;
     return SY_OK;
 }
 
@@ -214,6 +258,60 @@ size_t dtype_size(int dtype) {
 
 using namespace sy;
 
+// ---- stencil argument checks and chunked launches (shared by step/start/run) ----
+sy_status sy::stencil_param_checks(const sy_stencil_params* p) {
+    if (!p) return fail(SY_ERR_NULL_POINTER, "params is NULL");
+    if (p->ny < 0 || p->nx < 0) return fail(SY_ERR_INVALID_ARGUMENT, "negative grid size");
+    if (p->pitch < p->nx) return fail(SY_ERR_INVALID_ARGUMENT, "pitch %lld < nx %lld", (long long)p->pitch,
+                                      (long long)p->nx);
+    if (p->radius < 1 || p->radius > 4) return fail(SY_ERR_INVALID_ARGUMENT, "radius %d not in 1..4", p->radius);
+    if (dtype_size(p->dtype) == 0) return fail(SY_ERR_INVALID_ARGUMENT, "unknown dtype %d", p->dtype);
+    if (p->variant < 0 || p->variant > wave_variant_count(p->radius, p->dtype))
+        return fail(SY_ERR_INVALID_ARGUMENT, "variant %d not in 0..%d", p->variant,
+                    wave_variant_count(p->radius, p->dtype));
+    return SY_OK;
+}
+
+sy_status sy::stencil_common(Queue* q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
+                                void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                                sy_event* chunk_events, bool start) {
+    SY_TRY(stencil_param_checks(p));
+    if (p->ny == 0 || p->nx == 0) {
+        if (n_chunks == 0) return SY_OK;
+    }
+    SY_TRY(validate_chunks(p->ny, chunks, n_chunks));
+    if (halo_radius < p->radius)
+        return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
+    if (!u_cur || !u_next || (!start && !u_prev)) return fail(SY_ERR_NULL_POINTER, "field pointer is NULL");
+    size_t bytes = static_cast<size_t>(p->ny) * static_cast<size_t>(p->pitch) * dtype_size(p->dtype);
+    if (ranges_overlap(u_next, bytes, u_cur, bytes)) return fail(SY_ERR_ALIAS, "u_next overlaps u_cur");
+    if (!start && u_next != u_prev && ranges_overlap(u_next, bytes, u_prev, bytes))
+        return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
+    SY_TRY(use_device(q));
+    for (int c = 0; c < n_chunks; ++c) {
+        EventRecord* rec;
+        SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
+        WaveLaunch w;
+        w.ny = p->ny;
+        w.nx = p->nx;
+        w.pitch = p->pitch;
+        w.radius = p->radius;
+        w.dtype = p->dtype;
+        w.variant = p->variant;
+        w.c2 = start ? 0.5f * p->c2 : p->c2;
+        w.start = start;
+        w.u_prev = start ? u_cur : u_prev;
+        w.u_cur = u_cur;
+        w.u_next = u_next;
+        w.row_begin = chunks[c].begin;
+        w.row_end = chunks[c].end;
+        SY_TRY(launch_wave(q, w));
+        SY_TRY(end_event(q, rec));
+    }
+    return SY_OK;
+}
+
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -254,6 +352,7 @@ sy_status sy_queue_create(int device, void* cuda_stream, sy_queue_t* out) {
     if (!q) return fail(SY_ERR_OUT_OF_MEMORY, "queue allocation failed");
     q->device = device;
     q->ring.resize(kEventRing);
+    q->slot_owner.assign(kStampSlots, 0);
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&q->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) {
@@ -264,10 +363,17 @@ sy_status sy_queue_create(int device, void* cuda_stream, sy_queue_t* out) {
             q->owned = (e == cudaSuccess);
         }
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&q->d_stamps, 4ull * kStampSlots * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(q->d_stamps, 0, 4ull * kStampSlots * sizeof(unsigned long long));
     if (e != cudaSuccess) {
+        if (q->d_stamps) cudaFree(q->d_stamps);
+        if (q->aux) cudaStreamDestroy(q->aux);
+        if (q->owned) cudaStreamDestroy(q->stream);
         delete q;
         return cuda_fail(e, "sy_queue_create");
     }
+    q->launch = q->stream;
     nvml::device_t d = nullptr;
     if (nvml::device_for(device, &d)) {
         q->nvml_device = d;
@@ -282,11 +388,10 @@ sy_status sy_queue_destroy(sy_queue_t qh) {
     Queue* q = as_queue(qh);
     cudaSetDevice(q->device);
     cudaStreamSynchronize(q->stream);
-    for (auto& r : q->ring) {
-        if (r.start) cudaEventDestroy(r.start);
-        if (r.stop) cudaEventDestroy(r.stop);
-    }
+    if (q->run.exec) cudaGraphExecDestroy(q->run.exec);
     if (q->scratch) cudaFree(q->scratch);
+    if (q->d_stamps) cudaFree(q->d_stamps);
+    if (q->aux) cudaStreamDestroy(q->aux);
     if (q->owned) cudaStreamDestroy(q->stream);
     delete q;
     return SY_OK;
@@ -324,12 +429,23 @@ sy_status sy_event_elapsed(sy_queue_t qh, sy_event ev, double* ms) {
     EventRecord* r;
     SY_TRY(find_event(q, ev, &r));
     SY_TRY(use_device(q));
-    cudaError_t e = cudaEventQuery(r->stop);
-    if (e == cudaErrorNotReady) return fail(SY_ERR_NOT_READY, "event %llu not complete", (unsigned long long)ev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventQuery");
-    float f = 0.f;
-    SY_CUDA(cudaEventElapsedTime(&f, r->start, r->stop));
-    *ms = f;
+    std::vector<unsigned long long> st;
+    SY_TRY(read_stamps(q, r->slot, r->slot + 1, &st));
+    return stamp_ms(*r, st.data(), ms);
+}
+
+sy_status sy_events_elapsed(sy_queue_t qh, const sy_event* evs, int n, double* ms) {
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    if (n < 0) return fail(SY_ERR_INVALID_ARGUMENT, "n = %d < 0", n);
+    if (n == 0) return SY_OK;
+    if (!evs || !ms) return fail(SY_ERR_NULL_POINTER, "events or ms is NULL");
+    SY_TRY(use_device(q));
+    std::vector<EventRecord*> recs(n);
+    for (int i = 0; i < n; ++i) SY_TRY(find_event(q, evs[i], &recs[i]));
+    std::vector<unsigned long long> st;
+    SY_TRY(read_stamps(q, 0, kStampSlots, &st));
+    for (int i = 0; i < n; ++i) SY_TRY(stamp_ms(*recs[i], st.data() + 4ull * recs[i]->slot, &ms[i]));
     return SY_OK;
 }
 
@@ -484,58 +600,6 @@ sy_status sy_saxpy_split(sy_queue_t qh, int64_t n, float alpha, const float* x, 
 }
 
 // ---- stencil ------------------------------------------------------------------------------
-static sy_status stencil_param_checks(const sy_stencil_params* p) {
-    if (!p) return fail(SY_ERR_NULL_POINTER, "params is NULL");
-    if (p->ny < 0 || p->nx < 0) return fail(SY_ERR_INVALID_ARGUMENT, "negative grid size");
-    if (p->pitch < p->nx) return fail(SY_ERR_INVALID_ARGUMENT, "pitch %lld < nx %lld", (long long)p->pitch,
-                                      (long long)p->nx);
-    if (p->radius < 1 || p->radius > 4) return fail(SY_ERR_INVALID_ARGUMENT, "radius %d not in 1..4", p->radius);
-    if (dtype_size(p->dtype) == 0) return fail(SY_ERR_INVALID_ARGUMENT, "unknown dtype %d", p->dtype);
-    if (p->variant < 0 || p->variant > wave_variant_count(p->radius, p->dtype))
-        return fail(SY_ERR_INVALID_ARGUMENT, "variant %d not in 0..%d", p->variant,
-                    wave_variant_count(p->radius, p->dtype));
-    return SY_OK;
-}
-
-static sy_status stencil_common(Queue* q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
-                                void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
-                                sy_event* chunk_events, bool start) {
-    SY_TRY(stencil_param_checks(p));
-    if (p->ny == 0 || p->nx == 0) {
-        if (n_chunks == 0) return SY_OK;
-    }
-    SY_TRY(validate_chunks(p->ny, chunks, n_chunks));
-    if (halo_radius < p->radius)
-        return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
-    if (!u_cur || !u_next || (!start && !u_prev)) return fail(SY_ERR_NULL_POINTER, "field pointer is NULL");
-    size_t bytes = static_cast<size_t>(p->ny) * static_cast<size_t>(p->pitch) * dtype_size(p->dtype);
-    if (ranges_overlap(u_next, bytes, u_cur, bytes)) return fail(SY_ERR_ALIAS, "u_next overlaps u_cur");
-    if (!start && u_next != u_prev && ranges_overlap(u_next, bytes, u_prev, bytes))
-        return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
-    SY_TRY(use_device(q));
-    for (int c = 0; c < n_chunks; ++c) {
-        EventRecord* rec;
-        SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
-        WaveLaunch w;
-        w.ny = p->ny;
-        w.nx = p->nx;
-        w.pitch = p->pitch;
-        w.radius = p->radius;
-        w.dtype = p->dtype;
-        w.variant = p->variant;
-        w.c2 = start ? 0.5f * p->c2 : p->c2;
-        w.start = start;
-        w.u_prev = start ? u_cur : u_prev;
-        w.u_cur = u_cur;
-        w.u_next = u_next;
-        w.row_begin = chunks[c].begin;
-        w.row_end = chunks[c].end;
-        SY_TRY(launch_wave(q, w));
-        SY_TRY(end_event(q, rec));
-    }
-    return SY_OK;
-}
-
 sy_status sy_stencil_step(sy_queue_t qh, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
                           void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
                           sy_event* chunk_events) {

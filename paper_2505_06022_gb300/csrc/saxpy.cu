@@ -11,6 +11,7 @@
 // contracted into an FMA, so the result is fl(fl(alpha*x) + y) bit for bit.
 #include <cstdint>
 
+#include "stamp.cuh"
 #include "sy_internal.h"
 
 namespace sy {
@@ -25,7 +26,9 @@ __device__ __forceinline__ float saxpy1(float alpha, float x, float y) {
 
 // Vector body over n4 float4 elements (all three pointers 16-byte aligned).
 __global__ void __launch_bounds__(kThreads) saxpy_vec4_kernel(int64_t n4, float alpha, const float4* x,
-                                                              const float4* y, float4* z) {
+                                                              const float4* y, float4* z,
+                                                              unsigned long long* stamp) {
+    stamp_begin(stamp);
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
     int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
     // Main loop: kUnroll vectors per thread per trip, loads issued before use.
@@ -54,19 +57,22 @@ __global__ void __launch_bounds__(kThreads) saxpy_vec4_kernel(int64_t n4, float 
         r.w = saxpy1(alpha, a.w, b.w);
         __stcs(z + i, r);
     }
+    stamp_end(stamp);
 }
 
 // Scalar elements: [0, head) and [tail0, n).  Also the whole array when the
 // pointers are not mutually aligned (head = n, tail0 = n).
 __global__ void __launch_bounds__(kThreads) saxpy_scalar_kernel(int64_t n, int64_t head, int64_t tail0,
                                                                 float alpha, const float* x, const float* y,
-                                                                float* z) {
+                                                                float* z, unsigned long long* stamp) {
+    stamp_begin(stamp);
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
     const int64_t count = head + (n - tail0);
     for (int64_t t = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; t < count; t += stride) {
         int64_t i = t < head ? t : tail0 + (t - head);
         z[i] = saxpy1(alpha, __ldcs(x + i), __ldcs(y + i));
     }
+    stamp_end(stamp);
 }
 
 int64_t blocks_for(Queue* q, int64_t work_items) {
@@ -91,19 +97,21 @@ sy_status launch_saxpy(Queue* q, int64_t n, float alpha, const float* x, const f
     }
     if (n4 > 0) {
         int64_t blocks = blocks_for(q, (n4 + kUnroll - 1) / kUnroll);
-        saxpy_vec4_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, q->stream>>>(
+        saxpy_vec4_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, q->launch>>>(
             n4, alpha, reinterpret_cast<const float4*>(x + head), reinterpret_cast<const float4*>(y + head),
-            reinterpret_cast<float4*>(z + head));
+            reinterpret_cast<float4*>(z + head), q->cur_stamp);
         SY_CUDA(cudaGetLastError());
         ++q->launches;
+        q->cur_blocks += static_cast<uint64_t>(blocks);
     }
     const int64_t scalar = head + (n - tail0);
     if (scalar > 0) {
         int64_t blocks = blocks_for(q, scalar);
-        saxpy_scalar_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, q->stream>>>(n, head, tail0, alpha, x, y,
-                                                                                      z);
+        saxpy_scalar_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, q->launch>>>(n, head, tail0, alpha, x, y,
+                                                                                      z, q->cur_stamp);
         SY_CUDA(cudaGetLastError());
         ++q->launches;
+        q->cur_blocks += static_cast<uint64_t>(blocks);
     }
     return SY_OK;
 }

@@ -1,0 +1,32 @@
+// Device side of the per-launch timestamps (see sy_internal.h): the first
+// thread of every block records its start and, after the block's last store,
+// its end and completion.  `s` is a kernel argument (uniform), so the barrier
+// inside the branch is reached by every thread of the block or by none.
+#pragma once
+
+#include <cstdint>
+
+namespace sy {
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void stamp_begin(unsigned long long* s) {
+    if (s != nullptr && threadIdx.x == 0) atomicMax(&s[0], ~globaltimer_ns());
+}
+
+__device__ __forceinline__ void stamp_end(unsigned long long* s) {
+    if (s != nullptr) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicMax(&s[1], globaltimer_ns());
+            atomicAdd(&s[2], 1ull);
+        }
+    }
+}
+
+}  // namespace sy

@@ -31,12 +31,22 @@ void clear_error();
 // Host-side fault injection for tests: SY_FAULT=<name>[,<name>...].
 bool fault_enabled(const char* name);
 
-// ---- queue -----------------------------------------------------------------------
+// ---- device-side kernel timestamps -----------------------------------------------
+// Each timed launch owns one stamp slot of 4 x u64 in device memory, zeroed before
+// use: [0] = ~(earliest block start), [1] = latest block end (both %globaltimer, ns),
+// [2] = blocks finished, [3] = spare.  Blocks stamp with atomics, so timing a launch
+// adds no operation to the stream and does not separate consecutive kernels.
+constexpr uint32_t kStampSlots = 65536;
+constexpr uint32_t kStreamStampSlots = 49152;  // ring for directly issued launches
+constexpr uint32_t kStampPage = 1024;          // the ring is zeroed page by page ahead of use
+constexpr uint32_t kGraphStampSlots = kStampSlots - kStreamStampSlots;
+constexpr uint64_t kEventRing = 65536;
+
 struct EventRecord {
-    cudaEvent_t start = nullptr;
-    cudaEvent_t stop = nullptr;
-    uint64_t id = 0;       // 0 = slot unused
-    int64_t window = -1;   // metering window the kernel was issued in
+    uint64_t id = 0;        // 0 = unused
+    uint32_t slot = 0;      // stamp slot
+    uint64_t expected = 0;  // blocks that stamp the slot when the launch has finished
+    int64_t window = -1;    // metering window the launch was issued in
 };
 
 struct Window {
@@ -46,18 +56,45 @@ struct Window {
     bool have_energy = false;
 };
 
-constexpr uint64_t kEventRing = 65536;
+// One cached whole-run CUDA graph (sy_wave_run).
+struct RunGraph {
+    bool valid = false;
+    sy_stencil_params p{};
+    const void* u0 = nullptr;
+    void* ua = nullptr;
+    void* ub = nullptr;
+    int64_t steps = 0;
+    int halo = 0;
+    bool events = false;
+    std::vector<sy_chunk> chunks;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> expected;  // per graph stamp slot
+    uint64_t launches = 0;           // kernel launches per replay
+    const void* prev_out = nullptr;
+    const void* cur_out = nullptr;
+};
 
 struct Queue {
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // the queue's stream (owned or borrowed)
+    cudaStream_t launch = nullptr;  // where launchers enqueue: `stream`, or `aux` while capturing
+    cudaStream_t aux = nullptr;     // owned: graph capture and timestamp reads
     bool owned = false;
     int sm_count = 0;
     uint64_t launches = 0;
     std::mutex mu;
-    // events
+    // events and timestamps
     std::vector<EventRecord> ring;
     uint64_t next_event = 1;
+    unsigned long long* d_stamps = nullptr;
+    std::vector<uint64_t> slot_owner;  // event id that last used each slot
+    uint32_t next_stream_slot = 0;
+    bool capturing = false;
+    uint32_t next_graph_slot = 0;           // relative to kStreamStampSlots while capturing
+    std::vector<uint64_t> capture_expected;
+    // the launch being issued: launchers stamp `cur_stamp` and add their blocks
+    unsigned long long* cur_stamp = nullptr;
+    uint64_t cur_blocks = 0;
     // energy
     void* nvml_device = nullptr;
     bool energy_ok = false;
@@ -69,6 +106,7 @@ struct Queue {
     // scratch owned by the queue (allocated on first use)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    RunGraph run;
 };
 
 Queue* as_queue(sy_queue_t q);
@@ -78,8 +116,10 @@ sy_status use_device(Queue* q);
 // Scratch of at least `bytes` (device memory owned by the queue).
 sy_status queue_scratch(Queue* q, size_t bytes, void** out);
 
-// Event bracketing of one launch.  begin_event records the start event (when
-// `want` is non-null) and returns the slot; end_event records the stop event.
+// Event bracketing of one logical launch (one or more kernels stamping one slot).
+// begin_event assigns a stamp slot when `want` is non-null; the launchers then
+// pass q->cur_stamp to their kernels and add their grid sizes to q->cur_blocks;
+// end_event closes the record.
 sy_status begin_event(Queue* q, sy_event* want, EventRecord** rec);
 sy_status end_event(Queue* q, EventRecord* rec);
 
@@ -104,6 +144,11 @@ struct WaveLaunch {
     int64_t row_begin, row_end;
 };
 sy_status launch_wave(Queue* q, const WaveLaunch& w);
+// Argument checks and one launch per chunk, shared by sy_stencil_step/start/run.
+sy_status stencil_common(Queue* q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
+                         void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                         sy_event* chunk_events, bool start);
+sy_status stencil_param_checks(const sy_stencil_params* p);
 int wave_variant_count(int radius, int dtype);
 bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* tile_cols, int* threads);
 

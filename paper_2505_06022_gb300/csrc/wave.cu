@@ -51,6 +51,7 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
     a.row_begin = w.row_begin;
     a.row_end = w.row_end;
     a.c2 = w.c2;
+    a.stamp = q->cur_stamp;
     if (!aligned(w.u_cur, esize) || !aligned(w.u_next, esize) || (!w.start && !aligned(w.u_prev, esize)))
         return fail(SY_ERR_INVALID_ARGUMENT, "field pointers must be aligned to the element size (%zu bytes)", esize);
     const bool vec_ok = aligned(w.u_cur, 16) && aligned(w.u_next, 16) && (w.start || aligned(w.u_prev, 16)) &&
@@ -63,7 +64,8 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
         int64_t blocks = (a.tiles + wpb - 1) / wpb;
         const int64_t cap = static_cast<int64_t>(occupancy(vec_fn, threads)) * q->sm_count;
         if (blocks > cap) blocks = cap;
-        vec_fn<<<static_cast<unsigned>(blocks), threads, 0, q->stream>>>(a);
+        vec_fn<<<static_cast<unsigned>(blocks), threads, 0, q->launch>>>(a);
+        q->cur_blocks += static_cast<uint64_t>(blocks);
     } else {
         a.tiles_x = 0;
         a.tiles = 0;
@@ -71,7 +73,8 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
         int64_t blocks = (total + 255) / 256;
         const int64_t cap = static_cast<int64_t>(q->sm_count) * 8;
         if (blocks > cap) blocks = cap;
-        scalar_fn<<<static_cast<unsigned>(blocks), 256, 0, q->stream>>>(a);
+        scalar_fn<<<static_cast<unsigned>(blocks), 256, 0, q->launch>>>(a);
+        q->cur_blocks += static_cast<uint64_t>(blocks);
     }
     SY_CUDA(cudaGetLastError());
     ++q->launches;
@@ -87,7 +90,9 @@ bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* 
         return false;
     int rows, thr;
     if (variant == 0) {
-        rows = 8;
+        // Default: 4-row tiles, 256-thread blocks (76 registers for r = 1, three
+        // blocks per SM).  Measured best or within 1% of best at 8192^2 for FP32.
+        rows = 4;
         thr = 256;
     } else {
         rows = wave::kTileRows[(variant - 1) % 4];
@@ -224,12 +229,12 @@ sy_status launch_wave_energy(Queue* q, const sy_stencil_params* p, const void* u
     a.nx = p->nx;
     a.pitch_bytes = p->pitch * static_cast<int64_t>(esize);
     switch (p->dtype) {
-        case SY_F32: energy::launch_partials<float>(p->radius, a, partials, q->stream); break;
-        case SY_BF16: energy::launch_partials<__nv_bfloat16>(p->radius, a, partials, q->stream); break;
-        default: energy::launch_partials<__half>(p->radius, a, partials, q->stream); break;
+        case SY_F32: energy::launch_partials<float>(p->radius, a, partials, q->launch); break;
+        case SY_BF16: energy::launch_partials<__nv_bfloat16>(p->radius, a, partials, q->launch); break;
+        default: energy::launch_partials<__half>(p->radius, a, partials, q->launch); break;
     }
     SY_CUDA(cudaGetLastError());
-    energy::energy_final_kernel<<<1, kEnergyBlocks, 0, q->stream>>>(partials, static_cast<double>(p->c2), out3_device);
+    energy::energy_final_kernel<<<1, kEnergyBlocks, 0, q->launch>>>(partials, static_cast<double>(p->c2), out3_device);
     SY_CUDA(cudaGetLastError());
     q->launches += 2;
     return SY_OK;

@@ -32,6 +32,7 @@
 
 #include <cstdint>
 
+#include "stamp.cuh"
 #include "sy_internal.h"
 
 namespace sy {
@@ -178,6 +179,7 @@ struct Args {
     int64_t row_begin, row_end;
     int64_t tiles_x, tiles;  // vector kernel: tiles per row band, total tiles
     float c2;                // coefficient of L u
+    unsigned long long* stamp;  // timestamp slot of this launch, or null
 };
 
 // One output point from its neighbourhood, in the canonical operation order.
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
     using T = Traits<S>;
     constexpr int V = T::V;
     static_assert(R <= V, "radius must not exceed the vector width");
+    stamp_begin(a.stamp);
     const int lane = threadIdx.x & 31;
     const int64_t warps_per_block = blockDim.x >> 5;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * warps_per_block;
@@ -239,9 +242,11 @@ __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
             if (edge_lane && row < a.row_end)
                 edge[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + xe * sizeof(S)));
         }
+        if (nvalid < V) {  // only the vector straddling nx (or past it) needs masking
 #pragma unroll
-        for (int k = 0; k < RY + 2 * R; ++k) T::mask(cur[k], nvalid);
-        if (lane == 31) {
+            for (int k = 0; k < RY + 2 * R; ++k) T::mask(cur[k], nvalid);
+        }
+        if (lane == 31 && edge_valid < V) {
 #pragma unroll
             for (int k = 0; k < RY; ++k) T::mask(edge[k], edge_valid);
         }
@@ -285,12 +290,14 @@ __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
             }
         }
     }
+    stamp_end(a.stamp);
 }
 
 // One point per thread; any element-aligned layout.
 template <typename S, int R, bool START>
 __global__ void __launch_bounds__(256) wave_scalar_kernel(Args a) {
     using T = Traits<S>;
+    stamp_begin(a.stamp);
     const int64_t rows = a.row_end - a.row_begin;
     const int64_t total = rows * a.nx;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -311,6 +318,7 @@ __global__ void __launch_bounds__(256) wave_scalar_kernel(Args a) {
         const float up = START ? 0.0f : T::load1_cs(a.u_prev + off);
         T::store1(a.u_next + off, update<R, START>(at(i, j), up, vert, horz, a.c2));
     }
+    stamp_end(a.stamp);
 }
 
 // Row heights of the vector kernel's tiles; variant v (1-based) = (kTileRows[(v-1) % 4],
