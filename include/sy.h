@@ -257,6 +257,30 @@ sy_status sy_stencil_variant_info(int radius, int dtype, int variant, int* tile_
 sy_status sy_wave_energy(sy_queue_t q, const sy_stencil_params* p, const void* u_new, const void* u_old,
                          double* energy, double* kinetic, double* potential);
 
+/* Allocation-free form of sy_wave_energy.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * moment they need the energy -- code issuing work while a stream is being
+ * captured into a CUDA graph in global mode (cudaMalloc is not permitted then),
+ * applications whose own allocator owns all device memory, and loops that must
+ * never hit the device-wide synchronisation cudaMalloc/cudaFree can cause.  It
+ * allocates nothing and synchronises nothing:
+ *   - The per-block partial sums live in one fixed module-scope device array of
+ *     2 x 1024 doubles (16 KiB), which every GPU that loads the library holds
+ *     until the process exits.  The reduction always uses exactly that many; a
+ *     call needing more is rejected with SY_ERR_INVALID_ARGUMENT.
+ *   - It runs on the calling thread's current device, on `cuda_stream` (a
+ *     cudaStream_t; NULL = the legacy default stream), with no queue.
+ *   - out3 (device, 3 doubles, caller-owned) receives energy, kinetic and
+ *     potential, as sy_wave_energy computes them (same kernels, same order).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array and leaves its partial sums there; each
+ *     call overwrites all of them before reading, so nothing needs clearing, but
+ *     calls that overlap on the GPU (different streams, or a graph replayed
+ *     concurrently) race on it and must be serialised by the caller. */
+sy_status sy_wave_energy_static(void* cuda_stream, const sy_stencil_params* p, const void* u_new, const void* u_old,
+                                double* out3);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

@@ -85,6 +85,7 @@ _SIGS = {
     "sy_stencil_variant_count": [C.c_int, C.c_int, _p],
     "sy_stencil_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p, _p],
     "sy_wave_energy": [_p, _p, _p, _p, _p, _p, _p],
+    "sy_wave_energy_static": [_p, _p, _p, _p, _p],
     "sy_wave_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
 }
 _RESTYPE = {"sy_status_string": C.c_char_p, "sy_last_error": C.c_char_p, "sy_abi_version": C.c_int}
@@ -273,6 +274,12 @@ def sy_stencil_start(q: int, p: StencilParams, u0, u_m1, chunks, halo_radius: in
     _call("sy_stencil_start", q, C.byref(p), _ptr(u0), _ptr(u_m1), arr, k, halo_radius,
           evs if want_events else None)
     return list(evs[:k]) if want_events else []
+
+
+def sy_wave_energy_static(stream: int | None, p: StencilParams, u_new, u_old, out3) -> None:
+    """Allocation-free energy: writes (energy, kinetic, potential) into the
+    caller's device buffer out3 (3 float64) on `stream` (None = legacy default)."""
+    _call("sy_wave_energy_static", stream or None, C.byref(p), _ptr(u_new), _ptr(u_old), _ptr(out3))
 
 
 def sy_wave_run(q: int, p: StencilParams, u0, u_a, u_b, steps: int, chunks, halo_radius: int,

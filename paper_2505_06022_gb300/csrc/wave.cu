@@ -216,9 +216,12 @@ void launch_partials(int radius, EArgs a, double* partials, cudaStream_t s) {
 
 }  // namespace energy
 
-sy_status launch_wave_energy(Queue* q, const sy_stencil_params* p, const void* u_new, const void* u_old,
-                             double* partials, int n_partials, double* out3_device) {
-    if (n_partials != kEnergyBlocks) return fail(SY_ERR_INVALID_ARGUMENT, "energy partials must be %d", kEnergyBlocks);
+namespace {
+
+// Both energy kernels on `stream`: partials (2 * kEnergyBlocks doubles) then the
+// three results (energy, kinetic, potential) into out3 (device).
+sy_status launch_energy_on(cudaStream_t stream, const sy_stencil_params* p, const void* u_new, const void* u_old,
+                           double* partials, double* out3) {
     const size_t esize = dtype_size(p->dtype);
     if ((reinterpret_cast<uintptr_t>(u_new) % esize) || (reinterpret_cast<uintptr_t>(u_old) % esize))
         return fail(SY_ERR_INVALID_ARGUMENT, "field pointers must be aligned to the element size");
@@ -229,15 +232,86 @@ sy_status launch_wave_energy(Queue* q, const sy_stencil_params* p, const void* u
     a.nx = p->nx;
     a.pitch_bytes = p->pitch * static_cast<int64_t>(esize);
     switch (p->dtype) {
-        case SY_F32: energy::launch_partials<float>(p->radius, a, partials, q->launch); break;
-        case SY_BF16: energy::launch_partials<__nv_bfloat16>(p->radius, a, partials, q->launch); break;
-        default: energy::launch_partials<__half>(p->radius, a, partials, q->launch); break;
+        case SY_F32: energy::launch_partials<float>(p->radius, a, partials, stream); break;
+        case SY_BF16: energy::launch_partials<__nv_bfloat16>(p->radius, a, partials, stream); break;
+        default: energy::launch_partials<__half>(p->radius, a, partials, stream); break;
     }
     SY_CUDA(cudaGetLastError());
-    energy::energy_final_kernel<<<1, kEnergyBlocks, 0, q->launch>>>(partials, static_cast<double>(p->c2), out3_device);
+    energy::energy_final_kernel<<<1, kEnergyBlocks, 0, stream>>>(partials, static_cast<double>(p->c2), out3);
     SY_CUDA(cudaGetLastError());
+    return SY_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Allocation-free energy reduction (sy_wave_energy_static)
+// ---------------------------------------------------------------------------
+// Some callers cannot allocate device memory where they need the energy: code
+// issuing work while a stream is captured into a CUDA graph in global mode
+// (cudaMalloc is not permitted then), applications whose own allocator owns all
+// device memory, and loops that must never hit the device-wide synchronisation
+// cudaMalloc/cudaFree can cause.  For them the per-block partial sums live in
+// this module-scope array instead of the queue's scratch.  Size: 2 x
+// kEnergyBlocks doubles = 16 KiB, held by every GPU that loads the library until
+// the process exits.  Host code must not pass the array's name to a kernel (on
+// the host it names a stand-in, not device memory): it uses the address that
+// cudaGetSymbolAddress returns for the current device, looked up once per device.
+constexpr int kStaticEnergyDoubles = 2 * kEnergyBlocks;
+static __device__ __align__(256) double g_energy_partials_static[kStaticEnergyDoubles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of the static partials on the current device (set up on the
+// first call per device).
+sy_status static_partials(double** out) {
+    int dev = -1;
+    SY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SY_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_energy_partials_static);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_energy_partials_static)");
+        g_static_addr[dev] = ptr;
+    }
+    *out = static_cast<double*>(g_static_addr[dev]);
+    return SY_OK;
+}
+}  // namespace
+
+sy_status launch_wave_energy(Queue* q, const sy_stencil_params* p, const void* u_new, const void* u_old,
+                             double* partials, int n_partials, double* out3_device) {
+    if (n_partials != kEnergyBlocks) return fail(SY_ERR_INVALID_ARGUMENT, "energy partials must be %d", kEnergyBlocks);
+    SY_TRY(launch_energy_on(q->launch, p, u_new, u_old, partials, out3_device));
     q->launches += 2;
     return SY_OK;
 }
 
 }  // namespace sy
+
+extern "C" sy_status sy_wave_energy_static(void* cuda_stream, const sy_stencil_params* p, const void* u_new,
+                                           const void* u_old, double* out3) {
+    using namespace sy;
+    SY_TRY(stencil_param_checks(p));
+    if (!out3) return fail(SY_ERR_NULL_POINTER, "out3 is NULL");
+    if (reinterpret_cast<uintptr_t>(out3) % alignof(double))
+        return fail(SY_ERR_INVALID_ARGUMENT, "out3 must be 8-byte aligned");
+    // The reduction always writes 2 * kEnergyBlocks partial sums (its fixed shape).
+    const int64_t need = 2 * static_cast<int64_t>(kEnergyBlocks);
+    if (need > kStaticEnergyDoubles)
+        return fail(SY_ERR_INVALID_ARGUMENT, "the reduction needs %lld partial sums, the static scratch holds %d",
+                    static_cast<long long>(need), kStaticEnergyDoubles);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (p->ny == 0 || p->nx == 0) {
+        SY_CUDA(cudaMemsetAsync(out3, 0, 3 * sizeof(double), stream));
+        return SY_OK;
+    }
+    if (!u_new || !u_old) return fail(SY_ERR_NULL_POINTER, "field pointer is NULL");
+    double* partials = nullptr;
+    SY_TRY(static_partials(&partials));
+    return launch_energy_on(stream, p, u_new, u_old, partials, out3);
+}
