@@ -195,6 +195,162 @@ def run_reference(args) -> None:
 
 
 # ---------------------------------------------------------------------------
+# The other forms of the path, each against the plain form on the same GPU
+# ---------------------------------------------------------------------------
+
+def _metered(q, stream, fn, min_seconds: float = 0.6, min_reps: int = 3):
+    """Run fn() repeatedly for >= min_seconds inside one NVML metering window;
+    returns (reps, device ms per rep, joules or None)."""
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+
+    torch.cuda.synchronize()
+    try:
+        sy.sy_meter_begin(q.handle)
+        metered = True
+    except sy.SyError:
+        metered = False
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps, t0 = 0, time.perf_counter()
+    e0.record(stream)
+    while reps < min_reps or time.perf_counter() - t0 < min_seconds:
+        fn()
+        reps += 1
+        if reps % 4 == 0:
+            torch.cuda.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    joules = None
+    if metered:
+        try:
+            joules, _ = sy.sy_meter_end(q.handle)
+        except sy.SyError:
+            joules = None
+    return reps, e0.elapsed_time(e1) / reps, joules
+
+
+def measure_precision_form(q, stream, dtype: str) -> dict:
+    """8192^2 Gaussian, 200 steps, 4 chunks, with `dtype` storage: throughput, J/update,
+    error against the FP64 oracle on light-cone samples, discrete-energy drift."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import inputs
+
+    p = sy.stencil_params(NY, NX, RADIUS, C2, dtype)
+    chunks = sy.sy_split_rows(NY, CHUNKS)
+    u64 = inputs.gaussian_pulse(NY, NX, SIGMA)
+    host = inputs.to_storage(u64, dtype)
+    u0 = torch.from_numpy(host if dtype == "f32" else host.view(np.int16)).cuda()
+    A, B = torch.empty_like(u0), torch.empty_like(u0)
+    byptr = {u0.data_ptr(): u0, A.data_ptr(): A, B.data_ptr(): B}
+    # energy at the start: E(u^0, u^{-1})
+    pv, cv, _ = sy.sy_wave_run(q.handle, p, u0, A, B, 0, chunks, HALO)
+    E0 = sy.sy_wave_energy(q.handle, p, byptr[cv], byptr[pv])[0]
+    run = lambda: sy.sy_wave_run(q.handle, p, u0, A, B, STEPS, chunks, HALO)
+    run()
+    reps, ms, joules = _metered(q, stream, run)
+    pv, cv, _ = run()
+    torch.cuda.synchronize()
+    E1 = sy.sy_wave_energy(q.handle, p, byptr[cv], byptr[pv])[0]
+    got = byptr[cv].cpu().numpy()
+    got = got.astype(np.float64) if dtype == "f32" else oracle.storage_to_f64(got.view(np.uint16), oracle.DTYPES[dtype])
+    # light-cone samples against the FP64 oracle run from the FP64 initial field
+    worst, scale = 0.0, float(np.max(np.abs(got)))
+    h = (STEPS + 1) * RADIUS + 1
+    for (pi, pj) in [(NY // 2, NX // 2), (NY // 2, NX // 2 + 100), (NY // 2 - 70, NX // 2 + 70), (0, 0),
+                     (NY // 2 + 40, NX // 2 - 90)]:
+        y0, y1, x0, x1 = max(0, pi - h), min(NY, pi + h + 1), max(0, pj - h), min(NX, pj + h + 1)
+        _, c64 = oracle.wave_run_f64(np.ascontiguousarray(u64[y0:y1, x0:x1]), STEPS, RADIUS, C2)
+        worst = max(worst, abs(got[pi, pj] - c64[pi - y0, pj - x0]))
+    esize = 4 if dtype == "f32" else 2
+    upd = STEPS * NY * NX
+    return {"dtype": dtype, "updates_per_s": upd / (ms * 1e-3), "gb_per_s": 3 * esize * upd / (ms * 1e-3) / 1e9,
+            "ms_per_sim": ms, "j_per_update": None if not joules else joules / (reps * upd),
+            "max_abs_err_vs_f64_samples": worst, "max_rel_err_vs_f64_samples": worst / scale,
+            "energy_drift_rel": (E1 - E0) / E0}
+
+
+def measure_batched(q, stream) -> dict:
+    """64 uneven grids (sides log-uniform in [256, 4096], seed 1, radius in {1, 2, 4}), 100 steps:
+    one persistent launch per step in a CUDA graph (tile height tuned over {2, 4, 8}) against
+    one launch per grid per step (in a CUDA graph, and from the host stream)."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import inputs
+
+    shapes = inputs.batch_grids()
+    steps = 100
+    fields = []
+    for ny, nx, r in shapes:
+        pitch = (nx + 3) // 4 * 4
+        ub = torch.zeros((ny, pitch), dtype=torch.float32, device="cuda")
+        ub[:, :nx] = torch.from_numpy(inputs.batch_initial(ny, nx, "f32")).cuda()
+        fields.append((ny, nx, pitch, r, torch.empty_like(ub), ub))
+    points = sum(ny * nx for ny, nx, *_ in fields)
+    upd = steps * points
+    best = None
+    for tile_rows in (2, 4, 8):
+        plan = sy.sy_stencil_batch_plan(q.handle, [(ny, nx, pitch, r, C2, ua, ub) for ny, nx, pitch, r, ua, ub
+                                                   in fields], "f32", tile_rows)
+        sy.sy_stencil_batch_start(plan)
+        sy.sy_stencil_batch_capture(plan, steps)
+        sy.sy_stencil_batch_run(plan)
+        reps, ms, joules = _metered(q, stream, lambda: sy.sy_stencil_batch_run(plan), min_seconds=0.2)
+        if best is None or ms < best[1]:
+            best = (tile_rows, ms, joules, reps)
+        sy.sy_stencil_batch_destroy(plan)
+    tile_rows, _, _, _ = best
+    plan = sy.sy_stencil_batch_plan(q.handle, [(ny, nx, pitch, r, C2, ua, ub) for ny, nx, pitch, r, ua, ub
+                                               in fields], "f32", tile_rows)
+    sy.sy_stencil_batch_capture(plan, steps)
+    sy.sy_stencil_batch_run(plan)
+    reps, ms, joules = _metered(q, stream, lambda: sy.sy_stencil_batch_run(plan))
+    sy.sy_stencil_batch_destroy(plan)
+
+    # baseline: one launch per grid per step
+    params = [(sy.stencil_params(ny, nx, r, C2, "f32", pitch=pitch), ua, ub, [(0, ny)], r)
+              for ny, nx, pitch, r, ua, ub in fields]
+
+    def per_grid_steps():
+        for s in range(steps):
+            for p, ua, ub, ch, r in params:
+                prev, cur = (ua, ub) if s % 2 == 0 else (ub, ua)
+                sy.sy_stencil_step(qg.handle, p, prev, cur, prev, ch, r)
+
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        qg = sy.Queue(q.device, side)
+        per_grid_steps()  # warm-up (and occupancy lookups) outside the capture
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        per_grid_steps()
+    g.replay()
+    reps_g, ms_g, joules_g = _metered(q, stream, g.replay)
+    qs = sy.Queue(q.device, stream)
+    qg_saved = qg
+    qg = qs
+    reps_s, ms_s, _ = _metered(q, stream, per_grid_steps, min_seconds=0.3, min_reps=2)
+    qg = qg_saved
+    qs.close()
+    del g
+    return {"grids": len(fields), "points": points, "steps": steps, "tile_rows": tile_rows,
+            "batched_updates_per_s": upd / (ms * 1e-3), "batched_gb_per_s": 12 * upd / (ms * 1e-3) / 1e9,
+            "batched_ms_per_run": ms, "batched_j_per_update": None if not joules else joules / (reps * upd),
+            "per_grid_graph_updates_per_s": upd / (ms_g * 1e-3), "per_grid_graph_ms_per_run": ms_g,
+            "per_grid_graph_j_per_update": None if not joules_g else joules_g / (reps_g * upd),
+            "per_grid_stream_updates_per_s": upd / (ms_s * 1e-3), "per_grid_stream_ms_per_run": ms_s,
+            "launches_per_run": {"batched": steps, "per_grid": steps * len(fields)}}
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
 
@@ -328,6 +484,13 @@ def run_gpu(args) -> None:
         E = sy.sy_wave_energy(q.handle, p, byptr[cv], byptr[pv])[0]
         assert np.isfinite(E) and E > 0
 
+    forms = None
+    if rank == 0 and args.forms:
+        forms = {"plain_f32": {"updates_per_s": value, "gb_per_s": value * BYTES_PER_UPDATE / 1e9,
+                               "j_per_update": None if not energy else energy["j_per_update"]}}
+        for dt in ("bf16", "f16"):
+            forms[dt] = measure_precision_form(q, stream, dt)
+        forms["batched"] = measure_batched(q, stream)
     if dist:
         dist.barrier()
     if rank == 0:
@@ -346,6 +509,7 @@ def run_gpu(args) -> None:
             "energy": energy,
             "e2e": e2e,
             "gpu_launches": launches,
+            "forms": forms,
             "clocks": clk,
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
                                                                           "sample")},
@@ -363,6 +527,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sy", choices=["sy", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--forms", type=int, default=1, help="also measure the BF16/FP16 and batched forms (rank 0)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "sy":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -257,6 +257,54 @@ sy_status sy_stencil_variant_info(int radius, int dtype, int variant, int* tile_
 sy_status sy_wave_energy(sy_queue_t q, const sy_stencil_params* p, const void* u_new, const void* u_old,
                          double* energy, double* kinetic, double* potential);
 
+/* ------------------------------------------------------------------------- */
+/* Batched stencils: many independent, unevenly sized grids in one launch     */
+/* ------------------------------------------------------------------------- */
+/* Each grid is advanced with the stencil of sy_stencil_step over its whole row
+ * range (one chunk).  One persistent launch steps every grid once: the warps
+ * stride over the concatenated tile list of all grids, so small and large grids
+ * share the GPU instead of paying one launch each.  A run of steps can be
+ * captured into a CUDA graph and replayed.  Results are bit-identical to
+ * stepping every grid with sy_stencil_step. */
+typedef struct sy_batch_grid {
+    int64_t ny;     /* rows (>= 1) */
+    int64_t nx;     /* columns (>= 1) */
+    int64_t pitch;  /* elements between row starts (>= nx); pitch * sizeof(dtype) % 16 == 0 */
+    int32_t radius; /* 1..4 */
+    float c2;       /* (c dt / dx)^2 */
+    void* u_a;      /* device, 16-byte aligned, ny * pitch elements: u^{n-1} (or u^{-1} after the start) */
+    void* u_b;      /* device, 16-byte aligned, ny * pitch elements: u^n (or u^0 before the start) */
+} sy_batch_grid;
+
+typedef struct sy_batch_plan_s* sy_batch_plan_t;
+
+/* Build a plan over n_grids (1..4096) grids of one dtype.  tile_rows: tile height
+ * of the warp tiles, 2, 4 or 8 (0 = 4).  The grids' buffers must not overlap each
+ * other.  The plan copies the descriptors to the device; the buffers stay owned by
+ * the caller and must outlive the plan. */
+sy_status sy_stencil_batch_plan(sy_queue_t q, const sy_batch_grid* grids, int n_grids, int dtype, int tile_rows,
+                                sy_batch_plan_t* out);
+/* Totals of a plan (each pointer nullable): warp tiles, grid points, blocks of the
+ * persistent launch. */
+sy_status sy_stencil_batch_info(sy_batch_plan_t plan, int64_t* total_tiles, int64_t* points, int* blocks);
+/* Taylor start for every grid: u_a = u_b + (c2/2) L u_b (one launch). */
+sy_status sy_stencil_batch_start(sy_batch_plan_t plan, int timed);
+/* One leapfrog step of every grid (one launch).  parity 0: u_a <- step(u_a, u_b);
+ * parity 1: u_b <- step(u_b, u_a).  timed != 0 records the launch's device time
+ * (read with sy_stencil_batch_times, index 0). */
+sy_status sy_stencil_batch_step(sy_batch_plan_t plan, int parity, int timed);
+/* Capture `steps` consecutive steps, parities 0, 1, 0, ... into a CUDA graph owned
+ * by the plan (replacing any earlier capture).  Every launch is timed. */
+sy_status sy_stencil_batch_capture(sy_batch_plan_t plan, int64_t steps);
+/* Replay the captured steps on the queue's stream.  Each replay starts at parity
+ * 0, so with an even step count consecutive replays continue the simulation; after
+ * a replay of an odd count u_a holds the newest field. */
+sy_status sy_stencil_batch_run(sy_batch_plan_t plan);
+/* Device times (ms) of the plan's timed launches: index 0 = the last timed
+ * sy_stencil_batch_start/step, index 1 + s = step s of the last replay. */
+sy_status sy_stencil_batch_times(sy_batch_plan_t plan, double* ms, int n);
+sy_status sy_stencil_batch_destroy(sy_batch_plan_t plan);
+
 /* Allocation-free form of sy_wave_energy.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the
  * moment they need the energy -- code issuing work while a stream is being

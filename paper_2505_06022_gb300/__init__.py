@@ -45,6 +45,11 @@ class Chunk(C.Structure):
     _fields_ = [("begin", C.c_int64), ("end", C.c_int64)]
 
 
+class BatchGrid(C.Structure):
+    _fields_ = [("ny", C.c_int64), ("nx", C.c_int64), ("pitch", C.c_int64), ("radius", C.c_int32),
+                ("c2", C.c_float), ("u_a", C.c_void_p), ("u_b", C.c_void_p)]
+
+
 class StencilParams(C.Structure):
     _fields_ = [("ny", C.c_int64), ("nx", C.c_int64), ("pitch", C.c_int64), ("radius", C.c_int32),
                 ("dtype", C.c_int32), ("c2", C.c_float), ("variant", C.c_int32)]
@@ -86,6 +91,14 @@ _SIGS = {
     "sy_stencil_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p, _p],
     "sy_wave_energy": [_p, _p, _p, _p, _p, _p, _p],
     "sy_wave_energy_static": [_p, _p, _p, _p, _p],
+    "sy_stencil_batch_plan": [_p, _p, C.c_int, C.c_int, C.c_int, _p],
+    "sy_stencil_batch_info": [_p, _p, _p, _p],
+    "sy_stencil_batch_start": [_p, C.c_int],
+    "sy_stencil_batch_step": [_p, C.c_int, C.c_int],
+    "sy_stencil_batch_capture": [_p, _i64],
+    "sy_stencil_batch_run": [_p],
+    "sy_stencil_batch_times": [_p, _p, C.c_int],
+    "sy_stencil_batch_destroy": [_p],
     "sy_wave_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
 }
 _RESTYPE = {"sy_status_string": C.c_char_p, "sy_last_error": C.c_char_p, "sy_abi_version": C.c_int}
@@ -280,6 +293,49 @@ def sy_wave_energy_static(stream: int | None, p: StencilParams, u_new, u_old, ou
     """Allocation-free energy: writes (energy, kinetic, potential) into the
     caller's device buffer out3 (3 float64) on `stream` (None = legacy default)."""
     _call("sy_wave_energy_static", stream or None, C.byref(p), _ptr(u_new), _ptr(u_old), _ptr(out3))
+
+
+def sy_stencil_batch_plan(q: int, grids, dtype: str | int = "f32", tile_rows: int = 0) -> int:
+    """grids: iterable of (ny, nx, pitch, radius, c2, u_a, u_b) with tensors or addresses."""
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    gl = list(grids)
+    arr = (BatchGrid * max(1, len(gl)))(*[BatchGrid(ny, nx, pitch, r, c2, _ptr(a), _ptr(b))
+                                         for (ny, nx, pitch, r, c2, a, b) in gl])
+    h = C.c_void_p()
+    _call("sy_stencil_batch_plan", q, arr, len(gl), code, tile_rows, C.byref(h))
+    return h.value
+
+
+def sy_stencil_batch_info(plan: int) -> tuple[int, int, int]:
+    t, pts, b = C.c_int64(), C.c_int64(), C.c_int()
+    _call("sy_stencil_batch_info", plan, C.byref(t), C.byref(pts), C.byref(b))
+    return t.value, pts.value, b.value
+
+
+def sy_stencil_batch_start(plan: int, timed: bool = False) -> None:
+    _call("sy_stencil_batch_start", plan, int(timed))
+
+
+def sy_stencil_batch_step(plan: int, parity: int, timed: bool = False) -> None:
+    _call("sy_stencil_batch_step", plan, parity, int(timed))
+
+
+def sy_stencil_batch_capture(plan: int, steps: int) -> None:
+    _call("sy_stencil_batch_capture", plan, steps)
+
+
+def sy_stencil_batch_run(plan: int) -> None:
+    _call("sy_stencil_batch_run", plan)
+
+
+def sy_stencil_batch_times(plan: int, n: int) -> list[float]:
+    ms = (C.c_double * max(1, n))()
+    _call("sy_stencil_batch_times", plan, ms, n)
+    return list(ms[:n])
+
+
+def sy_stencil_batch_destroy(plan: int) -> None:
+    _call("sy_stencil_batch_destroy", plan)
 
 
 def sy_wave_run(q: int, p: StencilParams, u0, u_a, u_b, steps: int, chunks, halo_radius: int,

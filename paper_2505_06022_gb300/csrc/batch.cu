@@ -1,0 +1,353 @@
+// Batched leapfrog steps over many independent, unevenly sized grids: one
+// persistent launch advances every grid by one step, and a run of steps is
+// captured into a CUDA graph.
+//
+// Work list: the warp tiles of all grids, concatenated in plan order (each grid's
+// tiles in row-major order).  A persistent grid of SMs x occupancy blocks strides
+// over that list; a warp finds its grid by binary search over the tiles' prefix
+// sums (held in shared memory) and runs the same tile code as the single-field
+// kernel (wave_tile), with the grid's own radius selected at run time.  Grids of
+// every size therefore share the GPU in one launch instead of paying one
+// launch (and one partially filled last wave) per grid.
+//
+// Buffers: grid g owns u_a and u_b.  A step with parity 0 reads u_a (u^{n-1})
+// and u_b (u^n) and writes u^{n+1} over u_a; parity 1 swaps the roles.  The
+// Taylor start writes u^{-1} = start(u_b) into u_a.
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "wave_kernel.cuh"
+
+namespace sy {
+
+struct BatchGridDev {
+    char* ua;
+    char* ub;
+    int64_t ny, nx, pitch_bytes;
+    int64_t tiles_x;
+    int64_t tile_begin;
+    int32_t radius;
+    float c2;
+};
+
+struct BatchPlan {
+    Queue* q = nullptr;
+    int dtype = 0;
+    int tile_rows = 4;
+    int n_grids = 0;
+    int64_t total_tiles = 0;
+    int64_t points = 0;
+    BatchGridDev* d_desc = nullptr;
+    unsigned long long* d_stamps = nullptr;  // slot 0: last direct launch; 1..: graph launches
+    int64_t stamp_slots = 0;
+    std::vector<uint64_t> expected;          // blocks per stamped launch (index = slot)
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_steps = 0;
+    uint64_t graph_launches = 0;
+    int blocks = 0;                          // persistent grid size
+    int threads = 256;
+};
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr int kMaxBatchGrids = 4096;  // prefix sums in shared memory: 32 KiB
+
+template <typename S, int RY, bool START>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev* __restrict__ grids, int n_grids,
+                                                              int64_t total_tiles, int parity,
+                                                              unsigned long long* stamp) {
+    extern __shared__ int64_t s_begin[];  // n_grids + 1 prefix sums
+    stamp_begin(stamp);
+    for (int i = threadIdx.x; i <= n_grids; i += blockDim.x) s_begin[i] = i < n_grids ? grids[i].tile_begin : total_tiles;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_per_block = blockDim.x >> 5;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * warps_per_block;
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); t < total_tiles;
+         t += nwarps) {
+        int lo = 0, hi = n_grids - 1;  // largest g with s_begin[g] <= t (warp-uniform)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_begin[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchGridDev& G = grids[lo];
+        wave::Args a;
+        const bool swap = (parity & 1) != 0;
+        a.u_prev = swap ? G.ub : G.ua;
+        a.u_cur = START ? G.ub : (swap ? G.ua : G.ub);
+        a.u_next = START ? G.ua : (swap ? G.ub : G.ua);
+        a.ny = G.ny;
+        a.nx = G.nx;
+        a.pitch_bytes = G.pitch_bytes;
+        a.row_begin = 0;
+        a.row_end = G.ny;
+        a.tiles_x = G.tiles_x;
+        a.tiles = 0;
+        a.c2 = START ? 0.5f * G.c2 : G.c2;
+        a.stamp = nullptr;
+        const int64_t local = t - s_begin[lo];
+        const int64_t ty = local / G.tiles_x;
+        const int64_t tx = local - ty * G.tiles_x;
+        switch (G.radius) {
+            case 1: wave::wave_tile<S, 1, RY, START>(a, tx, ty, lane); break;
+            case 2: wave::wave_tile<S, 2, RY, START>(a, tx, ty, lane); break;
+            case 3: wave::wave_tile<S, 3, RY, START>(a, tx, ty, lane); break;
+            default: wave::wave_tile<S, 4, RY, START>(a, tx, ty, lane); break;
+        }
+    }
+    stamp_end(stamp);
+}
+
+using BatchFn = void (*)(const BatchGridDev*, int, int64_t, int, unsigned long long*);
+
+template <typename S, bool START>
+BatchFn pick_batch(int tile_rows) {
+    switch (tile_rows) {
+        case 2: return batch_kernel<S, 2, START>;
+        case 8: return batch_kernel<S, 8, START>;
+        default: return batch_kernel<S, 4, START>;
+    }
+}
+
+BatchFn batch_fn(int dtype, int tile_rows, bool start) {
+    switch (dtype) {
+        case SY_F32: return start ? pick_batch<float, true>(tile_rows) : pick_batch<float, false>(tile_rows);
+        case SY_BF16:
+            return start ? pick_batch<__nv_bfloat16, true>(tile_rows) : pick_batch<__nv_bfloat16, false>(tile_rows);
+        default: return start ? pick_batch<__half, true>(tile_rows) : pick_batch<__half, false>(tile_rows);
+    }
+}
+
+BatchPlan* as_plan(sy_batch_plan_t p) { return reinterpret_cast<BatchPlan*>(p); }
+
+// One persistent launch on q->launch; `slot` < 0 means untimed.
+sy_status launch_batch(BatchPlan* P, bool start, int parity, int64_t slot) {
+    Queue* q = P->q;
+    BatchFn fn = batch_fn(P->dtype, P->tile_rows, start);
+    unsigned long long* stamp = slot >= 0 ? P->d_stamps + 4 * slot : nullptr;
+    const size_t smem = sizeof(int64_t) * static_cast<size_t>(P->n_grids + 1);
+    fn<<<P->blocks, P->threads, smem, q->launch>>>(P->d_desc, P->n_grids, P->total_tiles, parity, stamp);
+    SY_CUDA(cudaGetLastError());
+    ++q->launches;
+    if (slot >= 0) P->expected[slot] = static_cast<uint64_t>(P->blocks);
+    return SY_OK;
+}
+
+}  // namespace
+}  // namespace sy
+
+using namespace sy;
+
+extern "C" {
+
+sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n_grids, int dtype, int tile_rows,
+                                sy_batch_plan_t* out) {
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    if (!out) return fail(SY_ERR_NULL_POINTER, "out is NULL");
+    *out = nullptr;
+    if (n_grids < 1 || n_grids > kMaxBatchGrids)
+        return fail(SY_ERR_INVALID_ARGUMENT, "n_grids = %d not in 1..%d", n_grids, kMaxBatchGrids);
+    if (!grids) return fail(SY_ERR_NULL_POINTER, "grids is NULL");
+    const size_t esize = dtype_size(dtype);
+    if (!esize) return fail(SY_ERR_INVALID_ARGUMENT, "unknown dtype %d", dtype);
+    if (tile_rows == 0) tile_rows = 4;
+    if (tile_rows != 2 && tile_rows != 4 && tile_rows != 8)
+        return fail(SY_ERR_INVALID_ARGUMENT, "tile_rows %d not in {2, 4, 8}", tile_rows);
+    const int V = static_cast<int>(16 / esize);
+    std::vector<BatchGridDev> desc(n_grids);
+    int64_t tiles = 0, points = 0;
+    for (int g = 0; g < n_grids; ++g) {
+        const sy_batch_grid& G = grids[g];
+        if (G.ny < 1 || G.nx < 1 || G.pitch < G.nx)
+            return fail(SY_ERR_INVALID_ARGUMENT, "grid %d: bad size %lld x %lld (pitch %lld)", g, (long long)G.ny,
+                        (long long)G.nx, (long long)G.pitch);
+        if (G.radius < 1 || G.radius > 4) return fail(SY_ERR_INVALID_ARGUMENT, "grid %d: radius %d", g, G.radius);
+        if (!G.u_a || !G.u_b) return fail(SY_ERR_NULL_POINTER, "grid %d: field pointer is NULL", g);
+        const int64_t pb = G.pitch * static_cast<int64_t>(esize);
+        if ((reinterpret_cast<uintptr_t>(G.u_a) | reinterpret_cast<uintptr_t>(G.u_b)) % 16 || pb % 16)
+            return fail(SY_ERR_INVALID_ARGUMENT,
+                        "grid %d: batched fields need 16-byte aligned rows (base and pitch); use sy_stencil_step", g);
+        const size_t bytes = static_cast<size_t>(G.ny) * static_cast<size_t>(pb);
+        if (ranges_overlap(G.u_a, bytes, G.u_b, bytes)) return fail(SY_ERR_ALIAS, "grid %d: u_a overlaps u_b", g);
+        for (int h = 0; h < g; ++h) {  // grids must not share memory (they are updated concurrently)
+            const size_t hb = static_cast<size_t>(grids[h].ny) * grids[h].pitch * esize;
+            if (ranges_overlap(G.u_a, bytes, grids[h].u_a, hb) || ranges_overlap(G.u_a, bytes, grids[h].u_b, hb) ||
+                ranges_overlap(G.u_b, bytes, grids[h].u_a, hb) || ranges_overlap(G.u_b, bytes, grids[h].u_b, hb))
+                return fail(SY_ERR_ALIAS, "grids %d and %d overlap", h, g);
+        }
+        BatchGridDev& D = desc[g];
+        D.ua = static_cast<char*>(G.u_a);
+        D.ub = static_cast<char*>(G.u_b);
+        D.ny = G.ny;
+        D.nx = G.nx;
+        D.pitch_bytes = pb;
+        D.tiles_x = (G.nx + 32 * V - 1) / (32 * V);
+        D.tile_begin = tiles;
+        D.radius = G.radius;
+        D.c2 = G.c2;
+        tiles += D.tiles_x * ((G.ny + tile_rows - 1) / tile_rows);
+        points += G.ny * G.nx;
+    }
+    SY_TRY(use_device(q));
+    BatchPlan* P = new (std::nothrow) BatchPlan();
+    if (!P) return fail(SY_ERR_OUT_OF_MEMORY, "plan allocation failed");
+    P->q = q;
+    P->dtype = dtype;
+    P->tile_rows = tile_rows;
+    P->n_grids = n_grids;
+    P->total_tiles = tiles;
+    P->points = points;
+    cudaError_t e = cudaMalloc(&P->d_desc, sizeof(BatchGridDev) * desc.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->d_desc, desc.data(), sizeof(BatchGridDev) * desc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        P->stamp_slots = 1;
+        e = cudaMalloc(&P->d_stamps, 4 * sizeof(unsigned long long));
+        P->expected.assign(1, 0);
+    }
+    int occ = 0;
+    const size_t smem = sizeof(int64_t) * static_cast<size_t>(n_grids + 1);
+    if (e == cudaSuccess) {
+        // the step kernel is the larger of the two; size the persistent grid for it
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, reinterpret_cast<const void*>(batch_fn(dtype, tile_rows, false)), kBatchThreads, smem);
+    }
+    if (e != cudaSuccess) {
+        if (P->d_desc) cudaFree(P->d_desc);
+        if (P->d_stamps) cudaFree(P->d_stamps);
+        delete P;
+        return cuda_fail(e, "sy_stencil_batch_plan");
+    }
+    if (occ < 1) occ = 1;
+    int64_t want = (tiles + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+    int64_t cap = static_cast<int64_t>(occ) * q->sm_count;
+    P->blocks = static_cast<int>(want < cap ? want : cap);
+    *out = reinterpret_cast<sy_batch_plan_t>(P);
+    return SY_OK;
+}
+
+sy_status sy_stencil_batch_info(sy_batch_plan_t ph, int64_t* total_tiles, int64_t* points, int* blocks) {
+    if (!ph) return fail(SY_ERR_NULL_POINTER, "plan is NULL");
+    BatchPlan* P = as_plan(ph);
+    if (total_tiles) *total_tiles = P->total_tiles;
+    if (points) *points = P->points;
+    if (blocks) *blocks = P->blocks;
+    return SY_OK;
+}
+
+sy_status sy_stencil_batch_start(sy_batch_plan_t ph, int timed) {
+    if (!ph) return fail(SY_ERR_NULL_POINTER, "plan is NULL");
+    BatchPlan* P = as_plan(ph);
+    SY_TRY(use_device(P->q));
+    if (timed) SY_CUDA(cudaMemsetAsync(P->d_stamps, 0, 4 * sizeof(unsigned long long), P->q->launch));
+    return launch_batch(P, true, 0, timed ? 0 : -1);
+}
+
+sy_status sy_stencil_batch_step(sy_batch_plan_t ph, int parity, int timed) {
+    if (!ph) return fail(SY_ERR_NULL_POINTER, "plan is NULL");
+    BatchPlan* P = as_plan(ph);
+    SY_TRY(use_device(P->q));
+    if (timed) SY_CUDA(cudaMemsetAsync(P->d_stamps, 0, 4 * sizeof(unsigned long long), P->q->launch));
+    return launch_batch(P, false, parity, timed ? 0 : -1);
+}
+
+sy_status sy_stencil_batch_capture(sy_batch_plan_t ph, int64_t steps) {
+    if (!ph) return fail(SY_ERR_NULL_POINTER, "plan is NULL");
+    BatchPlan* P = as_plan(ph);
+    if (steps < 1 || steps > (1 << 20)) return fail(SY_ERR_INVALID_ARGUMENT, "steps = %lld", (long long)steps);
+    Queue* q = P->q;
+    SY_TRY(use_device(q));
+    SY_CUDA(cudaStreamSynchronize(q->stream));
+    if (P->exec) {
+        cudaGraphExecDestroy(P->exec);
+        P->exec = nullptr;
+    }
+    if (P->stamp_slots < steps + 1) {
+        SY_CUDA(cudaFree(P->d_stamps));
+        P->d_stamps = nullptr;
+        SY_CUDA(cudaMalloc(&P->d_stamps, 4 * sizeof(unsigned long long) * static_cast<size_t>(steps + 1)));
+        P->stamp_slots = steps + 1;
+    }
+    P->expected.assign(static_cast<size_t>(steps + 1), 0);
+    const uint64_t launches0 = q->launches;
+    q->launch = q->aux;
+    cudaError_t e = cudaStreamBeginCapture(q->aux, cudaStreamCaptureModeThreadLocal);
+    sy_status st = e == cudaSuccess ? SY_OK : cuda_fail(e, "cudaStreamBeginCapture");
+    if (st == SY_OK) {
+        e = cudaMemsetAsync(P->d_stamps + 4, 0, 4 * sizeof(unsigned long long) * static_cast<size_t>(steps), q->aux);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");
+    }
+    for (int64_t s = 0; st == SY_OK && s < steps; ++s) st = launch_batch(P, false, static_cast<int>(s & 1), 1 + s);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(q->aux, &graph);
+    if (st == SY_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
+    q->launch = q->stream;
+    P->graph_launches = q->launches - launches0;
+    q->launches = launches0;
+    if (st == SY_OK) {
+        e = cudaGraphInstantiate(&P->exec, graph, 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != SY_OK) {
+        if (P->exec) cudaGraphExecDestroy(P->exec);
+        P->exec = nullptr;
+        return st;
+    }
+    P->graph_steps = steps;
+    return SY_OK;
+}
+
+sy_status sy_stencil_batch_run(sy_batch_plan_t ph) {
+    if (!ph) return fail(SY_ERR_NULL_POINTER, "plan is NULL");
+    BatchPlan* P = as_plan(ph);
+    if (!P->exec) return fail(SY_ERR_INVALID_ARGUMENT, "no captured run: call sy_stencil_batch_capture first");
+    SY_TRY(use_device(P->q));
+    SY_CUDA(cudaGraphLaunch(P->exec, P->q->stream));
+    P->q->launches += P->graph_launches;
+    return SY_OK;
+}
+
+sy_status sy_stencil_batch_times(sy_batch_plan_t ph, double* ms, int n) {
+    if (!ph) return fail(SY_ERR_NULL_POINTER, "plan is NULL");
+    BatchPlan* P = as_plan(ph);
+    if (n < 0 || n > P->stamp_slots) return fail(SY_ERR_INVALID_ARGUMENT, "n = %d not in 0..%lld", n,
+                                                 (long long)P->stamp_slots);
+    if (n && !ms) return fail(SY_ERR_NULL_POINTER, "ms is NULL");
+    SY_TRY(use_device(P->q));
+    std::vector<unsigned long long> st(4 * static_cast<size_t>(n));
+    if (n) {
+        SY_CUDA(cudaMemcpyAsync(st.data(), P->d_stamps, st.size() * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, P->q->aux));
+        SY_CUDA(cudaStreamSynchronize(P->q->aux));
+    }
+    for (int i = 0; i < n; ++i) {
+        const unsigned long long* s = &st[4 * static_cast<size_t>(i)];
+        if (P->expected[i] == 0) {
+            ms[i] = 0.0;
+            continue;
+        }
+        if (s[2] != P->expected[i]) return fail(SY_ERR_NOT_READY, "batch launch %d has not completed", i);
+        const unsigned long long start = ~s[0], end = s[1];
+        ms[i] = end > start ? static_cast<double>(end - start) * 1e-6 : 0.0;
+    }
+    return SY_OK;
+}
+
+sy_status sy_stencil_batch_destroy(sy_batch_plan_t ph) {
+    if (!ph) return SY_OK;
+    BatchPlan* P = as_plan(ph);
+    cudaSetDevice(P->q->device);
+    cudaStreamSynchronize(P->q->stream);
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->d_desc) cudaFree(P->d_desc);
+    if (P->d_stamps) cudaFree(P->d_stamps);
+    delete P;
+    return SY_OK;
+}
+
+}  // extern "C"

@@ -192,11 +192,102 @@ __device__ __forceinline__ float update(float u, float up, const float (&vert)[R
     return __fadd_rn(__fsub_rn(__fmul_rn(2.0f, u), up), __fmul_rn(c2, acc));
 }
 
+// One warp's tile: columns [(tx*32 + lane)*V, +V) of each lane, rows
+// [row_begin + ty*RY, +RY) of the chunk [row_begin, row_end), for a field laid
+// out as in `a`.  Shared by the single-field kernel and the batched kernel.
 template <typename S, int R, int RY, bool START>
-__global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
+__device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty, int lane) {
     using T = Traits<S>;
     constexpr int V = T::V;
     static_assert(R <= V, "radius must not exceed the vector width");
+    const int64_t x0 = (tx * 32 + lane) * V;
+    const int64_t y0 = a.row_begin + ty * RY;
+    const bool col_in = x0 < a.nx;
+    const int nvalid = col_in ? static_cast<int>(a.nx - x0 < V ? a.nx - x0 : V) : 0;
+
+    // ---- loads: everything for the tile is in flight before any arithmetic ----
+    uint4 cur[RY + 2 * R];
+#pragma unroll
+    for (int k = 0; k < RY + 2 * R; ++k) {
+        const int64_t row = y0 - R + k;
+        cur[k] = make_uint4(0u, 0u, 0u, 0u);
+        if (col_in && row >= 0 && row < a.ny && row < a.row_end + R)
+            cur[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + x0 * sizeof(S)));
+    }
+    uint4 prev[START ? 1 : RY];
+    if (!START) {
+#pragma unroll
+        for (int k = 0; k < RY; ++k) {
+            const int64_t row = y0 + k;
+            prev[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (col_in && row < a.row_end)
+                prev[k] =
+                    __ldcs(reinterpret_cast<const uint4*>(a.u_prev + row * a.pitch_bytes + x0 * sizeof(S)));
+        }
+    }
+    // warp edges: lane 0 fetches the vector left of the warp, lane 31 the one right of it
+    uint4 edge[RY];
+    const int64_t xe = lane == 0 ? x0 - V : x0 + V;
+    const bool edge_lane = (lane == 0 && xe >= 0) || (lane == 31 && xe < a.nx);
+    const int edge_valid = lane == 0 ? V : static_cast<int>(a.nx - xe < V ? a.nx - xe : V);
+#pragma unroll
+    for (int k = 0; k < RY; ++k) {
+        const int64_t row = y0 + k;
+        edge[k] = make_uint4(0u, 0u, 0u, 0u);
+        if (edge_lane && row < a.row_end)
+            edge[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + xe * sizeof(S)));
+    }
+    if (nvalid < V) {  // only the vector straddling nx (or past it) needs masking
+#pragma unroll
+        for (int k = 0; k < RY + 2 * R; ++k) T::mask(cur[k], nvalid);
+    }
+    if (lane == 31 && edge_valid < V) {
+#pragma unroll
+        for (int k = 0; k < RY; ++k) T::mask(edge[k], edge_valid);
+    }
+
+    // ---- arithmetic and stores, row by row ----
+#pragma unroll
+    for (int k = 0; k < RY; ++k) {
+        const int64_t row = y0 + k;
+        // ext[m] holds column x0 - R + m
+        float ext[V + 2 * R];
+#pragma unroll
+        for (int e = 0; e < V; ++e) ext[R + e] = T::elem(cur[k + R], e);
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+            float from_left = __shfl_up_sync(kFull, ext[R + V - d], 1);
+            float from_right = __shfl_down_sync(kFull, ext[R + d - 1], 1);
+            ext[R - d] = lane == 0 ? T::elem(edge[k], V - d) : from_left;
+            ext[R + V - 1 + d] = lane == 31 ? T::elem(edge[k], d - 1) : from_right;
+        }
+        float out[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            float vert[R], horz[R];
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                vert[d - 1] = __fadd_rn(T::elem(cur[k + R - d], e), T::elem(cur[k + R + d], e));
+                horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+            }
+            const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
+            out[e] = update<R, START>(ext[R + e], up, vert, horz, a.c2);
+        }
+        if (col_in && row < a.row_end) {
+            char* dst = a.u_next + row * a.pitch_bytes + x0 * sizeof(S);
+            if (nvalid == V) {
+                __stcs(reinterpret_cast<uint4*>(dst), T::pack(out));
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (e < nvalid) T::store1(dst + e * sizeof(S), out[e]);
+            }
+        }
+    }
+}
+
+template <typename S, int R, int RY, bool START>
+__global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
     stamp_begin(a.stamp);
     const int lane = threadIdx.x & 31;
     const int64_t warps_per_block = blockDim.x >> 5;
@@ -204,91 +295,7 @@ __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
     for (int64_t t = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); t < a.tiles;
          t += nwarps) {
         const int64_t ty = t / a.tiles_x;
-        const int64_t tx = t - ty * a.tiles_x;
-        const int64_t x0 = (tx * 32 + lane) * V;
-        const int64_t y0 = a.row_begin + ty * RY;
-        const bool col_in = x0 < a.nx;
-        const int nvalid = col_in ? static_cast<int>(a.nx - x0 < V ? a.nx - x0 : V) : 0;
-
-        // ---- loads: everything for the tile is in flight before any arithmetic ----
-        uint4 cur[RY + 2 * R];
-#pragma unroll
-        for (int k = 0; k < RY + 2 * R; ++k) {
-            const int64_t row = y0 - R + k;
-            cur[k] = make_uint4(0u, 0u, 0u, 0u);
-            if (col_in && row >= 0 && row < a.ny && row < a.row_end + R)
-                cur[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + x0 * sizeof(S)));
-        }
-        uint4 prev[START ? 1 : RY];
-        if (!START) {
-#pragma unroll
-            for (int k = 0; k < RY; ++k) {
-                const int64_t row = y0 + k;
-                prev[k] = make_uint4(0u, 0u, 0u, 0u);
-                if (col_in && row < a.row_end)
-                    prev[k] =
-                        __ldcs(reinterpret_cast<const uint4*>(a.u_prev + row * a.pitch_bytes + x0 * sizeof(S)));
-            }
-        }
-        // warp edges: lane 0 fetches the vector left of the warp, lane 31 the one right of it
-        uint4 edge[RY];
-        const int64_t xe = lane == 0 ? x0 - V : x0 + V;
-        const bool edge_lane = (lane == 0 && xe >= 0) || (lane == 31 && xe < a.nx);
-        const int edge_valid = lane == 0 ? V : static_cast<int>(a.nx - xe < V ? a.nx - xe : V);
-#pragma unroll
-        for (int k = 0; k < RY; ++k) {
-            const int64_t row = y0 + k;
-            edge[k] = make_uint4(0u, 0u, 0u, 0u);
-            if (edge_lane && row < a.row_end)
-                edge[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + xe * sizeof(S)));
-        }
-        if (nvalid < V) {  // only the vector straddling nx (or past it) needs masking
-#pragma unroll
-            for (int k = 0; k < RY + 2 * R; ++k) T::mask(cur[k], nvalid);
-        }
-        if (lane == 31 && edge_valid < V) {
-#pragma unroll
-            for (int k = 0; k < RY; ++k) T::mask(edge[k], edge_valid);
-        }
-
-        // ---- arithmetic and stores, row by row ----
-#pragma unroll
-        for (int k = 0; k < RY; ++k) {
-            const int64_t row = y0 + k;
-            // ext[m] holds column x0 - R + m
-            float ext[V + 2 * R];
-#pragma unroll
-            for (int e = 0; e < V; ++e) ext[R + e] = T::elem(cur[k + R], e);
-#pragma unroll
-            for (int d = 1; d <= R; ++d) {
-                float from_left = __shfl_up_sync(kFull, ext[R + V - d], 1);
-                float from_right = __shfl_down_sync(kFull, ext[R + d - 1], 1);
-                ext[R - d] = lane == 0 ? T::elem(edge[k], V - d) : from_left;
-                ext[R + V - 1 + d] = lane == 31 ? T::elem(edge[k], d - 1) : from_right;
-            }
-            float out[V];
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                float vert[R], horz[R];
-#pragma unroll
-                for (int d = 1; d <= R; ++d) {
-                    vert[d - 1] = __fadd_rn(T::elem(cur[k + R - d], e), T::elem(cur[k + R + d], e));
-                    horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
-                }
-                const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
-                out[e] = update<R, START>(ext[R + e], up, vert, horz, a.c2);
-            }
-            if (col_in && row < a.row_end) {
-                char* dst = a.u_next + row * a.pitch_bytes + x0 * sizeof(S);
-                if (nvalid == V) {
-                    __stcs(reinterpret_cast<uint4*>(dst), T::pack(out));
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e)
-                        if (e < nvalid) T::store1(dst + e * sizeof(S), out[e]);
-                }
-            }
-        }
+        wave_tile<S, R, RY, START>(a, t - ty * a.tiles_x, ty, lane);
     }
     stamp_end(a.stamp);
 }
