@@ -39,7 +39,7 @@ RADIUS = 1
 HALO = 1
 C2 = 0.25
 SIGMA = 64.0
-BYTES_PER_UPDATE = 12  # read u^n and u^{n-1}, write u^{n+1} (FP32)
+BYTES_PER_UPDATE = 12  # read u^n and u^{n-1}, write u^{n+1} (FP32; 6 for 16-bit storage)
 METRIC = "stencil GB/s & updates/s (fraction of HBM peak), J/update; learned/batched vs plain"
 WORKLOAD = ("wave2d leapfrog 5-point FP32, 8192x8192, c*dt/dx=0.5, 200 steps, Dirichlet-zero, "
             "Gaussian sigma=64 at centre, 4 row chunks, halo radius 1")
@@ -198,7 +198,7 @@ def run_reference(args) -> None:
 # The other forms of the path, each against the plain form on the same GPU
 # ---------------------------------------------------------------------------
 
-def _metered(q, stream, fn, min_seconds: float = 0.6, min_reps: int = 3):
+def _metered(q, stream, fn, min_seconds: float = 1.0, min_reps: int = 3):
     """Run fn() repeatedly for >= min_seconds inside one NVML metering window;
     returns (reps, device ms per rep, joules or None)."""
     import torch
@@ -350,6 +350,52 @@ def measure_batched(q, stream) -> dict:
             "launches_per_run": {"batched": steps, "per_grid": steps * len(fields)}}
 
 
+def measure_learned(q, stream) -> dict:
+    """The learned cost model, end to end on this GPU: the library tunes a reduced
+    corpus exhaustively (220 shapes), trains its MLP on 80% of the shapes with its own
+    kernels, and reports regret on the held-out 20% for the model and for the default
+    configuration; then the model picks the tile variant of the headline workload
+    (8192^2 FP32, radius 1, 4 chunks) and both picks are timed as whole simulations."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import costmodel, inputs
+
+    shapes = inputs.cost_corpus_shapes(n_stencil=200, n_saxpy=20, side_hi=8192, n_hi=1 << 26)
+    t0 = time.perf_counter()
+    corpus = costmodel.measure(q, shapes, reps=3)
+    t_measure = time.perf_counter() - t0
+    train_ids, test_ids = costmodel.split_shapes(len(shapes))
+    t1 = time.perf_counter()
+    model = costmodel.train(q, corpus, train_ids, epochs=250)
+    t_train = time.perf_counter() - t1
+    res = costmodel.evaluate(q, model, shapes, corpus, test_ids)
+    # choice for the headline workload among the tile variants (chunking fixed at 4)
+    nv = sy.sy_stencil_variant_count(1, sy.SY_F32)
+    infos = [sy.sy_stencil_variant_info(1, sy.SY_F32, v) for v in range(1, nv + 1)]
+    feats = np.stack([sy.sy_cost_features(1, sy.SY_F32, 1, NY, NX, r, c, t, CHUNKS) for r, c, t in infos])
+    pick = 1 + sy.sy_cost_model_choose(model, feats, 0)
+    sy.sy_mlp_destroy(model)
+    u0 = torch.from_numpy(inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), "f32")).cuda()
+    A, B = torch.empty_like(u0), torch.empty_like(u0)
+    chunks = sy.sy_split_rows(NY, CHUNKS)
+    timing = {}
+    for name, variant in (("default", 0), ("learned", pick)):
+        p = sy.stencil_params(NY, NX, 1, C2, "f32", variant=variant)
+        run = lambda: sy.sy_wave_run(q.handle, p, u0, A, B, STEPS, chunks, HALO)
+        run()
+        reps, ms, joules = _metered(q, stream, run)
+        upd = STEPS * NY * NX
+        timing[name] = {"variant": variant, "updates_per_s": upd / (ms * 1e-3),
+                        "j_per_update": None if not joules else joules / (reps * upd)}
+    rows, cols, thr = infos[pick - 1]
+    return {"corpus_rows": int(corpus["X"].shape[0]), "corpus_shapes": len(shapes), "measure_s": t_measure,
+            "train_s": t_train, "held_out_shapes": int(test_ids.size), "regret_model": res["model"],
+            "regret_default": res["default"], "regret_random_expected": res["random_expected_mean"],
+            "headline_pick": {"variant": pick, "tile_rows": rows, "threads": thr}, "headline": timing}
+
+
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
@@ -357,6 +403,13 @@ def measure_batched(q, stream) -> dict:
 def run_gpu(args) -> None:
     import numpy as np
     import torch
+
+    global RADIUS, HALO, BYTES_PER_UPDATE, WORKLOAD
+    if args.radius != 1 or args.dtype != "f32":  # a non-headline variant of the same workload
+        RADIUS = HALO = args.radius
+        BYTES_PER_UPDATE = 3 * (4 if args.dtype == "f32" else 2)
+        WORKLOAD = WORKLOAD.replace("5-point FP32", f"radius-{RADIUS} star, {args.dtype.upper()} storage") \
+                           .replace("halo radius 1", f"halo radius {RADIUS}")
 
     import paper_2505_06022_gb300 as sy
     from paper_2505_06022_gb300 import inputs
@@ -371,11 +424,11 @@ def run_gpu(args) -> None:
 
     stream = torch.cuda.current_stream()
     q = sy.Queue(local, stream)
-    p = sy.stencil_params(NY, NX, RADIUS, C2, "f32")
+    p = sy.stencil_params(NY, NX, RADIUS, C2, args.dtype)
     chunks = sy.sy_split_rows(NY, CHUNKS)
 
-    u0_host = inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), "f32")
-    u0 = torch.from_numpy(u0_host).cuda()  # resident initial field (never overwritten)
+    u0_host = inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), args.dtype)
+    u0 = torch.from_numpy(u0_host if args.dtype == "f32" else u0_host.view(np.int16)).cuda()  # resident, never written
     A = torch.empty_like(u0)
     B = torch.empty_like(u0)
 
@@ -430,7 +483,7 @@ def run_gpu(args) -> None:
     # Roofline of the dominant kernel (the chunked leapfrog step, 800 of the 804
     # launches of a step): algorithmic bytes per launch / average launch duration,
     # both over the CUDA-event-timed region.  The start's 4 launches move 8 B/point.
-    bytes_per_sim = 8 * NY * NX + STEPS * BYTES_PER_UPDATE * NY * NX
+    bytes_per_sim = (2 * BYTES_PER_UPDATE // 3) * NY * NX + STEPS * BYTES_PER_UPDATE * NY * NX
     launches_per_sim = (STEPS + 1) * CHUNKS
     avg_ms = ms_total / (args.steps * launches_per_sim)
     alg_bytes = bytes_per_sim / launches_per_sim
@@ -440,10 +493,11 @@ def run_gpu(args) -> None:
     chunk_bytes = BYTES_PER_UPDATE * (NY // CHUNKS) * NX
     peaks = measured_peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(),
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": ncu_traffic() if (args.dtype == "f32" and RADIUS == 1) else None,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "wave_vec_kernel<float,1,4,false>, one 2048x8192 chunk per launch",
+                "kernel": f"wave_vec_kernel<{args.dtype},{RADIUS},4,false>, one 2048x8192 chunk per launch",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "frac_of_nominal_8000": achieved / 8000.0,
                 "stamp_avg_chunk_ms": statistics.mean(stamp_ms),
@@ -457,7 +511,7 @@ def run_gpu(args) -> None:
     # ---- e2e: host (pinned) initial field in, final field out, through the same API ----
     e2e = None
     if True:
-        h_in = torch.from_numpy(u0_host).pin_memory()
+        h_in = torch.from_numpy(u0_host if args.dtype == "f32" else u0_host.view(np.int16)).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         d_in = torch.empty_like(u0)
         byptr = {A.data_ptr(): A, B.data_ptr(): B, d_in.data_ptr(): d_in}
@@ -478,19 +532,21 @@ def run_gpu(args) -> None:
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1)
         e2e = {"value": world * k_e2e * updates_per_step / (ms_e2e * 1e-3), "unit": "updates/s",
-               "h2d_bytes_per_step": h_in.numel() * 4, "d2h_bytes_per_step": h_out.numel() * 4,
+               "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
+               "d2h_bytes_per_step": h_out.numel() * h_out.element_size(),
                "ms_per_step": ms_e2e / k_e2e}
         # the result must be the physics, not garbage: energy of the final state is finite
         E = sy.sy_wave_energy(q.handle, p, byptr[cv], byptr[pv])[0]
         assert np.isfinite(E) and E > 0
 
     forms = None
-    if rank == 0 and args.forms:
+    if rank == 0 and args.forms and args.dtype == "f32" and RADIUS == 1:
         forms = {"plain_f32": {"updates_per_s": value, "gb_per_s": value * BYTES_PER_UPDATE / 1e9,
                                "j_per_update": None if not energy else energy["j_per_update"]}}
         for dt in ("bf16", "f16"):
             forms[dt] = measure_precision_form(q, stream, dt)
         forms["batched"] = measure_batched(q, stream)
+        forms["learned"] = measure_learned(q, stream)
     if dist:
         dist.barrier()
     if rank == 0:
@@ -498,7 +554,7 @@ def run_gpu(args) -> None:
         line = {
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "updates_per_step": updates_per_step,
                        "launches_per_step": launches // max(1, args.steps),
                        "l2": "inputs larger than L2 (three 256 MiB fields per step, 161 GB moved per step)",
@@ -527,7 +583,12 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sy", choices=["sy", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--forms", type=int, default=1, help="also measure the BF16/FP16 and batched forms (rank 0)")
+    ap.add_argument("--forms", type=int, default=1,
+                    help="also measure the BF16/FP16, batched and learned forms (rank 0, headline workload)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"],
+                    help="field storage of the wave workload (headline: f32)")
+    ap.add_argument("--radius", type=int, default=1, choices=[1, 2, 3, 4],
+                    help="stencil and halo radius of the wave workload (headline: 1)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "sy":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -305,6 +305,109 @@ sy_status sy_stencil_batch_run(sy_batch_plan_t plan);
 sy_status sy_stencil_batch_times(sy_batch_plan_t plan, double* ms, int n);
 sy_status sy_stencil_batch_destroy(sy_batch_plan_t plan);
 
+/* ------------------------------------------------------------------------- */
+/* Learned cost model: a 3-layer MLP trained on the GPU by the library's kernels */
+/* ------------------------------------------------------------------------- */
+/* Not in the paper (whose SYnergy layer picks device frequencies by model-driven
+ * energy targets, §4): here a small MLP predicts (log time, log energy) of a
+ * kernel configuration from its features, and the dispatcher takes the argmin.
+ *   h1 = silu(W1 x + b1), h2 = silu(W2 h1 + b2), y = W3 h2 + b3   (FP32)
+ *   loss = mean over samples and outputs of (y - t)^2, Adam (Kingma & Ba 2015).
+ * Parameter vector: W1[H][F] b1[H] W2[H][H] b2[H] W3[O][H] b3[O] (row-major,
+ * out x in).  Limits: F <= 32, H <= 64, O <= 4.  The model's weights and
+ * training scratch are device buffers owned by the handle. */
+typedef struct sy_mlp_s* sy_mlp_t;
+
+/* New model, weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from `seed`, biases 0,
+ * identity normalisation. */
+sy_status sy_mlp_create(sy_queue_t q, int in_features, int hidden, int out_features, uint64_t seed, sy_mlp_t* out);
+sy_status sy_mlp_destroy(sy_mlp_t m);
+sy_status sy_mlp_param_count(sy_mlp_t m, int64_t* n);
+/* Host copies of the parameters / of the last gradient (n = param count). */
+sy_status sy_mlp_get_params(sy_mlp_t m, float* host, int64_t n);
+sy_status sy_mlp_get_grad(sy_mlp_t m, float* host, int64_t n);
+/* Replace the parameters (and reset Adam's moments). */
+sy_status sy_mlp_set_params(sy_mlp_t m, const float* host, int64_t n);
+/* Raw forward (no normalisation): d_X device B x F (row-major), d_Y device B x O. */
+sy_status sy_mlp_forward(sy_mlp_t m, const float* d_X, int64_t B, float* d_Y);
+/* Forward + backward on device d_X (B x F), d_T (B x O): the gradient of the loss
+ * goes into the model's gradient buffer; *loss (nullable, host) receives the loss
+ * (and then the call synchronises).  The reduction over samples has a fixed shape,
+ * so the gradient is bit-reproducible. */
+sy_status sy_mlp_loss_grad(sy_mlp_t m, const float* d_X, const float* d_T, int64_t B, float* loss);
+/* One Adam step with the current gradient. */
+sy_status sy_mlp_adam_step(sy_mlp_t m, float lr, float beta1, float beta2, float eps);
+/* Train on host arrays X (n x F) and T (n x O): the inputs and targets are
+ * normalised to zero mean / unit variance per column (kept in the model), then
+ * `epochs` passes of Adam (beta 0.9 / 0.999, eps 1e-8) over minibatches of
+ * `batch` samples in an order shuffled per epoch from `seed`.  *final_loss
+ * (nullable) = loss of the last minibatch (normalised units). */
+sy_status sy_mlp_train(sy_mlp_t m, const float* X, const float* T, int64_t n, int epochs, int batch, float lr,
+                       uint64_t seed, float* final_loss);
+/* The model's normalisation vectors (each nullable; F, F, O, O floats). */
+sy_status sy_mlp_normalization(sy_mlp_t m, float* x_mean, float* x_std, float* y_mean, float* y_std);
+/* Predictions in target units for n host feature rows (n x F) -> pred (n x O). */
+sy_status sy_cost_model_predict(sy_mlp_t m, const float* features, int64_t n, float* pred);
+/* Index of the candidate (row of features, n x F) with the smallest predicted
+ * objective: 0 = time (output 0), 1 = energy (output 1), 2 = energy-delay product
+ * (sum of the two log outputs). */
+sy_status sy_cost_model_choose(sy_mlp_t m, const float* features, int n, int objective, int* best);
+/* Save / load a model (parameters and normalisation) as a small binary file. */
+sy_status sy_mlp_save(sy_mlp_t m, const char* path);
+sy_status sy_mlp_load(sy_queue_t q, const char* path, sy_mlp_t* out);
+
+/* ------------------------------------------------------------------------- */
+/* Exhaustive autotuner and cost-model features                                 */
+/* ------------------------------------------------------------------------- */
+/* One measured candidate.  Stencil: variant = tile variant (tile_rows x
+ * tile_cols warp tiles, `threads` per block).  SAXPY: variant = launch variant,
+ * tile_rows = waves of blocks per SM, tile_cols = 4 (floats per access),
+ * threads per block.  ms = median device time of one run over all chunks. */
+typedef struct sy_tune_record {
+    int32_t variant;
+    int32_t tile_rows;
+    int32_t tile_cols;
+    int32_t threads;
+    int32_t chunks;
+    double ms;
+} sy_tune_record;
+
+/* Time every tile variant x chunk count of one stencil step on the caller's
+ * buffers (same rules as sy_stencil_step; halo = radius): one warm-up run and
+ * `reps` timed runs per candidate, device timestamps, median.  out holds at
+ * least variant_count x n_counts records; *n_out receives how many were written.
+ * Synchronises the queue after every run. */
+sy_status sy_tune_stencil(sy_queue_t q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
+                          void* u_next, const int* chunk_counts, int n_counts, int reps, sy_tune_record* out,
+                          int max_out, int* n_out);
+/* The same for SAXPY over n floats (z = 1.5 x + y), launch variant x chunk count. */
+sy_status sy_tune_saxpy(sy_queue_t q, int64_t n, const float* x, const float* y, float* z, const int* chunk_counts,
+                        int n_counts, int reps, sy_tune_record* out, int max_out, int* n_out);
+/* SAXPY launch variants: 1..count; variant 0 is the default of sy_saxpy. */
+sy_status sy_saxpy_variant_count(int* count);
+sy_status sy_saxpy_variant_info(int variant, int* threads, int* waves);
+/* sy_saxpy_split with an explicit launch variant (what a tuner or the cost model chose). */
+sy_status sy_saxpy_config(sy_queue_t q, int64_t n, float alpha, const float* x, const float* y, float* z,
+                          int variant, const sy_chunk* chunks, int n_chunks, sy_event* events);
+
+/* A candidate configuration described for the cost model. */
+typedef struct sy_cost_query {
+    int32_t kind;      /* 0 = SAXPY, 1 = stencil step */
+    int32_t dtype;     /* storage (SAXPY: SY_F32) */
+    int32_t radius;    /* stencil radius (SAXPY: 0) */
+    int64_t ny, nx;    /* grid (SAXPY: ny = 1, nx = n) */
+    int32_t tile_rows; /* as in sy_tune_record */
+    int32_t tile_cols;
+    int32_t threads;
+    int32_t chunks;
+} sy_cost_query;
+#define SY_COST_FEATURES 13
+/* The model's input features of a candidate (SY_COST_FEATURES floats): kind,
+ * log2 bytes/point, flops/point, radius, log2 ny, log2 nx, log2 points,
+ * log2 tile_rows, log2 threads, log2 chunks, log2 total bytes, halo read factor
+ * (tile_rows + 2r) / tile_rows, log2 tile count. */
+sy_status sy_cost_features(const sy_cost_query* query, float* out);
+
 /* Allocation-free form of sy_wave_energy.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the
  * moment they need the energy -- code issuing work while a stream is being

@@ -50,6 +50,20 @@ class BatchGrid(C.Structure):
                 ("c2", C.c_float), ("u_a", C.c_void_p), ("u_b", C.c_void_p)]
 
 
+class TuneRecord(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("tile_rows", C.c_int32), ("tile_cols", C.c_int32),
+                ("threads", C.c_int32), ("chunks", C.c_int32), ("ms", C.c_double)]
+
+
+class CostQuery(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("radius", C.c_int32), ("ny", C.c_int64),
+                ("nx", C.c_int64), ("tile_rows", C.c_int32), ("tile_cols", C.c_int32), ("threads", C.c_int32),
+                ("chunks", C.c_int32)]
+
+
+SY_COST_FEATURES = 13
+
+
 class StencilParams(C.Structure):
     _fields_ = [("ny", C.c_int64), ("nx", C.c_int64), ("pitch", C.c_int64), ("radius", C.c_int32),
                 ("dtype", C.c_int32), ("c2", C.c_float), ("variant", C.c_int32)]
@@ -91,6 +105,27 @@ _SIGS = {
     "sy_stencil_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p, _p],
     "sy_wave_energy": [_p, _p, _p, _p, _p, _p, _p],
     "sy_wave_energy_static": [_p, _p, _p, _p, _p],
+    "sy_tune_stencil": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p],
+    "sy_tune_saxpy": [_p, _i64, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p],
+    "sy_saxpy_variant_count": [_p],
+    "sy_saxpy_variant_info": [C.c_int, _p, _p],
+    "sy_saxpy_config": [_p, _i64, C.c_float, _p, _p, _p, C.c_int, _p, C.c_int, _p],
+    "sy_cost_features": [_p, _p],
+    "sy_mlp_create": [_p, C.c_int, C.c_int, C.c_int, _u64, _p],
+    "sy_mlp_destroy": [_p],
+    "sy_mlp_param_count": [_p, _p],
+    "sy_mlp_get_params": [_p, _p, _i64],
+    "sy_mlp_get_grad": [_p, _p, _i64],
+    "sy_mlp_set_params": [_p, _p, _i64],
+    "sy_mlp_forward": [_p, _p, _i64, _p],
+    "sy_mlp_loss_grad": [_p, _p, _p, _i64, _p],
+    "sy_mlp_adam_step": [_p, C.c_float, C.c_float, C.c_float, C.c_float],
+    "sy_mlp_train": [_p, _p, _p, _i64, C.c_int, C.c_int, C.c_float, _u64, _p],
+    "sy_mlp_normalization": [_p, _p, _p, _p, _p],
+    "sy_cost_model_predict": [_p, _p, _i64, _p],
+    "sy_cost_model_choose": [_p, _p, C.c_int, C.c_int, _p],
+    "sy_mlp_save": [_p, C.c_char_p],
+    "sy_mlp_load": [_p, C.c_char_p, _p],
     "sy_stencil_batch_plan": [_p, _p, C.c_int, C.c_int, C.c_int, _p],
     "sy_stencil_batch_info": [_p, _p, _p, _p],
     "sy_stencil_batch_start": [_p, C.c_int],
@@ -336,6 +371,158 @@ def sy_stencil_batch_times(plan: int, n: int) -> list[float]:
 
 def sy_stencil_batch_destroy(plan: int) -> None:
     _call("sy_stencil_batch_destroy", plan)
+
+
+def _records(arr, n) -> list[dict]:
+    return [{"variant": arr[i].variant, "tile_rows": arr[i].tile_rows, "tile_cols": arr[i].tile_cols,
+             "threads": arr[i].threads, "chunks": arr[i].chunks, "ms": arr[i].ms} for i in range(n)]
+
+
+def sy_tune_stencil(q: int, p: StencilParams, u_prev, u_cur, u_next, chunk_counts=(1, 2, 4, 8), reps: int = 3):
+    counts = (C.c_int * len(chunk_counts))(*chunk_counts)
+    cap = sy_stencil_variant_count(p.radius, p.dtype) * len(chunk_counts)
+    out = (TuneRecord * cap)()
+    n = C.c_int()
+    _call("sy_tune_stencil", q, C.byref(p), _ptr(u_prev), _ptr(u_cur), _ptr(u_next), counts, len(chunk_counts),
+          reps, out, cap, C.byref(n))
+    return _records(out, n.value)
+
+
+def sy_tune_saxpy(q: int, n: int, x, y, z, chunk_counts=(1, 2, 4, 8), reps: int = 3):
+    counts = (C.c_int * len(chunk_counts))(*chunk_counts)
+    cap = sy_saxpy_variant_count() * len(chunk_counts)
+    out = (TuneRecord * cap)()
+    k = C.c_int()
+    _call("sy_tune_saxpy", q, n, _ptr(x), _ptr(y), _ptr(z), counts, len(chunk_counts), reps, out, cap, C.byref(k))
+    return _records(out, k.value)
+
+
+def sy_saxpy_variant_count() -> int:
+    n = C.c_int()
+    _call("sy_saxpy_variant_count", C.byref(n))
+    return n.value
+
+
+def sy_saxpy_variant_info(variant: int) -> tuple[int, int]:
+    t, w = C.c_int(), C.c_int()
+    _call("sy_saxpy_variant_info", variant, C.byref(t), C.byref(w))
+    return t.value, w.value
+
+
+def sy_saxpy_config(q: int, n: int, alpha: float, x, y, z, variant: int, chunks, want_events: bool = False):
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))()
+    _call("sy_saxpy_config", q, n, alpha, _ptr(x), _ptr(y), _ptr(z), variant, arr, k, evs if want_events else None)
+    return list(evs[:k]) if want_events else []
+
+
+def sy_cost_features(kind: int, dtype: int, radius: int, ny: int, nx: int, tile_rows: int, tile_cols: int,
+                     threads: int, chunks: int):
+    import numpy as np
+
+    out = np.empty(SY_COST_FEATURES, np.float32)
+    qy = CostQuery(kind, dtype, radius, ny, nx, tile_rows, tile_cols, threads, chunks)
+    _call("sy_cost_features", C.byref(qy), out.ctypes.data)
+    return out
+
+
+def _f32(a):
+    import numpy as np
+
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def sy_mlp_create(q: int, in_features: int, hidden: int = 64, out_features: int = 2, seed: int = 0) -> int:
+    h = C.c_void_p()
+    _call("sy_mlp_create", q, in_features, hidden, out_features, seed, C.byref(h))
+    return h.value
+
+
+def sy_mlp_destroy(m: int) -> None:
+    _call("sy_mlp_destroy", m)
+
+
+def sy_mlp_param_count(m: int) -> int:
+    n = C.c_int64()
+    _call("sy_mlp_param_count", m, C.byref(n))
+    return n.value
+
+
+def sy_mlp_get_params(m: int):
+    import numpy as np
+
+    out = np.empty(sy_mlp_param_count(m), np.float32)
+    _call("sy_mlp_get_params", m, out.ctypes.data, out.size)
+    return out
+
+
+def sy_mlp_get_grad(m: int):
+    import numpy as np
+
+    out = np.empty(sy_mlp_param_count(m), np.float32)
+    _call("sy_mlp_get_grad", m, out.ctypes.data, out.size)
+    return out
+
+
+def sy_mlp_set_params(m: int, params) -> None:
+    a = _f32(params)
+    _call("sy_mlp_set_params", m, a.ctypes.data, a.size)
+
+
+def sy_mlp_forward(m: int, d_X, B: int, d_Y) -> None:
+    _call("sy_mlp_forward", m, _ptr(d_X), B, _ptr(d_Y))
+
+
+def sy_mlp_loss_grad(m: int, d_X, d_T, B: int, want_loss: bool = True) -> float | None:
+    loss = C.c_float()
+    _call("sy_mlp_loss_grad", m, _ptr(d_X), _ptr(d_T), B, C.byref(loss) if want_loss else None)
+    return loss.value if want_loss else None
+
+
+def sy_mlp_adam_step(m: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    _call("sy_mlp_adam_step", m, lr, beta1, beta2, eps)
+
+
+def sy_mlp_train(m: int, X, T, epochs: int, batch: int, lr: float, seed: int = 0) -> float:
+    Xa, Ta = _f32(X), _f32(T)
+    loss = C.c_float()
+    _call("sy_mlp_train", m, Xa.ctypes.data, Ta.ctypes.data, Xa.shape[0], epochs, batch, lr, seed, C.byref(loss))
+    return loss.value
+
+
+def sy_mlp_normalization(m: int, F: int, O: int):
+    import numpy as np
+
+    xm, xs, ym, ys = (np.empty(F, np.float32), np.empty(F, np.float32), np.empty(O, np.float32),
+                      np.empty(O, np.float32))
+    _call("sy_mlp_normalization", m, xm.ctypes.data, xs.ctypes.data, ym.ctypes.data, ys.ctypes.data)
+    return xm, xs, ym, ys
+
+
+def sy_cost_model_predict(m: int, features, out_features: int = 2):
+    import numpy as np
+
+    F = _f32(features)
+    pred = np.empty((F.shape[0], out_features), np.float32)
+    _call("sy_cost_model_predict", m, F.ctypes.data, F.shape[0], pred.ctypes.data)
+    return pred
+
+
+def sy_cost_model_choose(m: int, features, objective: int = 0) -> int:
+    F = _f32(features)
+    best = C.c_int()
+    _call("sy_cost_model_choose", m, F.ctypes.data, F.shape[0], objective, C.byref(best))
+    return best.value
+
+
+def sy_mlp_save(m: int, path: str) -> None:
+    _call("sy_mlp_save", m, path.encode())
+
+
+def sy_mlp_load(q: int, path: str) -> int:
+    h = C.c_void_p()
+    _call("sy_mlp_load", q, path.encode(), C.byref(h))
+    return h.value
 
 
 def sy_wave_run(q: int, p: StencilParams, u0, u_a, u_b, steps: int, chunks, halo_radius: int,

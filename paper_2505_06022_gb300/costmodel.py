@@ -1,0 +1,233 @@
+"""Learned cost model: corpus, training and regret.
+
+The library measures its own kernels (sy_tune_stencil / sy_tune_saxpy: every
+candidate configuration, device timestamps), turns each candidate into features
+(sy_cost_features), trains its own MLP on the GPU (sy_mlp_train: the library's
+forward/backward/Adam kernels) to predict (log time, log energy), and is judged
+by regret against the exhaustive tuner on held-out shapes:
+
+    regret(shape) = t(candidate the model picks) / t(best measured candidate) - 1
+
+Energy labels: NVML's energy counter ticks every ~100 ms, far coarser than one
+kernel, so each group of kernels with the same kind, storage type and radius gets
+its busy power P from a >= 1 s burst of a representative launch, and a
+candidate's energy is P x its time (the same attribution sy_kernel_energy uses).
+
+Run:  python -m paper_2505_06022_gb300.costmodel [--stencil N] [--saxpy N] [--out corpus.npz]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import (DTYPE_CODES, Queue, SyError, inputs, stencil_params, sy_cost_features, sy_cost_model_predict,
+               sy_meter_begin, sy_meter_end, sy_mlp_create, sy_mlp_destroy, sy_mlp_save, sy_mlp_train,
+               sy_saxpy_variant_info, sy_stencil_step, sy_stencil_variant_info, sy_saxpy, sy_tune_saxpy,
+               sy_tune_stencil)
+
+CHUNK_COUNTS = (1, 2, 4, 8)
+F = 13
+
+
+def default_candidate(kind: int, dtype: str) -> tuple[int, int, int, int]:
+    """(tile_rows, tile_cols, threads, chunks) the library uses without the model."""
+    if kind == 1:
+        rows, cols, thr = sy_stencil_variant_info(1, DTYPE_CODES[dtype], 0)
+        return rows, cols, thr, 1
+    thr, waves = sy_saxpy_variant_info(0)
+    return waves, 4, thr, 1
+
+
+def _pitch(s: dict) -> int:
+    """Row pitch padded to 16 bytes, as an application allocating for the vector kernel would."""
+    v = 4 if s["dtype"] == "f32" else 8
+    return (s["nx"] + v - 1) // v * v
+
+
+def measure(q: Queue, shapes: list[dict], reps: int = 3, log=None) -> dict:
+    """Tune every shape exhaustively; returns feature rows, log-time labels and ids."""
+    import torch
+
+    st_pts = max([s["ny"] * _pitch(s) for s in shapes if s["kind"] == 1] or [1])
+    sx_n = max([s["n"] for s in shapes if s["kind"] == 0] or [1])
+    bufs = [torch.zeros(max(st_pts, sx_n) + 64, dtype=torch.float32, device="cuda") for _ in range(3)]
+    feats, logt, shape_id, meta = [], [], [], []
+    t0 = time.time()
+    for i, s in enumerate(shapes):
+        if s["kind"] == 1:
+            p = stencil_params(s["ny"], s["nx"], s["radius"], 0.25, s["dtype"], pitch=_pitch(s))
+            recs = sy_tune_stencil(q.handle, p, bufs[0], bufs[1], bufs[2], CHUNK_COUNTS, reps)
+            dt = DTYPE_CODES[s["dtype"]]
+            for r in recs:
+                feats.append(sy_cost_features(1, dt, s["radius"], s["ny"], s["nx"], r["tile_rows"], r["tile_cols"],
+                                              r["threads"], r["chunks"]))
+                logt.append(math.log(r["ms"]))
+                shape_id.append(i)
+                meta.append((r["tile_rows"], r["tile_cols"], r["threads"], r["chunks"]))
+        else:
+            recs = sy_tune_saxpy(q.handle, s["n"], bufs[0], bufs[1], bufs[2], CHUNK_COUNTS, reps)
+            for r in recs:
+                feats.append(sy_cost_features(0, 0, 0, 1, s["n"], r["tile_rows"], r["tile_cols"], r["threads"],
+                                              r["chunks"]))
+                logt.append(math.log(r["ms"]))
+                shape_id.append(i)
+                meta.append((r["tile_rows"], r["tile_cols"], r["threads"], r["chunks"]))
+        if log and (i + 1) % 50 == 0:
+            log(f"tuned {i + 1}/{len(shapes)} shapes, {len(logt)} rows, {time.time() - t0:.1f} s")
+    del bufs
+    return {"X": np.asarray(feats, np.float32), "logt": np.asarray(logt, np.float64),
+            "shape": np.asarray(shape_id, np.int64), "cand": np.asarray(meta, np.int64)}
+
+
+def group_power(q: Queue, seconds: float = 1.0) -> dict:
+    """Busy device power (W) per (kind, dtype, radius) group from >= `seconds` bursts."""
+    import torch
+
+    out = {}
+    n = 8192
+    fields = {dt: [torch.zeros(n * n * (4 if dt == "f32" else 2) // 4 + 64, dtype=torch.float32, device="cuda")
+                   for _ in range(3)] for dt in ("f32", "bf16")}
+    for dt in ("f32", "bf16"):
+        for r in (1, 2, 3, 4):
+            p = stencil_params(n, n, r, 0.25, dt)
+            a, b, c = fields[dt]
+            out[(1, dt, r)] = _burst(q, lambda: sy_stencil_step(q.handle, p, a, b, c, [(0, n)], r), seconds)
+    big = 1 << 27
+    x, y, z = (torch.zeros(big, dtype=torch.float32, device="cuda") for _ in range(3))
+    out[(0, "f32", 0)] = _burst(q, lambda: sy_saxpy(q.handle, big, 1.5, x, y, z), seconds)
+    return out
+
+
+def _burst(q: Queue, fn, seconds: float) -> float:
+    import torch
+
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    sy_meter_begin(q.handle)
+    t0 = time.time()
+    while time.time() - t0 < seconds:
+        for _ in range(20):
+            fn()
+        torch.cuda.synchronize()
+    joules, secs = sy_meter_end(q.handle)
+    return joules / secs
+
+
+def energy_labels(shapes, corpus, power: dict) -> np.ndarray:
+    """log J per row = log(P_group * t)."""
+    out = np.empty_like(corpus["logt"])
+    for k, sid in enumerate(corpus["shape"]):
+        s = shapes[sid]
+        key = (s["kind"], s["dtype"], s.get("radius", 0))
+        out[k] = math.log(power[key]) + corpus["logt"][k] - math.log(1e3)
+    return out
+
+
+def split_shapes(n_shapes: int, seed: int = 11, test_fraction: float = 0.2) -> tuple[np.ndarray, np.ndarray]:
+    """Held-out shapes never seen in training: a seeded permutation of the shape ids."""
+    order = np.argsort(inputs.splitmix64(seed, n_shapes))
+    n_test = max(1, int(round(test_fraction * n_shapes)))
+    return np.sort(order[n_test:]), np.sort(order[:n_test])
+
+
+def regret(shapes, corpus, pick) -> dict:
+    """Mean/median/max regret of `pick(rows) -> index into rows` over the shapes in corpus."""
+    regs = []
+    by_kind = {0: [], 1: []}
+    for sid in np.unique(corpus["shape"]):
+        rows = np.nonzero(corpus["shape"] == sid)[0]
+        t = np.exp(corpus["logt"][rows])
+        k = pick(sid, rows)
+        r = t[k] / t.min() - 1.0
+        regs.append(r)
+        by_kind[shapes[sid]["kind"]].append(r)
+    regs = np.asarray(regs)
+    return {"mean": float(regs.mean()), "median": float(np.median(regs)), "p90": float(np.quantile(regs, 0.9)),
+            "max": float(regs.max()), "shapes": int(regs.size),
+            "mean_stencil": float(np.mean(by_kind[1])) if by_kind[1] else None,
+            "mean_saxpy": float(np.mean(by_kind[0])) if by_kind[0] else None}
+
+
+def evaluate(q: Queue, model: int, shapes, corpus, test_ids) -> dict:
+    mask = np.isin(corpus["shape"], test_ids)
+    sub = {k: v[mask] for k, v in corpus.items()}
+    pred = sy_cost_model_predict(model, sub["X"])
+
+    def model_pick(sid, rows):
+        return int(np.argmin(pred[rows, 0]))
+
+    def default_pick(sid, rows):
+        s = shapes[sid]
+        want = default_candidate(s["kind"], s["dtype"])
+        for j, r in enumerate(rows):
+            if tuple(sub["cand"][r]) == want:
+                return j
+        raise KeyError(want)
+
+    def mean_pick(sid, rows):  # expected regret of a uniformly random candidate, as a reference
+        return None
+
+    res = {"model": regret(shapes, sub, model_pick), "default": regret(shapes, sub, default_pick)}
+    # expected regret of a random candidate
+    rr = []
+    for sid in np.unique(sub["shape"]):
+        t = np.exp(sub["logt"][sub["shape"] == sid])
+        rr.append(float(np.mean(t / t.min() - 1.0)))
+    res["random_expected_mean"] = float(np.mean(rr))
+    # log-time prediction error on held-out rows
+    res["held_out_rmse_log_time"] = float(np.sqrt(np.mean((pred[:, 0] - sub["logt"]) ** 2)))
+    return res
+
+
+def train(q: Queue, corpus, train_ids, epochs: int = 300, batch: int = 256, lr: float = 2e-3, seed: int = 7,
+          log_energy: np.ndarray | None = None) -> int:
+    mask = np.isin(corpus["shape"], train_ids)
+    X = corpus["X"][mask]
+    T = np.stack([corpus["logt"][mask], log_energy[mask] if log_energy is not None else corpus["logt"][mask]], 1)
+    model = sy_mlp_create(q.handle, F, 64, 2, seed=seed)
+    sy_mlp_train(model, X, T.astype(np.float32), epochs=epochs, batch=batch, lr=lr, seed=seed)
+    return model
+
+
+def main() -> None:
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--stencil", type=int, default=560)
+    ap.add_argument("--saxpy", type=int, default=40)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--out", default=None, help="save the corpus (npz) here")
+    ap.add_argument("--model", default=None, help="save the trained model here")
+    args = ap.parse_args()
+    torch.cuda.set_device(0)
+    q = Queue(0)
+    shapes = inputs.cost_corpus_shapes(n_stencil=args.stencil, n_saxpy=args.saxpy)
+    t0 = time.time()
+    corpus = measure(q, shapes, reps=args.reps, log=lambda m: print(m, flush=True))
+    t_measure = time.time() - t0
+    power = group_power(q)
+    loge = energy_labels(shapes, corpus, power)
+    train_ids, test_ids = split_shapes(len(shapes))
+    t1 = time.time()
+    model = train(q, corpus, train_ids, epochs=args.epochs, log_energy=loge)
+    t_train = time.time() - t1
+    res = evaluate(q, model, shapes, corpus, test_ids)
+    res.update({"rows": int(corpus["X"].shape[0]), "shapes": len(shapes), "train_shapes": int(train_ids.size),
+                "test_shapes": int(test_ids.size), "measure_s": t_measure, "train_s": t_train,
+                "group_power_w": {f"{k[0]}/{k[1]}/r{k[2]}": v for k, v in power.items()}})
+    if args.out:
+        np.savez(args.out, loge=loge, **corpus)
+    if args.model:
+        sy_mlp_save(model, args.model)
+    sy_mlp_destroy(model)
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

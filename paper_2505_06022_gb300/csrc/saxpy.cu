@@ -17,7 +17,7 @@
 namespace sy {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;  // scalar kernel and the default vector variant
 constexpr int kUnroll = 4;
 
 __device__ __forceinline__ float saxpy1(float alpha, float x, float y) {
@@ -25,12 +25,12 @@ __device__ __forceinline__ float saxpy1(float alpha, float x, float y) {
 }
 
 // Vector body over n4 float4 elements (all three pointers 16-byte aligned).
-__global__ void __launch_bounds__(kThreads) saxpy_vec4_kernel(int64_t n4, float alpha, const float4* x,
-                                                              const float4* y, float4* z,
-                                                              unsigned long long* stamp) {
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) saxpy_vec4_kernel(int64_t n4, float alpha, const float4* x,
+                                                             const float4* y, float4* z, unsigned long long* stamp) {
     stamp_begin(stamp);
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
-    int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * THREADS;
+    int64_t i = static_cast<int64_t>(blockIdx.x) * THREADS + threadIdx.x;
     // Main loop: kUnroll vectors per thread per trip, loads issued before use.
     for (; i + (kUnroll - 1) * stride < n4; i += kUnroll * stride) {
         float4 a[kUnroll], b[kUnroll];
@@ -75,16 +75,39 @@ __global__ void __launch_bounds__(kThreads) saxpy_scalar_kernel(int64_t n, int64
     stamp_end(stamp);
 }
 
-int64_t blocks_for(Queue* q, int64_t work_items) {
-    int64_t want = (work_items + kThreads - 1) / kThreads;
-    int64_t cap = static_cast<int64_t>(q->sm_count) * 8;  // 8 x 256 threads = full SM
+int64_t blocks_for(Queue* q, int64_t work_items, int threads, int waves) {
+    int64_t want = (work_items + threads - 1) / threads;
+    int64_t cap = static_cast<int64_t>(q->sm_count) * (2048 / threads) * waves;  // waves x a full SM
     if (want < 1) want = 1;
     return want < cap ? want : cap;
 }
 
+// Vector-kernel variants: threads in {128, 256, 512} x waves in {1, 2, 4}; 0 = 256 x 1.
+constexpr int kSaxpyThreads[3] = {128, 256, 512};
+constexpr int kSaxpyWaves[3] = {1, 2, 4};
+
 }  // namespace
 
+int saxpy_variant_count() { return 9; }
+
+bool saxpy_variant_info(int variant, int* threads, int* waves) {
+    if (variant < 0 || variant > 9) return false;
+    const int t = variant == 0 ? 256 : kSaxpyThreads[(variant - 1) / 3];
+    const int w = variant == 0 ? 1 : kSaxpyWaves[(variant - 1) % 3];
+    if (threads) *threads = t;
+    if (waves) *waves = w;
+    return true;
+}
+
 sy_status launch_saxpy(Queue* q, int64_t n, float alpha, const float* x, const float* y, float* z) {
+    return launch_saxpy_variant(q, n, alpha, x, y, z, 0);
+}
+
+sy_status launch_saxpy_variant(Queue* q, int64_t n, float alpha, const float* x, const float* y, float* z,
+                               int variant) {
+    int threads = 256, waves = 1;
+    if (!saxpy_variant_info(variant, &threads, &waves))
+        return fail(SY_ERR_INVALID_ARGUMENT, "SAXPY variant %d not in 0..%d", variant, saxpy_variant_count());
     const uintptr_t ax = reinterpret_cast<uintptr_t>(x) & 15u;
     const uintptr_t ay = reinterpret_cast<uintptr_t>(y) & 15u;
     const uintptr_t az = reinterpret_cast<uintptr_t>(z) & 15u;
@@ -96,17 +119,21 @@ sy_status launch_saxpy(Queue* q, int64_t n, float alpha, const float* x, const f
         tail0 = head + 4 * n4;
     }
     if (n4 > 0) {
-        int64_t blocks = blocks_for(q, (n4 + kUnroll - 1) / kUnroll);
-        saxpy_vec4_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, q->launch>>>(
-            n4, alpha, reinterpret_cast<const float4*>(x + head), reinterpret_cast<const float4*>(y + head),
-            reinterpret_cast<float4*>(z + head), q->cur_stamp);
+        const int64_t blocks = blocks_for(q, (n4 + kUnroll - 1) / kUnroll, threads, waves);
+        const float4* x4 = reinterpret_cast<const float4*>(x + head);
+        const float4* y4 = reinterpret_cast<const float4*>(y + head);
+        float4* z4 = reinterpret_cast<float4*>(z + head);
+        const unsigned g = static_cast<unsigned>(blocks);
+        if (threads == 128) saxpy_vec4_kernel<128><<<g, 128, 0, q->launch>>>(n4, alpha, x4, y4, z4, q->cur_stamp);
+        else if (threads == 512) saxpy_vec4_kernel<512><<<g, 512, 0, q->launch>>>(n4, alpha, x4, y4, z4, q->cur_stamp);
+        else saxpy_vec4_kernel<256><<<g, 256, 0, q->launch>>>(n4, alpha, x4, y4, z4, q->cur_stamp);
         SY_CUDA(cudaGetLastError());
         ++q->launches;
         q->cur_blocks += static_cast<uint64_t>(blocks);
     }
     const int64_t scalar = head + (n - tail0);
     if (scalar > 0) {
-        int64_t blocks = blocks_for(q, scalar);
+        const int64_t blocks = blocks_for(q, scalar, kThreads, 1);
         saxpy_scalar_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, q->launch>>>(n, head, tail0, alpha, x, y,
                                                                                       z, q->cur_stamp);
         SY_CUDA(cudaGetLastError());

@@ -130,6 +130,10 @@ size_t dtype_size(int dtype);
 
 // ---- kernel launchers (implemented in the .cu files) -----------------------------
 sy_status launch_saxpy(Queue* q, int64_t n, float alpha, const float* x, const float* y, float* z);
+sy_status launch_saxpy_variant(Queue* q, int64_t n, float alpha, const float* x, const float* y, float* z,
+                               int variant);
+int saxpy_variant_count();
+bool saxpy_variant_info(int variant, int* threads, int* waves);
 
 struct WaveLaunch {
     int64_t ny, nx, pitch;

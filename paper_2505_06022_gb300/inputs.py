@@ -110,3 +110,25 @@ def batch_grids(count: int = 64, seed: int = 1, side_lo: int = 256, side_hi: int
 def batch_initial(H: int, W: int, dtype: str = "f32") -> np.ndarray:
     """Initial field of one batched grid: centred Gaussian with sigma = min(H, W) / 16."""
     return to_storage(gaussian_pulse(H, W, min(H, W) / 16.0), dtype)
+
+
+def cost_corpus_shapes(seed: int = 4, n_stencil: int = 560, n_saxpy: int = 40, side_lo: int = 512,
+                       side_hi: int = 16384, n_lo: int = 1 << 16, n_hi: int = 1 << 28) -> list[dict]:
+    """Synthetic kernel corpus for the cost model.
+
+    Stencils: sides ny, nx log-uniform in [side_lo, side_hi] (independent), radius
+    uniform in 1..4, storage FP32 or BF16 with equal odds.  SAXPY: n log-uniform in
+    [n_lo, n_hi].  Five consecutive outputs of the stream with state `seed` per shape."""
+    z = splitmix64(seed, 5 * (n_stencil + n_saxpy))
+    u = (z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    out = []
+    lo, hi = math.log(side_lo), math.log(side_hi)
+    for s in range(n_stencil):
+        uy, ux, ur, ud = u[5 * s], u[5 * s + 1], u[5 * s + 2], u[5 * s + 3]
+        out.append({"kind": 1, "ny": int(round(math.exp(lo + (hi - lo) * uy))),
+                    "nx": int(round(math.exp(lo + (hi - lo) * ux))), "radius": 1 + int(ur * 4),
+                    "dtype": "f32" if ud < 0.5 else "bf16"})
+    nlo, nhi = math.log(n_lo), math.log(n_hi)
+    for s in range(n_stencil, n_stencil + n_saxpy):
+        out.append({"kind": 0, "n": int(round(math.exp(nlo + (nhi - nlo) * u[5 * s]))), "dtype": "f32"})
+    return out

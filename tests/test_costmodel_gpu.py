@@ -1,0 +1,69 @@
+"""Exhaustive tuner and the learned cost model (a reduced corpus measured by the
+library, an MLP trained on the GPU by the library's kernels), judged by regret on
+shapes held out from training -- and compared with the method without the model
+(the library's default configuration)."""
+import numpy as np
+import pytest
+
+import paper_2505_06022_gb300 as sy
+from paper_2505_06022_gb300 import costmodel, inputs
+
+from gpu_helpers import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def queue():
+    torch_cuda()
+    q = sy.Queue(0)
+    yield q
+    q.close()
+
+
+def test_tuner_records_are_complete_and_sane(queue):
+    torch = torch_cuda()
+    ny, nx = 1024, 2048
+    a, b, c = (torch.zeros(ny, nx, device="cuda") for _ in range(3))
+    p = sy.stencil_params(ny, nx, 2, 0.25, "f32")
+    recs = sy.sy_tune_stencil(queue.handle, p, a, b, c, (1, 4), reps=3)
+    assert len(recs) == 2 * sy.sy_stencil_variant_count(2, sy.SY_F32)
+    assert all(r["ms"] > 0 for r in recs)
+    assert {r["chunks"] for r in recs} == {1, 4}
+    x, y, z = (torch.zeros(1 << 22, device="cuda") for _ in range(3))
+    srec = sy.sy_tune_saxpy(queue.handle, 1 << 22, x, y, z, (1, 2), reps=2)
+    assert len(srec) == 2 * sy.sy_saxpy_variant_count() and all(r["ms"] > 0 for r in srec)
+    # every SAXPY variant computes the same bits
+    xv, yv = inputs.saxpy_inputs(100003, seed=1)
+    xd, yd = torch.from_numpy(xv).cuda(), torch.from_numpy(yv).cuda()
+    ref = None
+    for v in range(0, sy.sy_saxpy_variant_count() + 1):
+        zd = torch.empty_like(xd)
+        sy.sy_saxpy_config(queue.handle, xv.size, 2.5, xd, yd, zd, v, sy.sy_split_rows(xv.size, 3))
+        torch.cuda.synchronize()
+        got = zd.cpu().numpy().view(np.uint32)
+        ref = got if ref is None else ref
+        assert np.array_equal(got, ref)
+
+
+def test_features_are_finite_and_distinguish_candidates():
+    f1 = sy.sy_cost_features(1, sy.SY_F32, 2, 1000, 3000, 4, 128, 256, 1)
+    f2 = sy.sy_cost_features(1, sy.SY_F32, 2, 1000, 3000, 8, 128, 256, 4)
+    f3 = sy.sy_cost_features(0, sy.SY_F32, 0, 1, 1 << 20, 1, 4, 256, 1)
+    assert f1.shape == (sy.SY_COST_FEATURES,) and np.isfinite(np.stack([f1, f2, f3])).all()
+    assert not np.array_equal(f1, f2) and f3[0] == 0 and f1[0] == 1
+
+
+def test_learned_model_beats_the_default_on_held_out_shapes(queue):
+    shapes = inputs.cost_corpus_shapes(n_stencil=200, n_saxpy=20, side_hi=8192, n_hi=1 << 26)
+    corpus = costmodel.measure(queue, shapes, reps=3)
+    train_ids, test_ids = costmodel.split_shapes(len(shapes))
+    model = costmodel.train(queue, corpus, train_ids, epochs=250)
+    try:
+        res = costmodel.evaluate(queue, model, shapes, corpus, test_ids)
+    finally:
+        sy.sy_mlp_destroy(model)
+    # the model's pick is close to the exhaustive optimum and better than the fixed default
+    assert res["model"]["mean"] <= 0.10, res
+    assert res["model"]["mean"] < res["default"]["mean"], res
+    assert res["model"]["mean"] < 0.1 * res["random_expected_mean"], res
