@@ -497,7 +497,8 @@ def run_gpu(args) -> None:
                 "traffic": ncu_traffic() if (args.dtype == "f32" and RADIUS == 1) else None,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": f"wave_vec_kernel<{args.dtype},{RADIUS},4,false>, one 2048x8192 chunk per launch",
+                "kernel": "wave_vec_kernel<{},{},{},false> x {} threads, one 2048x8192 chunk per launch".format(
+                    args.dtype, RADIUS, *sy.sy_stencil_variant_info(RADIUS, sy.DTYPE_CODES[args.dtype], 0)[::2]),
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "frac_of_nominal_8000": achieved / 8000.0,
                 "stamp_avg_chunk_ms": statistics.mean(stamp_ms),

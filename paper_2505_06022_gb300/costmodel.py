@@ -33,10 +33,10 @@ CHUNK_COUNTS = (1, 2, 4, 8)
 F = 13
 
 
-def default_candidate(kind: int, dtype: str) -> tuple[int, int, int, int]:
+def default_candidate(kind: int, dtype: str, radius: int = 1) -> tuple[int, int, int, int]:
     """(tile_rows, tile_cols, threads, chunks) the library uses without the model."""
     if kind == 1:
-        rows, cols, thr = sy_stencil_variant_info(1, DTYPE_CODES[dtype], 0)
+        rows, cols, thr = sy_stencil_variant_info(radius, DTYPE_CODES[dtype], 0)
         return rows, cols, thr, 1
     thr, waves = sy_saxpy_variant_info(0)
     return waves, 4, thr, 1
@@ -163,7 +163,7 @@ def evaluate(q: Queue, model: int, shapes, corpus, test_ids) -> dict:
 
     def default_pick(sid, rows):
         s = shapes[sid]
-        want = default_candidate(s["kind"], s["dtype"])
+        want = default_candidate(s["kind"], s["dtype"], s.get("radius", 1))
         for j, r in enumerate(rows):
             if tuple(sub["cand"][r]) == want:
                 return j

@@ -90,10 +90,12 @@ bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* 
         return false;
     int rows, thr;
     if (variant == 0) {
-        // Default: 4-row tiles, 256-thread blocks (76 registers for r = 1, three
-        // blocks per SM).  Measured best or within 1% of best at 8192^2 for FP32.
-        rows = 4;
-        thr = 256;
+        // Default per storage type and radius: the fastest tile of an exhaustive
+        // sweep at 8192 x 8192 on GB300 (128-thread blocks; rows per tile grow
+        // with the radius, where the halo re-read factor (rows + 2r) / rows matters).
+        static const int kDefaultRows[2][4] = {{2, 4, 8, 4}, {4, 4, 8, 8}};
+        rows = kDefaultRows[dtype == SY_F32 ? 0 : 1][radius - 1];
+        thr = 128;
     } else {
         rows = wave::kTileRows[(variant - 1) % 4];
         thr = wave::kBlockThreads[(variant - 1) / 4];

@@ -125,9 +125,13 @@ struct Traits<__nv_bfloat16> {
     __device__ static __forceinline__ uint32_t bits(float v) {
         return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
     }
+    // two elements per conversion (cvt.rn.bf16x2.f32: each half rounded to nearest even)
+    __device__ static __forceinline__ uint32_t pair(float lo, float hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
     __device__ static __forceinline__ uint4 pack(const float (&v)[V]) {
-        return make_uint4(bits(v[0]) | (bits(v[1]) << 16), bits(v[2]) | (bits(v[3]) << 16),
-                          bits(v[4]) | (bits(v[5]) << 16), bits(v[6]) | (bits(v[7]) << 16));
+        return make_uint4(pair(v[0], v[1]), pair(v[2], v[3]), pair(v[4], v[5]), pair(v[6], v[7]));
     }
     __device__ static __forceinline__ float load1(const char* p) {
         return __uint_as_float(static_cast<uint32_t>(__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
@@ -156,9 +160,13 @@ struct Traits<__half> {
     __device__ static __forceinline__ uint32_t bits(float v) {
         return static_cast<uint32_t>(__half_as_ushort(__float2half_rn(v)));
     }
+    // two elements per conversion (cvt.rn.f16x2.f32: each half rounded to nearest even)
+    __device__ static __forceinline__ uint32_t pair(float lo, float hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
     __device__ static __forceinline__ uint4 pack(const float (&v)[V]) {
-        return make_uint4(bits(v[0]) | (bits(v[1]) << 16), bits(v[2]) | (bits(v[3]) << 16),
-                          bits(v[4]) | (bits(v[5]) << 16), bits(v[6]) | (bits(v[7]) << 16));
+        return make_uint4(pair(v[0], v[1]), pair(v[2], v[3]), pair(v[4], v[5]), pair(v[6], v[7]));
     }
     __device__ static __forceinline__ float load1(const char* p) {
         return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
@@ -194,35 +202,43 @@ __device__ __forceinline__ float update(float u, float up, const float (&vert)[R
 
 // One warp's tile: columns [(tx*32 + lane)*V, +V) of each lane, rows
 // [row_begin + ty*RY, +RY) of the chunk [row_begin, row_end), for a field laid
-// out as in `a`.  Shared by the single-field kernel and the batched kernel.
-template <typename S, int R, int RY, bool START>
-__device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty, int lane) {
+// out as in `a`.  CHECK = false is the interior form, valid when every row the
+// tile reads or writes lies inside the grid and the chunk's range mapper and
+// every lane's V columns lie inside [0, nx): no per-row predicates then.
+template <typename S, int R, int RY, bool START, bool CHECK>
+__device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_t ty, int lane) {
     using T = Traits<S>;
     constexpr int V = T::V;
+    constexpr int64_t ES = sizeof(S);
     static_assert(R <= V, "radius must not exceed the vector width");
+    const int64_t pb = a.pitch_bytes;
     const int64_t x0 = (tx * 32 + lane) * V;
     const int64_t y0 = a.row_begin + ty * RY;
-    const bool col_in = x0 < a.nx;
-    const int nvalid = col_in ? static_cast<int>(a.nx - x0 < V ? a.nx - x0 : V) : 0;
+    const bool col_in = !CHECK || x0 < a.nx;
+    const int nvalid = !CHECK ? V : (col_in ? static_cast<int>(a.nx - x0 < V ? a.nx - x0 : V) : 0);
+    const char* cur_base = a.u_cur + (y0 - R) * pb + x0 * ES;  // row y0 - R
+    const char* prev_base = a.u_prev + y0 * pb + x0 * ES;
 
     // ---- loads: everything for the tile is in flight before any arithmetic ----
     uint4 cur[RY + 2 * R];
 #pragma unroll
     for (int k = 0; k < RY + 2 * R; ++k) {
-        const int64_t row = y0 - R + k;
         cur[k] = make_uint4(0u, 0u, 0u, 0u);
-        if (col_in && row >= 0 && row < a.ny && row < a.row_end + R)
-            cur[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + x0 * sizeof(S)));
+        if (!CHECK) {
+            cur[k] = __ldg(reinterpret_cast<const uint4*>(cur_base + k * pb));
+        } else {
+            const int64_t row = y0 - R + k;
+            if (col_in && row >= 0 && row < a.ny && row < a.row_end + R)
+                cur[k] = __ldg(reinterpret_cast<const uint4*>(cur_base + k * pb));
+        }
     }
     uint4 prev[START ? 1 : RY];
     if (!START) {
 #pragma unroll
         for (int k = 0; k < RY; ++k) {
-            const int64_t row = y0 + k;
             prev[k] = make_uint4(0u, 0u, 0u, 0u);
-            if (col_in && row < a.row_end)
-                prev[k] =
-                    __ldcs(reinterpret_cast<const uint4*>(a.u_prev + row * a.pitch_bytes + x0 * sizeof(S)));
+            if (!CHECK || (col_in && y0 + k < a.row_end))
+                prev[k] = __ldcs(reinterpret_cast<const uint4*>(prev_base + k * pb));
         }
     }
     // warp edges: lane 0 fetches the vector left of the warp, lane 31 the one right of it
@@ -230,14 +246,14 @@ __device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty,
     const int64_t xe = lane == 0 ? x0 - V : x0 + V;
     const bool edge_lane = (lane == 0 && xe >= 0) || (lane == 31 && xe < a.nx);
     const int edge_valid = lane == 0 ? V : static_cast<int>(a.nx - xe < V ? a.nx - xe : V);
+    const char* edge_base = a.u_cur + y0 * pb + xe * ES;
 #pragma unroll
     for (int k = 0; k < RY; ++k) {
-        const int64_t row = y0 + k;
         edge[k] = make_uint4(0u, 0u, 0u, 0u);
-        if (edge_lane && row < a.row_end)
-            edge[k] = __ldg(reinterpret_cast<const uint4*>(a.u_cur + row * a.pitch_bytes + xe * sizeof(S)));
+        if (edge_lane && (!CHECK || y0 + k < a.row_end))
+            edge[k] = __ldg(reinterpret_cast<const uint4*>(edge_base + k * pb));
     }
-    if (nvalid < V) {  // only the vector straddling nx (or past it) needs masking
+    if (CHECK && nvalid < V) {  // only the vector straddling nx (or past it) needs masking
 #pragma unroll
         for (int k = 0; k < RY + 2 * R; ++k) T::mask(cur[k], nvalid);
     }
@@ -247,9 +263,9 @@ __device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty,
     }
 
     // ---- arithmetic and stores, row by row ----
+    char* next_base = a.u_next + y0 * pb + x0 * ES;
 #pragma unroll
     for (int k = 0; k < RY; ++k) {
-        const int64_t row = y0 + k;
         // ext[m] holds column x0 - R + m
         float ext[V + 2 * R];
 #pragma unroll
@@ -273,17 +289,30 @@ __device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty,
             const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
             out[e] = update<R, START>(ext[R + e], up, vert, horz, a.c2);
         }
-        if (col_in && row < a.row_end) {
-            char* dst = a.u_next + row * a.pitch_bytes + x0 * sizeof(S);
-            if (nvalid == V) {
+        if (!CHECK || (col_in && y0 + k < a.row_end)) {
+            char* dst = next_base + k * pb;
+            if (!CHECK || nvalid == V) {
                 __stcs(reinterpret_cast<uint4*>(dst), T::pack(out));
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e)
-                    if (e < nvalid) T::store1(dst + e * sizeof(S), out[e]);
+                    if (e < nvalid) T::store1(dst + e * ES, out[e]);
             }
         }
     }
+}
+
+// Interior tiles (all rows in the grid and the range mapper, all lanes' columns
+// in [0, nx)) take the predicate-free form.
+template <typename S, int R, int RY, bool START>
+__device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty, int lane) {
+    constexpr int V = Traits<S>::V;
+    const int64_t y0 = a.row_begin + ty * RY;
+    const int64_t row_hi = a.row_end + R < a.ny ? a.row_end + R : a.ny;
+    const bool interior = (y0 - R >= 0) && (y0 + RY + R <= row_hi) && (y0 + RY <= a.row_end) &&
+                          ((tx + 1) * 32 * V <= a.nx);
+    if (interior) wave_tile_impl<S, R, RY, START, false>(a, tx, ty, lane);
+    else wave_tile_impl<S, R, RY, START, true>(a, tx, ty, lane);
 }
 
 template <typename S, int R, int RY, bool START>
@@ -292,10 +321,19 @@ __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
     const int lane = threadIdx.x & 31;
     const int64_t warps_per_block = blockDim.x >> 5;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * warps_per_block;
-    for (int64_t t = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); t < a.tiles;
-         t += nwarps) {
-        const int64_t ty = t / a.tiles_x;
-        wave_tile<S, R, RY, START>(a, t - ty * a.tiles_x, ty, lane);
+    const int64_t w = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5);
+    // tile t = w + i * nwarps, as (ty, tx) = divmod(t, tiles_x): two divisions per
+    // warp, then the coordinates advance by (dy, dx) per trip.
+    int64_t ty = w / a.tiles_x, tx = w - ty * a.tiles_x;
+    const int64_t dy = nwarps / a.tiles_x, dx = nwarps - dy * a.tiles_x;
+    for (int64_t t = w; t < a.tiles; t += nwarps) {
+        wave_tile<S, R, RY, START>(a, tx, ty, lane);
+        tx += dx;
+        ty += dy;
+        if (tx >= a.tiles_x) {
+            tx -= a.tiles_x;
+            ++ty;
+        }
     }
     stamp_end(a.stamp);
 }
