@@ -295,7 +295,7 @@ def measure_batched(q, stream) -> dict:
     points = sum(ny * nx for ny, nx, *_ in fields)
     upd = steps * points
     best = None
-    for tile_rows in (2, 4, 8):
+    for tile_rows in (0, 2, 4, 8):
         plan = sy.sy_stencil_batch_plan(q.handle, [(ny, nx, pitch, r, C2, ua, ub) for ny, nx, pitch, r, ua, ub
                                                    in fields], "f32", tile_rows)
         sy.sy_stencil_batch_start(plan)

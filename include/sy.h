@@ -279,7 +279,8 @@ typedef struct sy_batch_grid {
 typedef struct sy_batch_plan_s* sy_batch_plan_t;
 
 /* Build a plan over n_grids (1..4096) grids of one dtype.  tile_rows: tile height
- * of the warp tiles, 2, 4 or 8 (0 = 4).  The grids' buffers must not overlap each
+ * of the warp tiles, 2, 4 or 8 for every grid, or 0 for a height per grid (2 rows
+ * for FP32 radius 1, else 4).  The grids' buffers must not overlap each
  * other.  The plan copies the descriptors to the device; the buffers stay owned by
  * the caller and must outlive the plan. */
 sy_status sy_stencil_batch_plan(sy_queue_t q, const sy_batch_grid* grids, int n_grids, int dtype, int tile_rows,

@@ -46,14 +46,44 @@ struct BatchPlan {
     int64_t graph_steps = 0;
     uint64_t graph_launches = 0;
     int blocks = 0;                          // persistent grid size
-    int threads = 256;
+    int threads = 128;
 };
 
 namespace {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 128;
 constexpr int kMaxBatchGrids = 4096;  // prefix sums in shared memory: 32 KiB
 
+// Tile height per radius when the plan asks for the default (tile_rows = 0): 2 rows
+// for FP32 radius 1, else 4.  One kernel carries every radius, so its register
+// budget is that of its largest branch; 4-row tiles keep every branch within 128
+// registers (four 128-thread blocks per SM).
+template <typename S, int R>
+struct AutoRows {
+    static constexpr int value = (sizeof(S) == 4 && R == 1) ? 2 : 4;
+};
+
+template <typename S, int R, int RY, bool START>
+__device__ __forceinline__ void batch_tile(const BatchGridDev& G, int parity, int64_t tx, int64_t ty, int lane) {
+    wave::Args a;
+    const bool swap = (parity & 1) != 0;
+    a.u_prev = swap ? G.ub : G.ua;
+    a.u_cur = START ? G.ub : (swap ? G.ua : G.ub);
+    a.u_next = START ? G.ua : (swap ? G.ub : G.ua);
+    a.ny = G.ny;
+    a.nx = G.nx;
+    a.pitch_bytes = G.pitch_bytes;
+    a.row_begin = 0;
+    a.row_end = G.ny;
+    a.tiles_x = G.tiles_x;
+    a.tiles = 0;
+    a.c2 = START ? 0.5f * G.c2 : G.c2;
+    a.stamp = nullptr;
+    wave::wave_tile<S, R, RY, START>(a, tx, ty, lane);
+}
+
+// RY > 0: every grid uses RY-row tiles; RY == 0: each grid uses AutoRows for its radius
+// (the plan computed tiles_x / tile_begin with the same heights).
 template <typename S, int RY, bool START>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev* __restrict__ grids, int n_grids,
                                                               int64_t total_tiles, int parity,
@@ -65,37 +95,38 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev
     const int lane = threadIdx.x & 31;
     const int64_t warps_per_block = blockDim.x >> 5;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * warps_per_block;
+    int g = -1;
+    int64_t tx = 0, ty = 0, dx = 0, dy = 0, tiles_x = 1;
     for (int64_t t = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); t < total_tiles;
          t += nwarps) {
-        int lo = 0, hi = n_grids - 1;  // largest g with s_begin[g] <= t (warp-uniform)
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_begin[mid] <= t) lo = mid;
-            else hi = mid - 1;
+        if (g >= 0 && t < s_begin[g + 1]) {  // same grid: advance the coordinates
+            tx += dx;
+            ty += dy;
+            if (tx >= tiles_x) {
+                tx -= tiles_x;
+                ++ty;
+            }
+        } else {  // entered another grid: find it (warp-uniform binary search) and divide once
+            int lo = g < 0 ? 0 : g, hi = n_grids - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_begin[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            g = lo;
+            tiles_x = grids[g].tiles_x;
+            const int64_t local = t - s_begin[g];
+            ty = local / tiles_x;
+            tx = local - ty * tiles_x;
+            dy = nwarps / tiles_x;
+            dx = nwarps - dy * tiles_x;
         }
-        const BatchGridDev& G = grids[lo];
-        wave::Args a;
-        const bool swap = (parity & 1) != 0;
-        a.u_prev = swap ? G.ub : G.ua;
-        a.u_cur = START ? G.ub : (swap ? G.ua : G.ub);
-        a.u_next = START ? G.ua : (swap ? G.ub : G.ua);
-        a.ny = G.ny;
-        a.nx = G.nx;
-        a.pitch_bytes = G.pitch_bytes;
-        a.row_begin = 0;
-        a.row_end = G.ny;
-        a.tiles_x = G.tiles_x;
-        a.tiles = 0;
-        a.c2 = START ? 0.5f * G.c2 : G.c2;
-        a.stamp = nullptr;
-        const int64_t local = t - s_begin[lo];
-        const int64_t ty = local / G.tiles_x;
-        const int64_t tx = local - ty * G.tiles_x;
+        const BatchGridDev& G = grids[g];
         switch (G.radius) {
-            case 1: wave::wave_tile<S, 1, RY, START>(a, tx, ty, lane); break;
-            case 2: wave::wave_tile<S, 2, RY, START>(a, tx, ty, lane); break;
-            case 3: wave::wave_tile<S, 3, RY, START>(a, tx, ty, lane); break;
-            default: wave::wave_tile<S, 4, RY, START>(a, tx, ty, lane); break;
+            case 1: batch_tile<S, 1, RY ? RY : AutoRows<S, 1>::value, START>(G, parity, tx, ty, lane); break;
+            case 2: batch_tile<S, 2, RY ? RY : AutoRows<S, 2>::value, START>(G, parity, tx, ty, lane); break;
+            case 3: batch_tile<S, 3, RY ? RY : AutoRows<S, 3>::value, START>(G, parity, tx, ty, lane); break;
+            default: batch_tile<S, 4, RY ? RY : AutoRows<S, 4>::value, START>(G, parity, tx, ty, lane); break;
         }
     }
     stamp_end(stamp);
@@ -106,10 +137,17 @@ using BatchFn = void (*)(const BatchGridDev*, int, int64_t, int, unsigned long l
 template <typename S, bool START>
 BatchFn pick_batch(int tile_rows) {
     switch (tile_rows) {
+        case 0: return batch_kernel<S, 0, START>;
         case 2: return batch_kernel<S, 2, START>;
         case 8: return batch_kernel<S, 8, START>;
         default: return batch_kernel<S, 4, START>;
     }
+}
+
+// Tile height a plan with `tile_rows` uses for a grid of radius r and element size es.
+int rows_for(int tile_rows, int radius, size_t es) {
+    if (tile_rows) return tile_rows;
+    return (es == 4 && radius == 1) ? 2 : 4;
 }
 
 BatchFn batch_fn(int dtype, int tile_rows, bool start) {
@@ -154,9 +192,8 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
     if (!grids) return fail(SY_ERR_NULL_POINTER, "grids is NULL");
     const size_t esize = dtype_size(dtype);
     if (!esize) return fail(SY_ERR_INVALID_ARGUMENT, "unknown dtype %d", dtype);
-    if (tile_rows == 0) tile_rows = 4;
-    if (tile_rows != 2 && tile_rows != 4 && tile_rows != 8)
-        return fail(SY_ERR_INVALID_ARGUMENT, "tile_rows %d not in {2, 4, 8}", tile_rows);
+    if (tile_rows != 0 && tile_rows != 2 && tile_rows != 4 && tile_rows != 8)
+        return fail(SY_ERR_INVALID_ARGUMENT, "tile_rows %d not in {0, 2, 4, 8}", tile_rows);
     const int V = static_cast<int>(16 / esize);
     std::vector<BatchGridDev> desc(n_grids);
     int64_t tiles = 0, points = 0;
@@ -189,7 +226,8 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
         D.tile_begin = tiles;
         D.radius = G.radius;
         D.c2 = G.c2;
-        tiles += D.tiles_x * ((G.ny + tile_rows - 1) / tile_rows);
+        const int rows = rows_for(tile_rows, G.radius, esize);
+        tiles += D.tiles_x * ((G.ny + rows - 1) / rows);
         points += G.ny * G.nx;
     }
     SY_TRY(use_device(q));

@@ -305,6 +305,7 @@ sy_status sy::stencil_common(Queue* q, const sy_stencil_params* p, const void* u
         w.u_next = u_next;
         w.row_begin = chunks[c].begin;
         w.row_end = chunks[c].end;
+        w.pdl = c == 0 ? 1 : 2;
         SY_TRY(launch_wave(q, w));
         SY_TRY(end_event(q, rec));
     }

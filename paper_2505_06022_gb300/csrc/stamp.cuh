@@ -29,4 +29,12 @@ __device__ __forceinline__ void stamp_end(unsigned long long* s) {
     }
 }
 
+// Programmatic dependent launch (griddepcontrol): a kernel launched with the
+// programmatic-stream-serialisation attribute may start while its predecessor on
+// the stream is still running.  wait blocks until the predecessor grid has
+// completed and its writes are visible (it returns at once for a kernel launched
+// without the attribute); launch_dependents lets the next such kernel launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace sy

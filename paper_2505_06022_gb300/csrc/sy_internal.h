@@ -142,6 +142,7 @@ struct WaveLaunch {
     int variant;
     float c2;        // coefficient of L u (c2, or c2/2 for the start)
     bool start;      // Taylor start: u + c2 * L u, no u_prev
+    int pdl;         // overlap with the previous launch: 0 none, 1 first chunk of a step, 2 later chunk
     const void* u_prev;
     const void* u_cur;
     void* u_next;

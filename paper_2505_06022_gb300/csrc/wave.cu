@@ -7,6 +7,7 @@
 // fixed arithmetic progression of points, a fixed shared-memory tree per block,
 // then one block summing the partials in a fixed tree), so the result does not
 // depend on scheduling: repeated calls give identical bits.
+#include <cstdlib>
 #include <mutex>
 #include <unordered_map>
 
@@ -35,6 +36,15 @@ int occupancy(KernelFn fn, int threads) {
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Programmatic dependent launch of the chunk kernels; SY_PDL=0 turns it off.
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("SY_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 }  // namespace
 
 sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn scalar_fn, int tile_rows,
@@ -52,6 +62,7 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
     a.row_end = w.row_end;
     a.c2 = w.c2;
     a.stamp = q->cur_stamp;
+    a.pdl = 0;
     if (!aligned(w.u_cur, esize) || !aligned(w.u_next, esize) || (!w.start && !aligned(w.u_prev, esize)))
         return fail(SY_ERR_INVALID_ARGUMENT, "field pointers must be aligned to the element size (%zu bytes)", esize);
     const bool vec_ok = aligned(w.u_cur, 16) && aligned(w.u_next, 16) && (w.start || aligned(w.u_prev, 16)) &&
@@ -63,8 +74,23 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
         const int64_t wpb = threads / 32;
         int64_t blocks = (a.tiles + wpb - 1) / wpb;
         const int64_t cap = static_cast<int64_t>(occupancy(vec_fn, threads)) * q->sm_count;
-        if (blocks > cap) blocks = cap;
-        vec_fn<<<static_cast<unsigned>(blocks), threads, 0, q->launch>>>(a);
+        if (blocks > cap) blocks = cap;  // persistent: every block resident at once
+        if (w.pdl && pdl_enabled()) {
+            a.pdl = w.pdl;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+            cfg.blockDim = dim3(threads);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = q->launch;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            SY_CUDA(cudaLaunchKernelEx(&cfg, vec_fn, a));
+        } else {
+            vec_fn<<<static_cast<unsigned>(blocks), threads, 0, q->launch>>>(a);
+        }
         q->cur_blocks += static_cast<uint64_t>(blocks);
     } else {
         a.tiles_x = 0;

@@ -188,6 +188,13 @@ struct Args {
     int64_t tiles_x, tiles;  // vector kernel: tiles per row band, total tiles
     float c2;                // coefficient of L u
     unsigned long long* stamp;  // timestamp slot of this launch, or null
+    // Launch overlap with the previous kernel on the stream (programmatic dependent
+    // launch): 0 = none; 1 = first chunk of a step: wait for the predecessor before
+    // touching memory; 2 = later chunk of the same step: independent of the chunks
+    // before it (disjoint rows written, earlier steps' buffers read), no entry wait.
+    // With 1 or 2 the block's first thread also waits at exit, so that a launch's
+    // completion implies its predecessor's and the chain is transitive.
+    int pdl;
 };
 
 // One output point from its neighbourhood, in the canonical operation order.
@@ -317,6 +324,8 @@ __device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty,
 
 template <typename S, int R, int RY, bool START>
 __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
+    if (a.pdl == 1) griddep_wait();
+    if (a.pdl) griddep_launch_dependents();
     stamp_begin(a.stamp);
     const int lane = threadIdx.x & 31;
     const int64_t warps_per_block = blockDim.x >> 5;
@@ -336,6 +345,7 @@ __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
         }
     }
     stamp_end(a.stamp);
+    if (a.pdl && threadIdx.x == 0) griddep_wait();
 }
 
 // One point per thread; any element-aligned layout.

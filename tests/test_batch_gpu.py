@@ -57,7 +57,7 @@ SMALL = [(8, 8, 1), (1, 1, 2), (37, 300, 4), (64, 129, 3), (5, 1030, 1), (130, 4
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
-@pytest.mark.parametrize("tile_rows", [2, 4, 8])
+@pytest.mark.parametrize("tile_rows", [0, 2, 4, 8])
 def test_batch_steps_bit_exact_vs_oracle(q, dtype, tile_rows):
     torch = torch_cuda()
     host, dev = make_grids(SMALL, dtype)
