@@ -258,6 +258,54 @@ sy_status sy_wave_energy(sy_queue_t q, const sy_stencil_params* p, const void* u
                          double* energy, double* kinetic, double* potential);
 
 /* ------------------------------------------------------------------------- */
+/* Data transfers inferred from range mappers; split-buffer execution           */
+/* ------------------------------------------------------------------------- */
+/* paper §3: the runtime splits a kernel across devices and uses the range
+ * mappers to infer the data transfers each chunk needs before it runs.  For the
+ * neighbourhood mapper of halo radius h, chunk c = [a, b) reads [a - h, b + h)
+ * clipped to [0, ny); the rows it does not write are moved from the chunks that
+ * write them, one transfer per run of rows with a single owner. */
+typedef struct sy_transfer {
+    int32_t src;       /* chunk that owns (writes) the rows */
+    int32_t dst;       /* chunk that reads them */
+    int64_t row_begin; /* global rows [row_begin, row_end) */
+    int64_t row_end;
+} sy_transfer;
+
+/* All transfers for a chunk list, in order of destination chunk (rows above, then
+ * below).  out = NULL only counts (*n_out). */
+sy_status sy_rm_transfers(int64_t ny, const sy_chunk* chunks, int n_chunks, int halo_radius, sy_transfer* out,
+                          int max_out, int* n_out);
+
+/* Local buffer of chunk c in split-buffer mode: halo_lo = min(h, begin) rows above
+ * its own rows, halo_hi = min(h, ny - end) rows below; local_rows = halo_lo +
+ * (end - begin) + halo_hi rows of p->pitch elements.  (Each pointer nullable.) */
+sy_status sy_split_layout(int64_t ny, const sy_chunk* chunks, int n_chunks, int halo_radius, int chunk,
+                          int64_t* halo_lo, int64_t* halo_hi, int64_t* local_rows);
+
+/* One step with every chunk's fields in buffers of its own (the layout above), as
+ * chunks on separate devices would hold them: first the inferred halo rows of
+ * u_cur are copied between the chunks' buffers (device to device), then each
+ * chunk's rows are stepped.  local_prev / local_cur / local_next: arrays of n_chunks
+ * device pointers; p describes the global grid.  Aliasing rules per chunk as in
+ * sy_stencil_step.  Bit-identical to sy_stencil_step on one shared buffer. */
+sy_status sy_stencil_step_split(sy_queue_t q, const sy_stencil_params* p, void* const* local_prev,
+                                void* const* local_cur, void* const* local_next, const sy_chunk* chunks,
+                                int n_chunks, int halo_radius, sy_event* chunk_events);
+/* One chunk on its own: step rows [row_begin, row_end) of the grid in p, reading
+ * [row_begin - r, row_end + r) clipped (the neighbourhood range mapper), with no
+ * requirement that other chunks exist -- the kernel a device runs on the chunk it
+ * holds (its halo rows having been brought in by the caller).  start != 0 runs the
+ * Taylor start instead (u_prev unused).  Same aliasing rules as sy_stencil_step. */
+sy_status sy_stencil_step_rows(sy_queue_t q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
+                               void* u_next, int64_t row_begin, int64_t row_end, int halo_radius, int start,
+                               sy_event* ev);
+/* The Taylor start in split-buffer mode (halos of u0 refreshed first). */
+sy_status sy_stencil_start_split(sy_queue_t q, const sy_stencil_params* p, void* const* local_u0,
+                                 void* const* local_um1, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                                 sy_event* chunk_events);
+
+/* ------------------------------------------------------------------------- */
 /* Batched stencils: many independent, unevenly sized grids in one launch     */
 /* ------------------------------------------------------------------------- */
 /* Each grid is advanced with the stencil of sy_stencil_step over its whole row

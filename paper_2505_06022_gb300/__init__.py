@@ -64,6 +64,10 @@ class CostQuery(C.Structure):
 SY_COST_FEATURES = 13
 
 
+class Transfer(C.Structure):
+    _fields_ = [("src", C.c_int32), ("dst", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64)]
+
+
 class StencilParams(C.Structure):
     _fields_ = [("ny", C.c_int64), ("nx", C.c_int64), ("pitch", C.c_int64), ("radius", C.c_int32),
                 ("dtype", C.c_int32), ("c2", C.c_float), ("variant", C.c_int32)]
@@ -105,6 +109,11 @@ _SIGS = {
     "sy_stencil_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p, _p],
     "sy_wave_energy": [_p, _p, _p, _p, _p, _p, _p],
     "sy_wave_energy_static": [_p, _p, _p, _p, _p],
+    "sy_rm_transfers": [_i64, _p, C.c_int, C.c_int, _p, C.c_int, _p],
+    "sy_split_layout": [_i64, _p, C.c_int, C.c_int, C.c_int, _p, _p, _p],
+    "sy_stencil_step_split": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
+    "sy_stencil_start_split": [_p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
+    "sy_stencil_step_rows": [_p, _p, _p, _p, _p, _i64, _i64, C.c_int, C.c_int, _p],
     "sy_tune_stencil": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p],
     "sy_tune_saxpy": [_p, _i64, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p],
     "sy_saxpy_variant_count": [_p],
@@ -371,6 +380,50 @@ def sy_stencil_batch_times(plan: int, n: int) -> list[float]:
 
 def sy_stencil_batch_destroy(plan: int) -> None:
     _call("sy_stencil_batch_destroy", plan)
+
+
+def sy_rm_transfers(ny: int, chunks, halo_radius: int) -> list[tuple[int, int, int, int]]:
+    """[(src, dst, row_begin, row_end)] inferred from the neighbourhood range mappers."""
+    arr, k = _chunks(chunks)
+    n = C.c_int()
+    _call("sy_rm_transfers", ny, arr, k, halo_radius, None, 0, C.byref(n))
+    out = (Transfer * max(1, n.value))()
+    _call("sy_rm_transfers", ny, arr, k, halo_radius, out, n.value, C.byref(n))
+    return [(out[i].src, out[i].dst, out[i].row_begin, out[i].row_end) for i in range(n.value)]
+
+
+def sy_split_layout(ny: int, chunks, halo_radius: int, chunk: int) -> tuple[int, int, int]:
+    arr, k = _chunks(chunks)
+    lo, hi, rows = C.c_int64(), C.c_int64(), C.c_int64()
+    _call("sy_split_layout", ny, arr, k, halo_radius, chunk, C.byref(lo), C.byref(hi), C.byref(rows))
+    return lo.value, hi.value, rows.value
+
+
+def _ptr_list(ts):
+    return (C.c_void_p * max(1, len(ts)))(*[_ptr(t) for t in ts])
+
+
+def sy_stencil_step_split(q: int, p: StencilParams, local_prev, local_cur, local_next, chunks, halo_radius: int,
+                          want_events: bool = False) -> list[int]:
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))()
+    _call("sy_stencil_step_split", q, C.byref(p), _ptr_list(local_prev), _ptr_list(local_cur),
+          _ptr_list(local_next), arr, k, halo_radius, evs if want_events else None)
+    return list(evs[:k]) if want_events else []
+
+
+def sy_stencil_start_split(q: int, p: StencilParams, local_u0, local_um1, chunks, halo_radius: int) -> None:
+    arr, k = _chunks(chunks)
+    _call("sy_stencil_start_split", q, C.byref(p), _ptr_list(local_u0), _ptr_list(local_um1), arr, k,
+          halo_radius, None)
+
+
+def sy_stencil_step_rows(q: int, p: StencilParams, u_prev, u_cur, u_next, row_begin: int, row_end: int,
+                         halo_radius: int, start: bool = False, want_event: bool = False) -> int:
+    ev = C.c_uint64()
+    _call("sy_stencil_step_rows", q, C.byref(p), _ptr(u_prev), _ptr(u_cur), _ptr(u_next), row_begin, row_end,
+          halo_radius, int(start), C.byref(ev) if want_event else None)
+    return ev.value
 
 
 def _records(arr, n) -> list[dict]:

@@ -1,0 +1,85 @@
+"""Split-buffer execution on the GPU: every chunk in a buffer of its own, halos
+moved by the transfers the range mappers infer (device-to-device copies).  Must be
+bit-identical to the oracle (and so to the shared-buffer mode)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2505_06022_gb300 as sy
+from paper_2505_06022_gb300 import inputs
+
+from gpu_helpers import bits, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+DT = {"f32": oracle.F32, "bf16": oracle.BF16, "f16": oracle.F16}
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch_cuda()
+    with sy.Queue(0) as queue:
+        yield queue.handle
+
+
+def to_local(u, chunks, h, c, pitch, tdt, torch):
+    ny = u.shape[0]
+    lo, hi, rows = sy.sy_split_layout(ny, chunks, h, c)
+    a, b = chunks[c]
+    buf = torch.zeros(rows, pitch, dtype=tdt, device="cuda")
+    src = u if u.dtype == np.float32 else u.view(np.int16)
+    buf[lo: lo + (b - a), : u.shape[1]] = torch.from_numpy(np.ascontiguousarray(src[a:b])).cuda()
+    return buf
+
+
+@pytest.mark.parametrize("dtype,r,h,ny,nx,chunks", [
+    ("f32", 1, 1, 64, 300, None),
+    ("f32", 2, 3, 37, 129, [(0, 1), (1, 3), (3, 30), (30, 37)]),     # chunks shorter than the halo
+    ("bf16", 4, 4, 50, 520, [(0, 20), (20, 22), (22, 50)]),
+    ("f16", 3, 3, 33, 70, [(0, 33)]),
+])
+def test_split_buffers_bit_exact(q, dtype, r, h, ny, nx, chunks):
+    torch = torch_cuda()
+    chunks = chunks or sy.sy_split_rows(ny, 4)
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 6.0) + 0.05 * inputs.random_field(3, ny, nx), dtype)
+    tdt = torch.float32 if dtype == "f32" else torch.int16
+    pitch = (nx + 7) // 8 * 8
+    cur = [to_local(u0, chunks, h, c, pitch, tdt, torch) for c in range(len(chunks))]
+    prev = [torch.zeros_like(t) for t in cur]
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype, pitch=pitch)
+    sy.sy_stencil_start_split(q, p, cur, prev, chunks, h)
+    steps = 8
+    for _ in range(steps):
+        sy.sy_stencil_step_split(q, p, prev, cur, prev, chunks, h)
+        prev, cur = cur, prev
+    torch.cuda.synchronize()
+    got = []
+    for c, (a, b) in enumerate(chunks):
+        lo, _, _ = sy.sy_split_layout(ny, chunks, h, c)
+        part = cur[c][lo: lo + (b - a), :nx].cpu().numpy()
+        got.append(part if dtype == "f32" else part.view(np.uint16))
+    _, want = oracle.wave_run_mirror(DT[dtype], u0, steps, r, 0.25)
+    assert np.array_equal(bits(np.ascontiguousarray(np.concatenate(got))), bits(want))
+
+
+def test_step_rows_matches_chunked_step(q):
+    torch = torch_cuda()
+    ny, nx, r = 90, 256, 2
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 9.0), "f32")
+    cur = torch.from_numpy(u0).cuda()
+    prev = torch.empty_like(cur)
+    p = sy.stencil_params(ny, nx, r, 0.25, "f32")
+    for a, b in [(0, 31), (31, 32), (32, 90)]:  # the same rows as a chunk list, one call each
+        sy.sy_stencil_step_rows(q, p, None, cur, prev, a, b, r, start=True)
+    nxt = torch.empty_like(cur)
+    for a, b in [(0, 45), (45, 90)]:
+        sy.sy_stencil_step_rows(q, p, prev, cur, nxt, a, b, r)
+    torch.cuda.synchronize()
+    op, oc = oracle.wave_run_mirror(oracle.F32, u0, 1, r, 0.25)
+    assert np.array_equal(nxt.cpu().numpy().view(np.uint32), oc.view(np.uint32))
+    with pytest.raises(sy.SyError) as e:
+        sy.sy_stencil_step_rows(q, p, prev, cur, nxt, 10, 91, r)
+    assert e.value.name == "SY_ERR_BAD_CHUNKS"
+    with pytest.raises(sy.SyError) as e:
+        sy.sy_stencil_step_rows(q, p, prev, cur, nxt, 0, 10, 1)
+    assert e.value.name == "SY_ERR_HALO_TOO_SMALL"
