@@ -95,7 +95,8 @@ int sy_abi_version(void);
  * creation (for sy_device_energy) when NVML is available. */
 sy_status sy_queue_create(int device, void* cuda_stream, sy_queue_t* out);
 sy_status sy_queue_destroy(sy_queue_t q);
-/* Block until all work submitted to the queue has completed. */
+/* Block until all work submitted to the queue has completed.  Returns
+ * SY_ERR_TIMEOUT (once) if a kernel's bounded wait gave up since the last sync. */
 sy_status sy_queue_sync(sy_queue_t q);
 /* The cudaStream_t the queue submits to. */
 sy_status sy_queue_stream(sy_queue_t q, void** cuda_stream);
@@ -239,6 +240,20 @@ sy_status sy_stencil_start(sy_queue_t q, const sy_stencil_params* p, const void*
 sy_status sy_wave_run(sy_queue_t q, const sy_stencil_params* p, const void* u0, void* u_a, void* u_b, int64_t steps,
                       const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* events, const void** prev_out,
                       const void** cur_out);
+
+/* Temporal blocking: T leapfrog steps (T = 2 or 4; radius 1 or 2) in one pass over
+ * memory.  Each chunk reads u^{n-1} (u_prev) and u^n (u_cur) with a halo of T x r
+ * rows (halo_radius >= T * radius) and writes u^{n+T-1} (out_prev) and u^{n+T}
+ * (out_cur) for its rows; the intermediate steps are recomputed on the halo in
+ * shared memory instead of being written and re-read.  Tiles are staged by TMA
+ * (rows must be 16-byte aligned: base pointers and pitch).  Results are
+ * bit-identical to T calls of sy_stencil_step.  The outputs must not overlap the
+ * inputs or each other (chunks read each other's input rows while writing).
+ * The kernel's waits are bounded: if one gives up, the next sy_queue_sync returns
+ * SY_ERR_TIMEOUT and the outputs are invalid. */
+sy_status sy_stencil_multistep(sy_queue_t q, const sy_stencil_params* p, int T, const void* u_prev,
+                               const void* u_cur, void* out_prev, void* out_cur, const sy_chunk* chunks, int n_chunks,
+                               int halo_radius, sy_event* chunk_events);
 
 /* Number of tile variants for a (radius, dtype); variant ids are 1..count
  * (0 always means the default).  tile_rows / tile_cols / threads (nullable)

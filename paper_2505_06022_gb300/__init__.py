@@ -143,6 +143,7 @@ _SIGS = {
     "sy_stencil_batch_run": [_p],
     "sy_stencil_batch_times": [_p, _p, C.c_int],
     "sy_stencil_batch_destroy": [_p],
+    "sy_stencil_multistep": [_p, _p, C.c_int, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_wave_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
 }
 _RESTYPE = {"sy_status_string": C.c_char_p, "sy_last_error": C.c_char_p, "sy_abi_version": C.c_int}
@@ -590,6 +591,15 @@ def sy_wave_run(q: int, p: StencilParams, u0, u_a, u_b, steps: int, chunks, halo
     _call("sy_wave_run", q, C.byref(p), _ptr(u0), _ptr(u_a), _ptr(u_b), steps, arr, k, halo_radius, evs,
           C.byref(pv), C.byref(cv))
     return pv.value, cv.value, (list(evs[:n_ev]) if want_events else [])
+
+
+def sy_stencil_multistep(q: int, p: StencilParams, T: int, u_prev, u_cur, out_prev, out_cur, chunks,
+                         halo_radius: int, want_events: bool = False) -> list[int]:
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))()
+    _call("sy_stencil_multistep", q, C.byref(p), T, _ptr(u_prev), _ptr(u_cur), _ptr(out_prev), _ptr(out_cur), arr,
+          k, halo_radius, evs if want_events else None)
+    return list(evs[:k]) if want_events else []
 
 
 def sy_stencil_variant_count(radius: int, dtype: int) -> int:

@@ -54,7 +54,7 @@ def stale() -> bool:
 
 def _flags_for(src: str) -> list[str]:
     name = os.path.basename(src)
-    extra = EXACT if (name.startswith("wave") or name.startswith("saxpy") or name.startswith("batch")) else []
+    extra = EXACT if name.startswith(("wave", "saxpy", "batch", "tb")) else []
     return COMMON + extra
 
 

@@ -367,8 +367,11 @@ sy_status sy_queue_create(int device, void* cuda_stream, sy_queue_t* out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&q->d_stamps, 4ull * kStampSlots * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(q->d_stamps, 0, 4ull * kStampSlots * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&q->d_flags, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(q->d_flags, 0, sizeof(unsigned int));
     if (e != cudaSuccess) {
         if (q->d_stamps) cudaFree(q->d_stamps);
+        if (q->d_flags) cudaFree(q->d_flags);
         if (q->aux) cudaStreamDestroy(q->aux);
         if (q->owned) cudaStreamDestroy(q->stream);
         delete q;
@@ -392,6 +395,7 @@ sy_status sy_queue_destroy(sy_queue_t qh) {
     if (q->run.exec) cudaGraphExecDestroy(q->run.exec);
     if (q->scratch) cudaFree(q->scratch);
     if (q->d_stamps) cudaFree(q->d_stamps);
+    if (q->d_flags) cudaFree(q->d_flags);
     if (q->aux) cudaStreamDestroy(q->aux);
     if (q->owned) cudaStreamDestroy(q->stream);
     delete q;
@@ -403,6 +407,12 @@ sy_status sy_queue_sync(sy_queue_t qh) {
     SY_TRY(check_queue(qh, &q));
     SY_TRY(use_device(q));
     SY_CUDA(cudaStreamSynchronize(q->stream));
+    unsigned int flags = 0;
+    SY_CUDA(cudaMemcpy(&flags, q->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags) {
+        SY_CUDA(cudaMemset(q->d_flags, 0, sizeof flags));
+        return fail(SY_ERR_TIMEOUT, "a kernel's bounded wait gave up (flags 0x%x); its outputs are invalid", flags);
+    }
     return SY_OK;
 }
 
@@ -614,6 +624,62 @@ sy_status sy_stencil_start(sy_queue_t qh, const sy_stencil_params* p, const void
     Queue* q;
     SY_TRY(check_queue(qh, &q));
     return stencil_common(q, p, nullptr, u0, u_m1, chunks, n_chunks, halo_radius, chunk_events, true);
+}
+
+sy_status sy_stencil_multistep(sy_queue_t qh, const sy_stencil_params* p, int T, const void* u_prev,
+                               const void* u_cur, void* out_prev, void* out_cur, const sy_chunk* chunks, int n_chunks,
+                               int halo_radius, sy_event* chunk_events) {
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil_param_checks(p));
+    if (T != 2 && T != 4) return fail(SY_ERR_INVALID_ARGUMENT, "T = %d not in {2, 4}", T);
+    if (p->radius > 2) return fail(SY_ERR_UNSUPPORTED, "temporal blocking supports radius 1 and 2");
+    if (p->ny == 0 || p->nx == 0) {
+        if (n_chunks == 0) return SY_OK;
+    }
+    SY_TRY(validate_chunks(p->ny, chunks, n_chunks));
+    if (halo_radius < T * p->radius)
+        return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < T x radius = %d", halo_radius, T * p->radius);
+    if (!u_prev || !u_cur || !out_prev || !out_cur) return fail(SY_ERR_NULL_POINTER, "field pointer is NULL");
+    const size_t es = dtype_size(p->dtype);
+    const int64_t pb = p->pitch * static_cast<int64_t>(es);
+    const uintptr_t all = reinterpret_cast<uintptr_t>(u_prev) | reinterpret_cast<uintptr_t>(u_cur) |
+                          reinterpret_cast<uintptr_t>(out_prev) | reinterpret_cast<uintptr_t>(out_cur);
+    if ((all % 16) || (pb % 16))
+        return fail(SY_ERR_INVALID_ARGUMENT, "temporal blocking needs 16-byte aligned rows (base and pitch)");
+    const size_t bytes = static_cast<size_t>(p->ny) * static_cast<size_t>(pb);
+    const void* in[2] = {u_prev, u_cur};
+    const void* outs[2] = {out_prev, out_cur};
+    for (const void* o : outs)
+        for (const void* i : in)
+            if (ranges_overlap(o, bytes, i, bytes))
+                return fail(SY_ERR_ALIAS, "outputs must not overlap the inputs (other chunks read them)");
+    if (ranges_overlap(out_prev, bytes, out_cur, bytes)) return fail(SY_ERR_ALIAS, "out_prev overlaps out_cur");
+    SY_TRY(use_device(q));
+    const int fault = fault_enabled("tb_timeout") ? 1 : 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        EventRecord* rec;
+        SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
+        TBLaunch w;
+        w.ny = p->ny;
+        w.nx = p->nx;
+        w.pitch_bytes = pb;
+        w.radius = p->radius;
+        w.dtype = p->dtype;
+        w.T = T;
+        w.c2 = p->c2;
+        w.u_prev = u_prev;
+        w.u_cur = u_cur;
+        w.out_prev = out_prev;
+        w.out_cur = out_cur;
+        w.row_begin = chunks[c].begin;
+        w.row_end = chunks[c].end;
+        w.fault = fault;
+        w.pdl = c == 0 ? 1 : 2;
+        SY_TRY(launch_tb(q, w));
+        SY_TRY(end_event(q, rec));
+    }
+    return SY_OK;
 }
 
 sy_status sy_stencil_variant_count(int radius, int dtype, int* count) {

@@ -103,6 +103,9 @@ struct Queue {
     uint64_t window_e0 = 0;
     double window_t0 = 0.0;
     std::vector<Window> windows;
+    // error flags kernels with bounded waits set (bit 0: a wait timed out); read and
+    // cleared by sy_queue_sync
+    unsigned int* d_flags = nullptr;
     // scratch owned by the queue (allocated on first use)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -156,6 +159,21 @@ sy_status stencil_common(Queue* q, const sy_stencil_params* p, const void* u_pre
 sy_status stencil_param_checks(const sy_stencil_params* p);
 int wave_variant_count(int radius, int dtype);
 bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* tile_cols, int* threads);
+
+// Temporal blocking (tb.cu): T steps per pass for rows [row_begin, row_end).
+struct TBLaunch {
+    int64_t ny, nx, pitch_bytes;
+    int radius, dtype, T;
+    float c2;
+    const void* u_prev;
+    const void* u_cur;
+    void* out_prev;
+    void* out_cur;
+    int64_t row_begin, row_end;
+    int fault;  // host-injected fault for tests
+    int pdl;
+};
+sy_status launch_tb(Queue* q, const TBLaunch& w);
 
 sy_status launch_wave_energy(Queue* q, const sy_stencil_params* p, const void* u_new, const void* u_old,
                              double* partials, int n_partials, double* out3_device);

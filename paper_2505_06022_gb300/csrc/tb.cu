@@ -1,0 +1,338 @@
+// Temporal blocking: T leapfrog steps per pass over HBM.
+//
+// A block owns a tile of BY x BX output points of a row chunk.  TMA
+// (cp.async.bulk.tensor.2d, completion counted on an mbarrier) copies the
+// tile's u^n and u^{n-1} with a halo of T*r rows and PAD >= T*r columns into
+// shared memory; points outside the grid arrive as zeros (the copy's
+// out-of-bounds fill), which are the Dirichlet ghosts.  The block then advances
+// T steps in shared memory over shrinking regions -- step k computes u^{n+k}
+// on the tile grown by (T-k)*r, recomputing the halo instead of re-reading it
+// from HBM -- and writes u^{n+T-1} and u^{n+T} for the tile.  HBM traffic is two
+// reads and two writes per point per pass: 16/T bytes per FP32 update instead
+// of 12.  Every point is computed with the single-step operation order and
+// rounded to storage after every step, so results are bit-identical to T calls
+// of the single-step kernel.
+//
+// Blocks are persistent and double-buffered: while a tile is computed, the
+// elected thread has already issued the copies of the block's next tile into
+// the other stage.  Every wait on an mbarrier is bounded by a clock limit; on
+// expiry the block sets an error flag, waits (again bounded) for its own
+// copies in flight, and returns; the host reports SY_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdlib>
+#include <mutex>
+
+#include "wave_kernel.cuh"
+
+namespace sy {
+namespace tb {
+
+constexpr int kThreads = 256;
+constexpr int BX = 128;
+constexpr int BY = 32;
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+struct TBArgs {
+    char* out_prev;  // u^{n+T-1}
+    char* out_cur;   // u^{n+T}
+    int64_t ny, nx, pitch_bytes;
+    int64_t row_begin, row_end;
+    int64_t tiles_x, tiles;
+    float c2;
+    unsigned int* err;           // error flags (bit 0: a wait timed out)
+    unsigned long long* stamp;   // timestamp slot or null
+    int fault;                   // host-injected fault for tests: 1 = never issue the first copy
+    int pdl;                     // as in wave::Args
+};
+
+template <typename S, int R, int T>
+struct Geo {
+    static constexpr int ES = sizeof(S);
+    static constexpr int VEC = 16 / ES;                                     // elements per 16 bytes
+    static constexpr int PAD = ((T * R + VEC - 1) / VEC) * VEC;             // 16-byte aligned x halo
+    static constexpr int W = BX + 2 * PAD;                                  // box / row width (elements)
+    static constexpr int H = BY + 2 * T * R;                                // box height
+    static constexpr int BUF = ((W * H * ES + 127) / 128) * 128;            // one field, 128-byte aligned
+    static constexpr int SMEM = 4 * BUF + 2 * 8;                            // 2 stages x 2 fields + 2 barriers
+    static constexpr unsigned TX = 2u * W * H * ES;                         // bytes a stage receives
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: true when the phase completed, false after kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename S>
+__device__ __forceinline__ float ld_s(const S* buf, int idx);
+template <>
+__device__ __forceinline__ float ld_s<float>(const float* buf, int idx) { return buf[idx]; }
+template <>
+__device__ __forceinline__ float ld_s<__nv_bfloat16>(const __nv_bfloat16* buf, int idx) {
+    return __uint_as_float(static_cast<uint32_t>(__bfloat16_as_ushort(buf[idx])) << 16);
+}
+template <>
+__device__ __forceinline__ float ld_s<__half>(const __half* buf, int idx) { return __half2float(buf[idx]); }
+
+template <typename S>
+__device__ __forceinline__ S to_s(float v);
+template <>
+__device__ __forceinline__ float to_s<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_s<__half>(float v) { return __float2half_rn(v); }
+
+template <typename S, int R, int T>
+__global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant__ CUtensorMap map_prev,
+                                                           const __grid_constant__ CUtensorMap map_cur, TBArgs a) {
+    using G = Geo<S, R, T>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * G::BUF);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kThreads / 32;
+
+    if (a.pdl == 1) griddep_wait();
+    if (a.pdl) griddep_launch_dependents();
+    stamp_begin(a.stamp);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // copies of tile t into stage s: u^{n-1} box into field 1, u^n box into field 0
+    auto issue = [&](int64_t t, int s, bool skip) {
+        const int64_t ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+        const int x = static_cast<int>(tx * BX) - G::PAD;
+        const int y = static_cast<int>(a.row_begin + ty * BY) - T * R;
+        unsigned char* base = smem + 2 * s * G::BUF;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic writes to this stage
+        mbar_expect_tx(&bars[s], G::TX);
+        if (!skip) {
+            tma_load_2d(base, &map_cur, x, y, &bars[s]);
+            tma_load_2d(base + G::BUF, &map_prev, x, y, &bars[s]);
+        }
+    };
+
+    int64_t t = blockIdx.x;
+    unsigned uses[2] = {0u, 0u};
+    if (t < a.tiles && tid == 0) issue(t, 0, a.fault == 1);
+    for (int it = 0; t < a.tiles; ++it, t += gridDim.x) {
+        const int s = it & 1;
+        const int64_t tn = t + gridDim.x;
+        if (tn < a.tiles && tid == 0) issue(tn, s ^ 1, false);
+        // every thread waits (acquiring the copied data); the block decides together
+        const bool ok = mbar_wait_bounded(&bars[s], uses[s] & 1u);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicOr(a.err, 1u);
+                // let this block's own copies land before its shared memory is released
+                mbar_wait_bounded(&bars[s], uses[s] & 1u);
+                if (tn < a.tiles) mbar_wait_bounded(&bars[s ^ 1], uses[s ^ 1] & 1u);
+            }
+            return;  // the whole block returns: no barrier below is left half-reached
+        }
+        ++uses[s];
+        S* X = reinterpret_cast<S*>(smem + 2 * s * G::BUF);  // u^{m}
+        S* Y = reinterpret_cast<S*>(smem + 2 * s * G::BUF + G::BUF);  // u^{m-1}, overwritten by u^{m+1}
+        const int64_t ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+        const int64_t y0 = a.row_begin + ty * BY, x0 = tx * BX;
+
+#pragma unroll 1
+        for (int k = 1; k <= T; ++k) {
+            const int grow = (T - k) * R;  // region = tile grown by `grow`
+            const int rows = BY + 2 * grow, cols = BX + 2 * grow;
+            const int oy = k * R, ox = G::PAD - grow;
+            for (int i = warp; i < rows; i += kWarps) {
+                const int64_t gy = y0 - grow + i;
+                const int brow = (oy + i) * G::W;
+                for (int j = lane; j < cols; j += 32) {
+                    const int64_t gx = x0 - grow + j;
+                    const int b = brow + ox + j;
+                    float vert[R], horz[R];
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        vert[d - 1] = __fadd_rn(ld_s(X, b - d * G::W), ld_s(X, b + d * G::W));
+                        horz[d - 1] = __fadd_rn(ld_s(X, b - d), ld_s(X, b + d));
+                    }
+                    float v = wave::update<R, false>(ld_s(X, b), ld_s(Y, b), vert, horz, a.c2);
+                    if (gy < 0 || gy >= a.ny || gx < 0 || gx >= a.nx) v = 0.0f;  // ghosts stay zero
+                    Y[b] = to_s<S>(v);
+                }
+            }
+            __syncthreads();
+            S* tmp = X;  // u^{n+k} is now in Y
+            X = Y;
+            Y = tmp;
+        }
+        // X = u^{n+T} and Y = u^{n+T-1} on the tile: write the tile's rows of the chunk
+        for (int i = warp; i < BY; i += kWarps) {
+            const int64_t gy = y0 + i;
+            if (gy >= a.row_end) break;
+            const int brow = (T * R + i) * G::W + G::PAD;
+            S* oc = reinterpret_cast<S*>(a.out_cur + gy * a.pitch_bytes);
+            S* op = reinterpret_cast<S*>(a.out_prev + gy * a.pitch_bytes);
+            for (int j = lane; j < BX; j += 32) {
+                const int64_t gx = x0 + j;
+                if (gx < a.nx) {
+                    oc[gx] = X[brow + j];
+                    op[gx] = Y[brow + j];
+                }
+            }
+        }
+        __syncthreads();  // the stage is free for the copy issued in the next iteration but one
+    }
+    stamp_end(a.stamp);
+    if (a.pdl && tid == 0) griddep_wait();
+}
+
+// ---- host ----------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <typename S, int R, int T>
+sy_status make_map(const void* base, int64_t ny, int64_t nx, int64_t pitch_bytes, CUtensorMap* map) {
+    using G = Geo<S, R, T>;
+    auto enc = encode_fn();
+    if (!enc) return fail(SY_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    const CUtensorMapDataType dt = sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch_bytes)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(G::W), static_cast<cuuint32_t>(G::H)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SY_ERR_INVALID_ARGUMENT, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    return SY_OK;
+}
+
+template <typename S, int R, int T>
+sy_status launch_tb(Queue* q, const TBLaunch& w) {
+    using G = Geo<S, R, T>;
+    auto kern = wave_tb_kernel<S, R, T>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    });
+    if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute(tb smem)");
+    CUtensorMap mp, mc;
+    sy_status st = make_map<S, R, T>(w.u_prev, w.ny, w.nx, w.pitch_bytes, &mp);
+    if (st == SY_OK) st = make_map<S, R, T>(w.u_cur, w.ny, w.nx, w.pitch_bytes, &mc);
+    if (st != SY_OK) return st;
+    TBArgs a;
+    a.out_prev = static_cast<char*>(w.out_prev);
+    a.out_cur = static_cast<char*>(w.out_cur);
+    a.ny = w.ny;
+    a.nx = w.nx;
+    a.pitch_bytes = w.pitch_bytes;
+    a.row_begin = w.row_begin;
+    a.row_end = w.row_end;
+    a.tiles_x = (w.nx + BX - 1) / BX;
+    a.tiles = a.tiles_x * ((w.row_end - w.row_begin + BY - 1) / BY);
+    a.c2 = w.c2;
+    a.err = q->d_flags;
+    a.stamp = q->cur_stamp;
+    a.fault = w.fault;
+    a.pdl = w.pdl;
+    if (a.tiles == 0) return SY_OK;
+    int occ = 0;
+    SY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, G::SMEM));
+    if (occ < 1) return fail(SY_ERR_UNSUPPORTED, "temporal-blocking kernel does not fit on an SM");
+    int64_t blocks = static_cast<int64_t>(occ) * q->sm_count;
+    if (blocks > a.tiles) blocks = a.tiles;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = q->launch;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = w.pdl ? 1 : 0;
+    SY_CUDA(cudaLaunchKernelEx(&cfg, kern, mp, mc, a));
+    ++q->launches;
+    q->cur_blocks += static_cast<uint64_t>(blocks);
+    return SY_OK;
+}
+
+template <typename S, int T>
+sy_status launch_r(Queue* q, const TBLaunch& w) {
+    switch (w.radius) {
+        case 1: return launch_tb<S, 1, T>(q, w);
+        case 2: return launch_tb<S, 2, T>(q, w);
+        default: return fail(SY_ERR_UNSUPPORTED, "temporal blocking supports radius 1 and 2 (asked %d)", w.radius);
+    }
+}
+
+template <typename S>
+sy_status launch_T(Queue* q, const TBLaunch& w) {
+    switch (w.T) {
+        case 2: return launch_r<S, 2>(q, w);
+        case 4: return launch_r<S, 4>(q, w);
+        default: return fail(SY_ERR_UNSUPPORTED, "temporal blocking supports T = 2 and 4 (asked %d)", w.T);
+    }
+}
+
+}  // namespace tb
+
+sy_status launch_tb(Queue* q, const TBLaunch& w) {
+    switch (w.dtype) {
+        case SY_F32: return tb::launch_T<float>(q, w);
+        case SY_BF16: return tb::launch_T<__nv_bfloat16>(q, w);
+        default: return tb::launch_T<__half>(q, w);
+    }
+}
+
+}  // namespace sy

@@ -1,0 +1,119 @@
+"""Temporal blocking (T steps per pass, TMA-staged tiles): bit-identical to T
+single steps -- against the oracle on small and ragged grids, and against the
+single-step path at the full 8192 x 8192 workload -- plus its error paths,
+including a bounded wait that is made to run out (host-injected: the first copy
+is never issued), which must come back as SY_ERR_TIMEOUT with the context still
+usable."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2505_06022_gb300 as sy
+from paper_2505_06022_gb300 import inputs
+
+from gpu_helpers import bits, to_host, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+DT = {"f32": oracle.F32, "bf16": oracle.BF16, "f16": oracle.F16}
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch_cuda()
+    with sy.Queue(0) as queue:
+        yield queue.handle
+
+
+def run_tb(q, u0, T, r, dtype, chunks, passes, pitch=None, torch=None):
+    ny, nx = u0.shape
+    pitch = pitch or nx
+    tdt = torch.float32 if dtype == "f32" else torch.int16
+    B = torch.zeros(ny, pitch, dtype=tdt, device="cuda")
+    B[:, :nx] = torch.from_numpy(u0 if dtype == "f32" else u0.view(np.int16)).cuda()
+    A, C, D = (torch.zeros_like(B) for _ in range(3))
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype, pitch=pitch)
+    sy.sy_stencil_start(q, p, B, A, chunks, T * r)
+    pairs = [(A, B), (C, D)]
+    for k in range(passes):
+        (ip, ic), (op, oc) = pairs[k % 2], pairs[(k + 1) % 2]
+        sy.sy_stencil_multistep(q, p, T, ip, ic, op, oc, chunks, T * r)
+    sy.sy_queue_sync(q)
+    return pairs[passes % 2]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("T,r", [(2, 1), (4, 1), (2, 2), (4, 2)])
+@pytest.mark.parametrize("ny,nx,chunks", [(70, 300, None), (33, 129, [(0, 1), (1, 5), (5, 33)]), (130, 520, None)])
+def test_tb_bit_exact_vs_oracle(q, dtype, T, r, ny, nx, chunks):
+    torch = torch_cuda()
+    chunks = chunks or sy.sy_split_rows(ny, 3)
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 7.0) + 0.05 * inputs.random_field(2, ny, nx), dtype)
+    v = 4 if dtype == "f32" else 8
+    pitch = (nx + v - 1) // v * v
+    passes = 3
+    prev, cur = run_tb(q, u0, T, r, dtype, chunks, passes, pitch, torch)
+    st = np.float32 if dtype == "f32" else np.uint16
+    op, oc = oracle.wave_run_mirror(DT[dtype], u0, passes * T, r, 0.25)
+    assert np.array_equal(bits(to_host(cur, (ny, nx), st)), bits(oc))
+    assert np.array_equal(bits(to_host(prev, (ny, nx), st)), bits(op))
+
+
+@pytest.mark.parametrize("T", [2, 4])
+def test_tb_full_size_equals_single_steps(q, T):
+    torch = torch_cuda()
+    n, steps = 8192, 200
+    u0 = inputs.to_storage(inputs.gaussian_pulse(n, n, 64.0), "f32")
+    chunks = sy.sy_split_rows(n, 4)
+    prev, cur = run_tb(q, u0, T, 1, "f32", chunks, steps // T, torch=torch)
+    d0 = torch.from_numpy(u0).cuda()
+    a, b = torch.empty_like(d0), torch.empty_like(d0)
+    p = sy.stencil_params(n, n, 1, 0.25, "f32")
+    pv, cv, _ = sy.sy_wave_run(q, p, d0, a, b, steps, chunks, 1)
+    torch.cuda.synchronize()
+    byptr = {d0.data_ptr(): d0, a.data_ptr(): a, b.data_ptr(): b}
+    assert torch.equal(cur.view(torch.int32), byptr[cv].view(torch.int32))
+    assert torch.equal(prev.view(torch.int32), byptr[pv].view(torch.int32))
+
+
+def test_tb_errors(q):
+    torch = torch_cuda()
+    a, b, c, d = (torch.zeros(64, 128, device="cuda") for _ in range(4))
+    p = sy.stencil_params(64, 128, 1, 0.25, "f32")
+    cases = [((p, 2, a, b, a, d, [(0, 64)], 2), "SY_ERR_ALIAS"),
+             ((p, 2, a, b, c, c, [(0, 64)], 2), "SY_ERR_ALIAS"),
+             ((p, 2, a, b, c, d, [(0, 64)], 1), "SY_ERR_HALO_TOO_SMALL"),
+             ((p, 3, a, b, c, d, [(0, 64)], 3), "SY_ERR_INVALID_ARGUMENT"),
+             ((sy.stencil_params(64, 128, 3, 0.25, "f32"), 2, a, b, c, d, [(0, 64)], 6), "SY_ERR_UNSUPPORTED"),
+             ((sy.stencil_params(64, 127, 1, 0.25, "f32", pitch=127), 2, a, b, c, d, [(0, 64)], 2),
+              "SY_ERR_INVALID_ARGUMENT")]
+    for args, name in cases:
+        with pytest.raises(sy.SyError) as e:
+            sy.sy_stencil_multistep(q, *args)
+        assert e.value.name == name
+
+
+def test_tb_bounded_wait_times_out_and_context_survives(q):
+    torch = torch_cuda()
+    ny, nx = 256, 512
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 10.0), "f32")
+    old = os.environ.get("SY_FAULT")
+    os.environ["SY_FAULT"] = "tb_timeout"
+    try:
+        a, b, c, d = (torch.zeros(ny, nx, device="cuda") for _ in range(4))
+        p = sy.stencil_params(ny, nx, 1, 0.25, "f32")
+        sy.sy_stencil_multistep(q, p, 2, a, b, c, d, [(0, ny)], 2)
+        with pytest.raises(sy.SyError) as e:
+            sy.sy_queue_sync(q)
+        assert e.value.name == "SY_ERR_TIMEOUT"
+    finally:
+        if old is None:
+            del os.environ["SY_FAULT"]
+        else:
+            os.environ["SY_FAULT"] = old
+    sy.sy_queue_sync(q)  # the flag was reported once and cleared
+    prev, cur = run_tb(q, u0, 2, 1, "f32", [(0, ny)], 2, torch=torch)  # and the context still works
+    _, oc = oracle.wave_run_mirror(oracle.F32, u0, 4, 1, 0.25)
+    assert np.array_equal(cur.cpu().numpy().view(np.uint32), oc.view(np.uint32))
