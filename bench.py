@@ -350,6 +350,44 @@ def measure_batched(q, stream) -> dict:
             "launches_per_run": {"batched": steps, "per_grid": steps * len(fields)}}
 
 
+def measure_temporal(q, stream, T: int, dtype: str = "f32") -> dict:
+    """The headline simulation (8192^2, 200 steps, 4 row chunks) with temporal blocking: the
+    Taylor start, then 200/T passes of T steps each (halo T*r), from the resident initial field.
+    Not the headline configuration (its halo is 1); reported beside it."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import inputs
+
+    host = inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), dtype)
+    u0 = torch.from_numpy(host if dtype == "f32" else host.view(np.int16)).cuda()
+    A, C, D = (torch.empty_like(u0) for _ in range(3))
+    Bw = torch.empty_like(u0)
+    p = sy.stencil_params(NY, NX, 1, C2, dtype)
+    chunks = sy.sy_split_rows(NY, CHUNKS)
+    halo = T
+
+    def sim():
+        sy.sy_stencil_start(q.handle, p, u0, A, chunks, halo)
+        pairs = [(A, u0), (C, D), (A, Bw)]
+        cur = pairs[0]
+        for k in range(STEPS // T):
+            nxt = pairs[1] if k % 2 == 0 else pairs[2]
+            sy.sy_stencil_multistep(q.handle, p, T, cur[0], cur[1], nxt[0], nxt[1], chunks, halo)
+            cur = nxt
+        return cur
+
+    sim()
+    reps, ms, joules = _metered(q, stream, sim)
+    sy.sy_queue_sync(q.handle)
+    esize = 4 if dtype == "f32" else 2
+    upd = STEPS * NY * NX
+    return {"T": T, "dtype": dtype, "halo": halo, "updates_per_s": upd / (ms * 1e-3), "ms_per_sim": ms,
+            "hbm_bytes_per_update": 4 * esize / T, "j_per_update": None if not joules else joules / (reps * upd),
+            "equivalent_single_step_gb_per_s": 3 * esize * upd / (ms * 1e-3) / 1e9}
+
+
 def measure_learned(q, stream) -> dict:
     """The learned cost model, end to end on this GPU: the library tunes a reduced
     corpus exhaustively (220 shapes), trains its MLP on 80% of the shapes with its own
@@ -547,6 +585,8 @@ def run_gpu(args) -> None:
         for dt in ("bf16", "f16"):
             forms[dt] = measure_precision_form(q, stream, dt)
         forms["batched"] = measure_batched(q, stream)
+        forms["temporal_T2"] = measure_temporal(q, stream, 2)
+        forms["temporal_T4"] = measure_temporal(q, stream, 4)
         forms["learned"] = measure_learned(q, stream)
     if dist:
         dist.barrier()

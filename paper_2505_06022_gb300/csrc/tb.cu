@@ -119,10 +119,79 @@ __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(float v) { return _
 template <>
 __device__ __forceinline__ __half to_s<__half>(float v) { return __float2half_rn(v); }
 
+// One step over buffer rows [k*R, H - k*R) and every column of the W-wide
+// buffers: X holds u^m, Y holds u^{m-1} and receives u^{m+1}.  Each thread owns one
+// 16-byte column group and a contiguous run of rows; the 2R+1 rows of its group
+// around the current row stay in registers (a rolling window), the groups left
+// and right of it supply the horizontal neighbours.  Results in the outer PAD
+// columns are computed from partial neighbourhoods, but the needed region of
+// step k, [PAD - (T-k)R, PAD + BX + (T-k)R), lies inside [k R, W - k R) where
+// every value is exact (PAD >= T R).  Points outside the grid are set to zero
+// (interior tiles skip the test).
+template <typename S, int R, int T>
+__device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_buf0, int x_buf0, bool interior,
+                                        int64_t ny, int64_t nx, float c2) {
+    using G = Geo<S, R, T>;
+    using Tr = wave::Traits<S>;
+    constexpr int V = Tr::V;
+    constexpr int NG = G::W / V;               // 16-byte groups per row
+    constexpr int NRL = kThreads / NG;         // row lanes
+    const int g = threadIdx.x % NG, rl = threadIdx.x / NG;
+    if (rl >= NRL) return;
+    const int r_lo = k * R, r_hi = G::H - k * R;
+    const int per = (r_hi - r_lo + NRL - 1) / NRL;
+    const int r0 = r_lo + rl * per;
+    const int r1 = r0 + per < r_hi ? r0 + per : r_hi;
+    if (r0 >= r1) return;
+    uint4 win[2 * R + 1];  // rows r - R .. r + R of group g
+#pragma unroll
+    for (int d = 0; d < 2 * R; ++d) win[d] = X[(r0 - R + d) * NG + g];
+    for (int r = r0; r < r1; ++r) {
+        win[2 * R] = X[(r + R) * NG + g];
+        const uint4 lv = X[r * NG + g - 1];  // previous group (in bounds: r >= R >= 1)
+        const uint4 rv = X[r * NG + g + 1];  // next group (in bounds: r + 1 <= H - 1)
+        const uint4 pv = Y[r * NG + g];
+        float ext[V + 2 * R];                // columns g*V - R .. g*V + V + R - 1
+#pragma unroll
+        for (int e = 0; e < V; ++e) ext[R + e] = Tr::elem(win[R], e);
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+            ext[R - d] = Tr::elem(lv, V - d);
+            ext[R + V - 1 + d] = Tr::elem(rv, d - 1);
+        }
+        float out[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            float vert[R], horz[R];
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                vert[d - 1] = __fadd_rn(Tr::elem(win[R - d], e), Tr::elem(win[R + d], e));
+                horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+            }
+            out[e] = wave::update<R, false>(ext[R + e], Tr::elem(pv, e), vert, horz, c2);
+        }
+        if (!interior) {  // ghosts outside the grid stay zero
+            const int64_t gy = static_cast<int64_t>(y_buf0) + r;
+            const bool row_in = gy >= 0 && gy < ny;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const int64_t gx = static_cast<int64_t>(x_buf0) + g * V + e;
+                if (!row_in || gx < 0 || gx >= nx) out[e] = 0.0f;
+            }
+        }
+        Y[r * NG + g] = Tr::pack(out);
+#pragma unroll
+        for (int d = 0; d < 2 * R; ++d) win[d] = win[d + 1];
+    }
+}
+
 template <typename S, int R, int T>
 __global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant__ CUtensorMap map_prev,
                                                            const __grid_constant__ CUtensorMap map_cur, TBArgs a) {
     using G = Geo<S, R, T>;
+    using Tr = wave::Traits<S>;
+    constexpr int V = Tr::V;
+    constexpr int NG = G::W / V;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * G::BUF);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -138,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant
     }
     __syncthreads();
 
-    // copies of tile t into stage s: u^{n-1} box into field 1, u^n box into field 0
+    // copies of tile t into stage s: u^n box into field 0, u^{n-1} box into field 1
     auto issue = [&](int64_t t, int s, bool skip) {
         const int64_t ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
         const int x = static_cast<int>(tx * BX) - G::PAD;
@@ -153,71 +222,68 @@ __global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant
     };
 
     int64_t t = blockIdx.x;
-    unsigned uses[2] = {0u, 0u};
+    unsigned uses0 = 0u, uses1 = 0u;
     if (t < a.tiles && tid == 0) issue(t, 0, a.fault == 1);
     for (int it = 0; t < a.tiles; ++it, t += gridDim.x) {
         const int s = it & 1;
         const int64_t tn = t + gridDim.x;
         if (tn < a.tiles && tid == 0) issue(tn, s ^ 1, false);
+        const unsigned par = (s ? uses1 : uses0) & 1u;
         // every thread waits (acquiring the copied data); the block decides together
-        const bool ok = mbar_wait_bounded(&bars[s], uses[s] & 1u);
+        const bool ok = mbar_wait_bounded(&bars[s], par);
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
                 atomicOr(a.err, 1u);
                 // let this block's own copies land before its shared memory is released
-                mbar_wait_bounded(&bars[s], uses[s] & 1u);
-                if (tn < a.tiles) mbar_wait_bounded(&bars[s ^ 1], uses[s ^ 1] & 1u);
+                mbar_wait_bounded(&bars[s], par);
+                if (tn < a.tiles) mbar_wait_bounded(&bars[s ^ 1], (s ? uses0 : uses1) & 1u);
             }
             return;  // the whole block returns: no barrier below is left half-reached
         }
-        ++uses[s];
-        S* X = reinterpret_cast<S*>(smem + 2 * s * G::BUF);  // u^{m}
-        S* Y = reinterpret_cast<S*>(smem + 2 * s * G::BUF + G::BUF);  // u^{m-1}, overwritten by u^{m+1}
+        if (s) ++uses1;
+        else ++uses0;
+        uint4* X = reinterpret_cast<uint4*>(smem + 2 * s * G::BUF);  // u^{m}
+        uint4* Y = reinterpret_cast<uint4*>(smem + 2 * s * G::BUF + G::BUF);  // u^{m-1} -> u^{m+1}
         const int64_t ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
         const int64_t y0 = a.row_begin + ty * BY, x0 = tx * BX;
+        const int y_buf0 = static_cast<int>(y0) - T * R;  // global row of buffer row 0
+        const int x_buf0 = static_cast<int>(x0) - G::PAD;  // global column of buffer column 0
+        const bool interior = y_buf0 >= 0 && y_buf0 + G::H <= a.ny && x_buf0 >= 0 && x_buf0 + G::W <= a.nx;
 
 #pragma unroll 1
         for (int k = 1; k <= T; ++k) {
-            const int grow = (T - k) * R;  // region = tile grown by `grow`
-            const int rows = BY + 2 * grow, cols = BX + 2 * grow;
-            const int oy = k * R, ox = G::PAD - grow;
-            for (int i = warp; i < rows; i += kWarps) {
-                const int64_t gy = y0 - grow + i;
-                const int brow = (oy + i) * G::W;
-                for (int j = lane; j < cols; j += 32) {
-                    const int64_t gx = x0 - grow + j;
-                    const int b = brow + ox + j;
-                    float vert[R], horz[R];
-#pragma unroll
-                    for (int d = 1; d <= R; ++d) {
-                        vert[d - 1] = __fadd_rn(ld_s(X, b - d * G::W), ld_s(X, b + d * G::W));
-                        horz[d - 1] = __fadd_rn(ld_s(X, b - d), ld_s(X, b + d));
-                    }
-                    float v = wave::update<R, false>(ld_s(X, b), ld_s(Y, b), vert, horz, a.c2);
-                    if (gy < 0 || gy >= a.ny || gx < 0 || gx >= a.nx) v = 0.0f;  // ghosts stay zero
-                    Y[b] = to_s<S>(v);
-                }
-            }
+            tb_step<S, R, T>(X, Y, k, y_buf0, x_buf0, interior, a.ny, a.nx, a.c2);
             __syncthreads();
-            S* tmp = X;  // u^{n+k} is now in Y
+            uint4* tmp = X;  // u^{m+1} is now in Y
             X = Y;
             Y = tmp;
         }
-        // X = u^{n+T} and Y = u^{n+T-1} on the tile: write the tile's rows of the chunk
-        for (int i = warp; i < BY; i += kWarps) {
+        // X = u^{n+T} and Y = u^{n+T-1} on the tile: write the tile's rows of the chunk,
+        // one 16-byte group per thread (element stores at the right edge of the grid)
+        constexpr int TG = BX / V;  // groups per tile row
+        for (int idx = tid; idx < BY * TG; idx += kThreads) {
+            const int i = idx / TG, gg = idx - i * TG;
             const int64_t gy = y0 + i;
-            if (gy >= a.row_end) break;
-            const int brow = (T * R + i) * G::W + G::PAD;
-            S* oc = reinterpret_cast<S*>(a.out_cur + gy * a.pitch_bytes);
-            S* op = reinterpret_cast<S*>(a.out_prev + gy * a.pitch_bytes);
-            for (int j = lane; j < BX; j += 32) {
-                const int64_t gx = x0 + j;
-                if (gx < a.nx) {
-                    oc[gx] = X[brow + j];
-                    op[gx] = Y[brow + j];
+            const int64_t gx = x0 + static_cast<int64_t>(gg) * V;
+            if (gy >= a.row_end || gx >= a.nx) continue;
+            const int bidx = (T * R + i) * NG + G::PAD / V + gg;
+            char* oc = a.out_cur + gy * a.pitch_bytes + gx * G::ES;
+            char* op = a.out_prev + gy * a.pitch_bytes + gx * G::ES;
+            if (gx + V <= a.nx) {
+                *reinterpret_cast<uint4*>(oc) = X[bidx];
+                *reinterpret_cast<uint4*>(op) = Y[bidx];
+            } else {
+                const S* xs = reinterpret_cast<const S*>(&X[bidx]);
+                const S* ys = reinterpret_cast<const S*>(&Y[bidx]);
+                for (int e = 0; e < V && gx + e < a.nx; ++e) {
+                    reinterpret_cast<S*>(oc)[e] = xs[e];
+                    reinterpret_cast<S*>(op)[e] = ys[e];
                 }
             }
         }
+        (void)lane;
+        (void)warp;
+        (void)kWarps;
         __syncthreads();  // the stage is free for the copy issued in the next iteration but one
     }
     stamp_end(a.stamp);
