@@ -310,6 +310,9 @@ def measure_batched(q, stream) -> dict:
                                                in fields], "f32", tile_rows)
     sy.sy_stencil_batch_capture(plan, steps)
     sy.sy_stencil_batch_run(plan)
+    l0 = q.launches
+    sy.sy_stencil_batch_run(plan)
+    batched_launches = q.launches - l0
     reps, ms, joules = _metered(q, stream, lambda: sy.sy_stencil_batch_run(plan))
     sy.sy_stencil_batch_destroy(plan)
 
@@ -347,7 +350,8 @@ def measure_batched(q, stream) -> dict:
             "per_grid_graph_updates_per_s": upd / (ms_g * 1e-3), "per_grid_graph_ms_per_run": ms_g,
             "per_grid_graph_j_per_update": None if not joules_g else joules_g / (reps_g * upd),
             "per_grid_stream_updates_per_s": upd / (ms_s * 1e-3), "per_grid_stream_ms_per_run": ms_s,
-            "launches_per_run": {"batched": steps, "per_grid": steps * len(fields)}}
+            "launches_per_run": {"batched": batched_launches, "per_grid": steps * len(fields)},
+            "mode": "one launch per radius class per step" if tile_rows == 0 else "one launch per step"}
 
 
 def measure_temporal(q, stream, T: int, dtype: str = "f32") -> dict:

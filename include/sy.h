@@ -342,14 +342,16 @@ typedef struct sy_batch_grid {
 typedef struct sy_batch_plan_s* sy_batch_plan_t;
 
 /* Build a plan over n_grids (1..4096) grids of one dtype.  tile_rows: tile height
- * of the warp tiles, 2, 4 or 8 for every grid, or 0 for a height per grid (2 rows
- * for FP32 radius 1, else 4).  The grids' buffers must not overlap each
+ * of the warp tiles, 2, 4 or 8 for every grid (one launch per step, each grid's
+ * radius chosen at run time), or 0 for per-radius launches: the grids of each
+ * radius get a kernel compiled for that radius (its own register budget, the
+ * single-field default tile height), and the launches of a step overlap.  The grids' buffers must not overlap each
  * other.  The plan copies the descriptors to the device; the buffers stay owned by
  * the caller and must outlive the plan. */
 sy_status sy_stencil_batch_plan(sy_queue_t q, const sy_batch_grid* grids, int n_grids, int dtype, int tile_rows,
                                 sy_batch_plan_t* out);
 /* Totals of a plan (each pointer nullable): warp tiles, grid points, blocks of the
- * persistent launch. */
+ * persistent launches of one step. */
 sy_status sy_stencil_batch_info(sy_batch_plan_t plan, int64_t* total_tiles, int64_t* points, int* blocks);
 /* Taylor start for every grid: u_a = u_b + (c2/2) L u_b (one launch). */
 sy_status sy_stencil_batch_start(sy_batch_plan_t plan, int timed);

@@ -31,6 +31,17 @@ struct BatchGridDev {
     float c2;
 };
 
+// A group of grids stepped by one persistent launch: every grid of the plan
+// (radius chosen per grid at run time), or, in per-radius mode, the grids of one
+// radius (a kernel compiled for that radius, with its own register budget).
+struct BatchClass {
+    int radius = 0;           // 0 = mixed radii
+    int64_t desc_off = 0;     // first descriptor of the class in d_desc
+    int n = 0;                // grids in the class
+    int64_t tiles = 0;
+    int blocks = 0;           // persistent grid size of the class's launch
+};
+
 struct BatchPlan {
     Queue* q = nullptr;
     int dtype = 0;
@@ -38,6 +49,7 @@ struct BatchPlan {
     int n_grids = 0;
     int64_t total_tiles = 0;
     int64_t points = 0;
+    std::vector<BatchClass> classes;
     BatchGridDev* d_desc = nullptr;
     unsigned long long* d_stamps = nullptr;  // slot 0: last direct launch; 1..: graph launches
     int64_t stamp_slots = 0;
@@ -53,15 +65,6 @@ namespace {
 
 constexpr int kBatchThreads = 128;
 constexpr int kMaxBatchGrids = 4096;  // prefix sums in shared memory: 32 KiB
-
-// Tile height per radius when the plan asks for the default (tile_rows = 0): 2 rows
-// for FP32 radius 1, else 4.  One kernel carries every radius, so its register
-// budget is that of its largest branch; 4-row tiles keep every branch within 128
-// registers (four 128-thread blocks per SM).
-template <typename S, int R>
-struct AutoRows {
-    static constexpr int value = (sizeof(S) == 4 && R == 1) ? 2 : 4;
-};
 
 template <typename S, int R, int RY, bool START>
 __device__ __forceinline__ void batch_tile(const BatchGridDev& G, int parity, int64_t tx, int64_t ty, int lane) {
@@ -82,13 +85,27 @@ __device__ __forceinline__ void batch_tile(const BatchGridDev& G, int parity, in
     wave::wave_tile<S, R, RY, START>(a, tx, ty, lane);
 }
 
-// RY > 0: every grid uses RY-row tiles; RY == 0: each grid uses AutoRows for its radius
-// (the plan computed tiles_x / tile_begin with the same heights).
-template <typename S, int RY, bool START>
+// Tile height of the per-radius kernels: the single-field defaults (FP32 2/4/8/4 rows
+// for r = 1..4, 16-bit 4/4/8/8).
+template <typename S, int R>
+struct ClassRows {
+    static constexpr int value = sizeof(S) == 4 ? (R == 1 ? 2 : R == 3 ? 8 : 4) : (R <= 2 ? 4 : 8);
+};
+
+// RFIX = 0: grids of any radius, dispatched per grid at run time, RY-row tiles (one
+// kernel carries every radius, so its register budget is that of the largest
+// branch).  RFIX = 1..4: every grid has that radius, ClassRows tiles.
+// pdl as in the single-field kernel: 1 = wait for the previous launch first, 2 = an
+// independent launch of the same step; with either, completion implies the
+// predecessor's completion.
+template <typename S, int RFIX, int RY, bool START>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev* __restrict__ grids, int n_grids,
                                                               int64_t total_tiles, int parity,
-                                                              unsigned long long* stamp) {
+                                                              unsigned long long* stamp, int pdl) {
+    static_assert(RFIX != 0 || RY != 0, "a mixed-radius kernel needs a tile height");
     extern __shared__ int64_t s_begin[];  // n_grids + 1 prefix sums
+    if (pdl == 1) griddep_wait();
+    if (pdl) griddep_launch_dependents();
     stamp_begin(stamp);
     for (int i = threadIdx.x; i <= n_grids; i += blockDim.x) s_begin[i] = i < n_grids ? grids[i].tile_begin : total_tiles;
     __syncthreads();
@@ -122,55 +139,90 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev
             dx = nwarps - dy * tiles_x;
         }
         const BatchGridDev& G = grids[g];
-        switch (G.radius) {
-            case 1: batch_tile<S, 1, RY ? RY : AutoRows<S, 1>::value, START>(G, parity, tx, ty, lane); break;
-            case 2: batch_tile<S, 2, RY ? RY : AutoRows<S, 2>::value, START>(G, parity, tx, ty, lane); break;
-            case 3: batch_tile<S, 3, RY ? RY : AutoRows<S, 3>::value, START>(G, parity, tx, ty, lane); break;
-            default: batch_tile<S, 4, RY ? RY : AutoRows<S, 4>::value, START>(G, parity, tx, ty, lane); break;
+        if (RFIX) {
+            batch_tile<S, RFIX ? RFIX : 1, ClassRows<S, RFIX ? RFIX : 1>::value, START>(G, parity, tx, ty, lane);
+        } else {
+            switch (G.radius) {
+                case 1: batch_tile<S, 1, RY ? RY : 4, START>(G, parity, tx, ty, lane); break;
+                case 2: batch_tile<S, 2, RY ? RY : 4, START>(G, parity, tx, ty, lane); break;
+                case 3: batch_tile<S, 3, RY ? RY : 4, START>(G, parity, tx, ty, lane); break;
+                default: batch_tile<S, 4, RY ? RY : 4, START>(G, parity, tx, ty, lane); break;
+            }
         }
     }
     stamp_end(stamp);
+    if (pdl && threadIdx.x == 0) griddep_wait();
 }
 
-using BatchFn = void (*)(const BatchGridDev*, int, int64_t, int, unsigned long long*);
+using BatchFn = void (*)(const BatchGridDev*, int, int64_t, int, unsigned long long*, int);
 
+// radius 1..4: the class kernel of that radius (per-radius plans); radius 0: the
+// mixed-radius kernel with tile_rows-row tiles (2, 4 or 8).
 template <typename S, bool START>
-BatchFn pick_batch(int tile_rows) {
+BatchFn pick_batch(int tile_rows, int radius) {
+    switch (radius) {
+        case 1: return batch_kernel<S, 1, 0, START>;
+        case 2: return batch_kernel<S, 2, 0, START>;
+        case 3: return batch_kernel<S, 3, 0, START>;
+        case 4: return batch_kernel<S, 4, 0, START>;
+    }
     switch (tile_rows) {
-        case 0: return batch_kernel<S, 0, START>;
-        case 2: return batch_kernel<S, 2, START>;
-        case 8: return batch_kernel<S, 8, START>;
-        default: return batch_kernel<S, 4, START>;
+        case 2: return batch_kernel<S, 0, 2, START>;
+        case 8: return batch_kernel<S, 0, 8, START>;
+        default: return batch_kernel<S, 0, 4, START>;
     }
 }
 
-// Tile height a plan with `tile_rows` uses for a grid of radius r and element size es.
+// Tile height a grid of radius r gets: per-radius mode (tile_rows == 0) uses ClassRows,
+// a uniform plan tile_rows.
 int rows_for(int tile_rows, int radius, size_t es) {
     if (tile_rows) return tile_rows;
-    return (es == 4 && radius == 1) ? 2 : 4;
+    if (es == 4) return radius == 1 ? 2 : radius == 3 ? 8 : 4;
+    return radius <= 2 ? 4 : 8;
 }
 
-BatchFn batch_fn(int dtype, int tile_rows, bool start) {
+BatchFn batch_fn(int dtype, int tile_rows, int radius, bool start) {
     switch (dtype) {
-        case SY_F32: return start ? pick_batch<float, true>(tile_rows) : pick_batch<float, false>(tile_rows);
+        case SY_F32: return start ? pick_batch<float, true>(tile_rows, radius) : pick_batch<float, false>(tile_rows, radius);
         case SY_BF16:
-            return start ? pick_batch<__nv_bfloat16, true>(tile_rows) : pick_batch<__nv_bfloat16, false>(tile_rows);
-        default: return start ? pick_batch<__half, true>(tile_rows) : pick_batch<__half, false>(tile_rows);
+            return start ? pick_batch<__nv_bfloat16, true>(tile_rows, radius)
+                         : pick_batch<__nv_bfloat16, false>(tile_rows, radius);
+        default:
+            return start ? pick_batch<__half, true>(tile_rows, radius) : pick_batch<__half, false>(tile_rows, radius);
     }
 }
 
 BatchPlan* as_plan(sy_batch_plan_t p) { return reinterpret_cast<BatchPlan*>(p); }
 
-// One persistent launch on q->launch; `slot` < 0 means untimed.
+// One step (or the start) of every grid: one persistent launch per class, on
+// q->launch; the first waits for the previous launch, later classes of the same step
+// overlap it.  `slot` < 0 means untimed.
 sy_status launch_batch(BatchPlan* P, bool start, int parity, int64_t slot) {
     Queue* q = P->q;
-    BatchFn fn = batch_fn(P->dtype, P->tile_rows, start);
     unsigned long long* stamp = slot >= 0 ? P->d_stamps + 4 * slot : nullptr;
-    const size_t smem = sizeof(int64_t) * static_cast<size_t>(P->n_grids + 1);
-    fn<<<P->blocks, P->threads, smem, q->launch>>>(P->d_desc, P->n_grids, P->total_tiles, parity, stamp);
-    SY_CUDA(cudaGetLastError());
-    ++q->launches;
-    if (slot >= 0) P->expected[slot] = static_cast<uint64_t>(P->blocks);
+    uint64_t blocks = 0;
+    for (size_t c = 0; c < P->classes.size(); ++c) {
+        const BatchClass& K = P->classes[c];
+        if (K.tiles == 0) continue;
+        BatchFn fn = batch_fn(P->dtype, P->tile_rows, K.radius, start);
+        const size_t smem = sizeof(int64_t) * static_cast<size_t>(K.n + 1);
+        const int pdl = c == 0 ? 1 : 2;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(K.blocks));
+        cfg.blockDim = dim3(P->threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = q->launch;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        SY_CUDA(cudaLaunchKernelEx(&cfg, fn, static_cast<const BatchGridDev*>(P->d_desc + K.desc_off), K.n, K.tiles,
+                                   parity, stamp, pdl));
+        ++q->launches;
+        blocks += static_cast<uint64_t>(K.blocks);
+    }
+    if (slot >= 0) P->expected[slot] = blocks;
     return SY_OK;
 }
 
@@ -195,8 +247,7 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
     if (tile_rows != 0 && tile_rows != 2 && tile_rows != 4 && tile_rows != 8)
         return fail(SY_ERR_INVALID_ARGUMENT, "tile_rows %d not in {0, 2, 4, 8}", tile_rows);
     const int V = static_cast<int>(16 / esize);
-    std::vector<BatchGridDev> desc(n_grids);
-    int64_t tiles = 0, points = 0;
+    // validation first, in the caller's order
     for (int g = 0; g < n_grids; ++g) {
         const sy_batch_grid& G = grids[g];
         if (G.ny < 1 || G.nx < 1 || G.pitch < G.nx)
@@ -216,20 +267,42 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
                 ranges_overlap(G.u_b, bytes, grids[h].u_a, hb) || ranges_overlap(G.u_b, bytes, grids[h].u_b, hb))
                 return fail(SY_ERR_ALIAS, "grids %d and %d overlap", h, g);
         }
-        BatchGridDev& D = desc[g];
-        D.ua = static_cast<char*>(G.u_a);
-        D.ub = static_cast<char*>(G.u_b);
-        D.ny = G.ny;
-        D.nx = G.nx;
-        D.pitch_bytes = pb;
-        D.tiles_x = (G.nx + 32 * V - 1) / (32 * V);
-        D.tile_begin = tiles;
-        D.radius = G.radius;
-        D.c2 = G.c2;
-        const int rows = rows_for(tile_rows, G.radius, esize);
-        tiles += D.tiles_x * ((G.ny + rows - 1) / rows);
-        points += G.ny * G.nx;
     }
+    // classes: per radius (tile_rows == 0) or one mixed class; descriptors class by class
+    std::vector<BatchClass> classes;
+    std::vector<BatchGridDev> desc;
+    desc.reserve(n_grids);
+    const int radii_lo = tile_rows == 0 ? 1 : 0, radii_hi = tile_rows == 0 ? 4 : 0;
+    int64_t total_tiles = 0, points = 0;
+    for (int r = radii_lo; r <= radii_hi; ++r) {
+        BatchClass K;
+        K.radius = r;
+        K.desc_off = static_cast<int64_t>(desc.size());
+        for (int g = 0; g < n_grids; ++g) {
+            const sy_batch_grid& G = grids[g];
+            if (r != 0 && G.radius != r) continue;
+            BatchGridDev D;
+            D.ua = static_cast<char*>(G.u_a);
+            D.ub = static_cast<char*>(G.u_b);
+            D.ny = G.ny;
+            D.nx = G.nx;
+            D.pitch_bytes = G.pitch * static_cast<int64_t>(esize);
+            D.tiles_x = (G.nx + 32 * V - 1) / (32 * V);
+            D.tile_begin = K.tiles;
+            D.radius = G.radius;
+            D.c2 = G.c2;
+            const int rows = rows_for(tile_rows, G.radius, esize);
+            K.tiles += D.tiles_x * ((G.ny + rows - 1) / rows);
+            points += G.ny * G.nx;
+            desc.push_back(D);
+            ++K.n;
+        }
+        if (K.n) {
+            total_tiles += K.tiles;
+            classes.push_back(K);
+        }
+    }
+    const int64_t tiles = total_tiles;
     SY_TRY(use_device(q));
     BatchPlan* P = new (std::nothrow) BatchPlan();
     if (!P) return fail(SY_ERR_OUT_OF_MEMORY, "plan allocation failed");
@@ -239,6 +312,7 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
     P->n_grids = n_grids;
     P->total_tiles = tiles;
     P->points = points;
+    P->classes = classes;
     cudaError_t e = cudaMalloc(&P->d_desc, sizeof(BatchGridDev) * desc.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(P->d_desc, desc.data(), sizeof(BatchGridDev) * desc.size(), cudaMemcpyHostToDevice);
@@ -247,12 +321,17 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
         e = cudaMalloc(&P->d_stamps, 4 * sizeof(unsigned long long));
         P->expected.assign(1, 0);
     }
-    int occ = 0;
-    const size_t smem = sizeof(int64_t) * static_cast<size_t>(n_grids + 1);
-    if (e == cudaSuccess) {
-        // the step kernel is the larger of the two; size the persistent grid for it
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, reinterpret_cast<const void*>(batch_fn(dtype, tile_rows, false)), kBatchThreads, smem);
+    for (BatchClass& K : P->classes) {  // persistent grid per class, sized for its step kernel
+        int occ = 0;
+        const size_t smem = sizeof(int64_t) * static_cast<size_t>(K.n + 1);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, reinterpret_cast<const void*>(batch_fn(dtype, tile_rows, K.radius, false)), kBatchThreads, smem);
+        if (occ < 1) occ = 1;
+        const int64_t want = (K.tiles + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+        const int64_t cap = static_cast<int64_t>(occ) * q->sm_count;
+        K.blocks = static_cast<int>(want < cap ? want : cap);
+        if (K.blocks < 1) K.blocks = 1;
     }
     if (e != cudaSuccess) {
         if (P->d_desc) cudaFree(P->d_desc);
@@ -260,10 +339,8 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
         delete P;
         return cuda_fail(e, "sy_stencil_batch_plan");
     }
-    if (occ < 1) occ = 1;
-    int64_t want = (tiles + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
-    int64_t cap = static_cast<int64_t>(occ) * q->sm_count;
-    P->blocks = static_cast<int>(want < cap ? want : cap);
+    P->blocks = 0;
+    for (const BatchClass& K : P->classes) P->blocks += K.blocks;
     *out = reinterpret_cast<sy_batch_plan_t>(P);
     return SY_OK;
 }
