@@ -354,6 +354,39 @@ def measure_batched(q, stream) -> dict:
             "mode": "one launch per radius class per step" if tile_rows == 0 else "one launch per step"}
 
 
+def measure_saxpy(q, stream) -> dict:
+    """SAXPY (the paper's Listing 1): N = 2^20, alpha = 2.5, seed 0 (the configured case,
+    latency-bound: 12.6 MB per call), and N = 2^28 (3.2 GB per call, HBM-bound); elements/s
+    and GB/s (12 B per element) over back-to-back calls, and the result checked bit for bit
+    against fl(fl(alpha x) + y) computed on the host in FP64 (exact for these inputs)."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import inputs
+
+    out = {}
+    for log2n in (20, 28):
+        n = 1 << log2n
+        x, y = inputs.saxpy_inputs(n, seed=0)
+        xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        zd = torch.empty_like(xd)
+        calls = 2000 if log2n == 20 else 40
+        run = lambda: [sy.sy_saxpy(q.handle, n, 2.5, xd, yd, zd) for _ in range(calls)]
+        run()
+        reps, ms, joules = _metered(q, stream, run, min_seconds=0.5)
+        per = ms / calls
+        z = zd.cpu().numpy()
+        want = ((np.float32(2.5) * x.astype(np.float64)).astype(np.float32).astype(np.float64)
+                + y.astype(np.float64)).astype(np.float32)
+        out[f"n_2^{log2n}"] = {"elements_per_s": n / (per * 1e-3), "gb_per_s": 12 * n / (per * 1e-3) / 1e9,
+                               "us_per_call": per * 1e3, "bit_exact": bool(np.array_equal(z.view(np.uint32),
+                                                                                         want.view(np.uint32))),
+                               "j_per_element": None if not joules else joules / (reps * calls * n)}
+        del xd, yd, zd
+    return out
+
+
 def measure_temporal(q, stream, T: int, dtype: str = "f32") -> dict:
     """The headline simulation (8192^2, 200 steps, 4 row chunks) with temporal blocking: the
     Taylor start, then 200/T passes of T steps each (halo T*r), from the resident initial field.
@@ -588,6 +621,7 @@ def run_gpu(args) -> None:
                                "j_per_update": None if not energy else energy["j_per_update"]}}
         for dt in ("bf16", "f16"):
             forms[dt] = measure_precision_form(q, stream, dt)
+        forms["saxpy"] = measure_saxpy(q, stream)
         forms["batched"] = measure_batched(q, stream)
         forms["temporal_T2"] = measure_temporal(q, stream, 2)
         forms["temporal_T4"] = measure_temporal(q, stream, 4)
