@@ -54,7 +54,8 @@ typedef enum sy_status {
     SY_ERR_TIMEOUT = 9,          /* a bounded device-side wait gave up */
     SY_ERR_OUT_OF_MEMORY = 10,   /* library-internal allocation failed */
     SY_ERR_NOT_READY = 11,       /* queried work has not completed */
-    SY_ERR_IO = 12               /* file read/write failed */
+    SY_ERR_IO = 12,              /* file read/write failed */
+    SY_ERR_NVML = 13             /* an NVML call failed (return code in sy_last_error()) */
 } sy_status;
 
 /* Storage type of a field.  Arithmetic is always FP32 (energy: FP64). */
@@ -473,6 +474,66 @@ typedef struct sy_cost_query {
  * log2 tile_rows, log2 threads, log2 chunks, log2 total bytes, halo read factor
  * (tile_rows + 2r) / tile_rows, log2 tile count. */
 sy_status sy_cost_features(const sy_cost_query* query, float* out);
+
+/* ------------------------------------------------------------------------- */
+/* Energy targets by frequency scaling (paper §4: a queue given the target    */
+/* MIN_EDP runs at the clock frequency that minimises the energy-delay        */
+/* product; frequencies are set through NVML on NVIDIA GPUs).                 */
+/*                                                                            */
+/* Device selection here is by NVML index, so that the host logic runs       */
+/* without a GPU; sy_clock_nvml_index maps a CUDA ordinal to it.              */
+/* Changing clocks alters a device-wide setting that outlives the process and */
+/* every other user of the GPU inherits; sy_clock_lock, sy_clock_unlock and   */
+/* sy_clock_sweep therefore refuse with SY_ERR_UNSUPPORTED, before any NVML   */
+/* call, unless the environment variable SY_CLOCK_CONTROL is "1".             */
+/* ------------------------------------------------------------------------- */
+typedef enum sy_energy_target {
+    SY_TARGET_MIN_TIME = 0,   /* minimise t */
+    SY_TARGET_MIN_ENERGY = 1, /* minimise E */
+    SY_TARGET_MIN_EDP = 2,    /* minimise E * t (the paper's MIN_EDP) */
+    SY_TARGET_MIN_ED2P = 3    /* minimise E * t^2 */
+} sy_energy_target;
+
+/* One measured (or predicted) operating point of a kernel or region. */
+typedef struct sy_freq_point {
+    uint32_t sm_mhz; /* SM (graphics) clock the point was taken at */
+    double seconds;  /* time of the measured work, > 0 */
+    double joules;   /* energy of the measured work, >= 0 */
+} sy_freq_point;
+
+/* Index of the point that minimises the target's objective.  Ties go to the
+ * higher clock, then to the lower index.  SY_ERR_INVALID_ARGUMENT for n < 1, an
+ * unknown target, or a time <= 0, energy < 0 or a non-finite value. */
+sy_status sy_clock_choose(int target, const sy_freq_point* points, int n, int* index);
+
+/* NVML index of CUDA device `cuda_device` (matched by PCI bus id). */
+sy_status sy_clock_nvml_index(int cuda_device, uint32_t* nvml_index);
+
+/* Read-only: the memory clock the device runs at and the SM clocks NVML
+ * supports with it, highest first (at most `cap` written, *n = how many exist). */
+sy_status sy_clock_supported(uint32_t nvml_index, uint32_t* mem_mhz, uint32_t* sm_mhz, int cap, int* n);
+
+/* Read-only: current and maximum SM clock. */
+sy_status sy_clock_current(uint32_t nvml_index, uint32_t* sm_mhz, uint32_t* sm_max_mhz);
+
+/* Lock the SM clock to `sm_mhz` (one of sy_clock_supported's values, else
+ * SY_ERR_INVALID_ARGUMENT), and release the lock.  Gated as described above;
+ * SY_ERR_NVML if NVML refuses (e.g. no permission). */
+sy_status sy_clock_lock(uint32_t nvml_index, uint32_t sm_mhz);
+sy_status sy_clock_unlock(uint32_t nvml_index);
+
+/* Called by sy_clock_sweep with the clock locked at sm_mhz: runs the work and
+ * reports its time and energy; returns 0 on success, anything else aborts. */
+typedef int (*sy_measure_fn)(void* ctx, uint32_t sm_mhz, double* seconds, double* joules);
+
+/* Per-kernel frequency selection by measurement: for each of the n candidate
+ * clocks in order, lock it, call `measure`, and record the point in
+ * points[i]; then release the lock (always, also after a failure) and choose
+ * by `target` (*best = index into points).  Gated as described above.  Every
+ * candidate is validated before the first lock.  A failing measure returns
+ * SY_ERR_INVALID_ARGUMENT with the lock already released. */
+sy_status sy_clock_sweep(uint32_t nvml_index, const uint32_t* sm_mhz, int n, sy_measure_fn measure, void* ctx,
+                         int target, sy_freq_point* points, int* best);
 
 /* Allocation-free form of sy_wave_energy.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the

@@ -30,7 +30,7 @@ STATUS = {
     0: "SY_OK", 1: "SY_ERR_INVALID_ARGUMENT", 2: "SY_ERR_NULL_POINTER", 3: "SY_ERR_ALIAS",
     4: "SY_ERR_BAD_CHUNKS", 5: "SY_ERR_HALO_TOO_SMALL", 6: "SY_ERR_UNSUPPORTED", 7: "SY_ERR_CUDA",
     8: "SY_ERR_NVML_UNAVAILABLE", 9: "SY_ERR_TIMEOUT", 10: "SY_ERR_OUT_OF_MEMORY", 11: "SY_ERR_NOT_READY",
-    12: "SY_ERR_IO",
+    12: "SY_ERR_IO", 13: "SY_ERR_NVML",
 }
 
 
@@ -66,6 +66,14 @@ SY_COST_FEATURES = 13
 
 class Transfer(C.Structure):
     _fields_ = [("src", C.c_int32), ("dst", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64)]
+
+
+class FreqPoint(C.Structure):
+    _fields_ = [("sm_mhz", C.c_uint32), ("seconds", C.c_double), ("joules", C.c_double)]
+
+
+SY_TARGET_MIN_TIME, SY_TARGET_MIN_ENERGY, SY_TARGET_MIN_EDP, SY_TARGET_MIN_ED2P = 0, 1, 2, 3
+MEASURE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double))
 
 
 class StencilParams(C.Structure):
@@ -145,6 +153,13 @@ _SIGS = {
     "sy_stencil_batch_destroy": [_p],
     "sy_stencil_multistep": [_p, _p, C.c_int, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_wave_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
+    "sy_clock_choose": [C.c_int, _p, C.c_int, _p],
+    "sy_clock_nvml_index": [C.c_int, _p],
+    "sy_clock_supported": [C.c_uint32, _p, _p, C.c_int, _p],
+    "sy_clock_current": [C.c_uint32, _p, _p],
+    "sy_clock_lock": [C.c_uint32, C.c_uint32],
+    "sy_clock_unlock": [C.c_uint32],
+    "sy_clock_sweep": [C.c_uint32, _p, C.c_int, MEASURE_FN, _p, C.c_int, _p, _p],
 }
 _RESTYPE = {"sy_status_string": C.c_char_p, "sy_last_error": C.c_char_p, "sy_abi_version": C.c_int}
 
@@ -662,3 +677,62 @@ class Queue:
     @property
     def launches(self) -> int:
         return sy_queue_launch_count(self.handle)
+
+
+# ---- energy targets by frequency scaling ------------------------------------------
+
+def sy_clock_choose(target: int, points) -> int:
+    """Index of the (sm_mhz, seconds, joules) point minimising the target's objective."""
+    arr = (FreqPoint * max(1, len(points)))(*[FreqPoint(int(f), float(t), float(j)) for f, t, j in points])
+    idx = C.c_int(-1)
+    _call("sy_clock_choose", int(target), arr, len(points), C.byref(idx))
+    return idx.value
+
+
+def sy_clock_nvml_index(cuda_device: int) -> int:
+    out = C.c_uint32(0)
+    _call("sy_clock_nvml_index", int(cuda_device), C.byref(out))
+    return out.value
+
+
+def sy_clock_supported(nvml_index: int) -> tuple[int, list[int]]:
+    """(memory clock, supported SM clocks highest first), read-only."""
+    mem, n = C.c_uint32(0), C.c_int(0)
+    _call("sy_clock_supported", int(nvml_index), C.byref(mem), None, 0, C.byref(n))
+    buf = (C.c_uint32 * max(1, n.value))()
+    _call("sy_clock_supported", int(nvml_index), C.byref(mem), buf, n.value, C.byref(n))
+    return mem.value, list(buf[: n.value])
+
+
+def sy_clock_current(nvml_index: int) -> tuple[int, int]:
+    cur, mx = C.c_uint32(0), C.c_uint32(0)
+    _call("sy_clock_current", int(nvml_index), C.byref(cur), C.byref(mx))
+    return cur.value, mx.value
+
+
+def sy_clock_lock(nvml_index: int, sm_mhz: int) -> None:
+    _call("sy_clock_lock", int(nvml_index), int(sm_mhz))
+
+
+def sy_clock_unlock(nvml_index: int) -> None:
+    _call("sy_clock_unlock", int(nvml_index))
+
+
+def sy_clock_sweep(nvml_index: int, candidates, measure, target: int = SY_TARGET_MIN_EDP):
+    """Lock each candidate SM clock in turn, call measure(sm_mhz) -> (seconds, joules), release
+    the lock, and choose by target.  Returns (best index, [(sm_mhz, seconds, joules), ...])."""
+    def cb(_ctx, mhz, t_out, j_out):
+        try:
+            t, j = measure(int(mhz))
+            t_out[0], j_out[0] = float(t), float(j)
+            return 0
+        except Exception:  # reported to the library as a failed measurement
+            return 1
+
+    fn = MEASURE_FN(cb)
+    n = len(candidates)
+    freqs = (C.c_uint32 * max(1, n))(*[int(f) for f in candidates])
+    pts = (FreqPoint * max(1, n))()
+    best = C.c_int(-1)
+    _call("sy_clock_sweep", int(nvml_index), freqs, n, fn, None, int(target), pts, C.byref(best))
+    return best.value, [(p.sm_mhz, p.seconds, p.joules) for p in pts[:n]]

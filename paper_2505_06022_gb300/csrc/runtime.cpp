@@ -64,10 +64,16 @@ static ret_t (*p_init)(void) = nullptr;
 static ret_t (*p_by_pci)(const char*, device_t*) = nullptr;
 static ret_t (*p_energy)(device_t, unsigned long long*) = nullptr;
 
+static void* g_handle = nullptr;
+
+// SY_NVML_LIB names another library exporting the same NVML entry points (a test
+// double); by default the driver's libnvidia-ml.so.1.
 static void load() {
     if (fault_enabled("nvml_missing")) return;
-    void* h = dlopen("libnvidia-ml.so.1", RTLD_NOW | RTLD_LOCAL);
+    const char* path = getenv("SY_NVML_LIB");
+    void* h = dlopen(path && *path ? path : "libnvidia-ml.so.1", RTLD_NOW | RTLD_LOCAL);
     if (!h) return;
+    g_handle = h;
     p_init = reinterpret_cast<ret_t (*)(void)>(dlsym(h, "nvmlInit_v2"));
     p_by_pci = reinterpret_cast<ret_t (*)(const char*, device_t*)>(dlsym(h, "nvmlDeviceGetHandleByPciBusId_v2"));
     p_energy = reinterpret_cast<ret_t (*)(device_t, unsigned long long*)>(
@@ -77,10 +83,12 @@ static void load() {
     g_ok = true;
 }
 
-static bool available() {
+bool available() {
     std::call_once(g_once, load);
     return g_ok && !fault_enabled("nvml_missing");
 }
+
+void* symbol(const char* name) { return available() ? dlsym(g_handle, name) : nullptr; }
 
 static bool device_for(int cuda_device, device_t* out) {
     if (!available()) return false;
@@ -333,6 +341,7 @@ const char* sy_status_string(sy_status s) {
         case SY_ERR_OUT_OF_MEMORY: return "SY_ERR_OUT_OF_MEMORY";
         case SY_ERR_NOT_READY: return "SY_ERR_NOT_READY";
         case SY_ERR_IO: return "SY_ERR_IO";
+        case SY_ERR_NVML: return "SY_ERR_NVML";
     }
     return "SY_ERR_UNKNOWN";
 }

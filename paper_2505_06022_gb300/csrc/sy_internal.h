@@ -31,6 +31,13 @@ void clear_error();
 // Host-side fault injection for tests: SY_FAULT=<name>[,<name>...].
 bool fault_enabled(const char* name);
 
+namespace nvml {
+// True once NVML is loaded and initialised (libnvidia-ml.so.1, or SY_NVML_LIB).
+bool available();
+// An entry point of the loaded NVML library, or nullptr.
+void* symbol(const char* name);
+}  // namespace nvml
+
 // ---- device-side kernel timestamps -----------------------------------------------
 // Each timed launch owns one stamp slot of 4 x u64 in device memory, zeroed before
 // use: [0] = ~(earliest block start), [1] = latest block end (both %globaltimer, ns),

@@ -115,9 +115,11 @@ def test_graph_run_equals_per_grid_steps(q):
         sy.sy_stencil_batch_destroy(plan)
 
 
-def test_config2_full_batch_sampled(q):
+@pytest.mark.parametrize("tile_rows", [0, 4], ids=["classes", "rows4"])
+def test_config2_full_batch_sampled(q, tile_rows):
     """64 grids, sides log-uniform in [256, 4096] (seed 1), radius from {1, 2, 4}, 100 steps in one
-    graph; sampled points of the largest and smallest grids against the oracle (light cone)."""
+    graph, as per-radius-class launches (the timed configuration) and as one launch per step with
+    4-row tiles; sampled points of the largest and smallest grids against the oracle (light cone)."""
     torch = torch_cuda()
     shapes = inputs.batch_grids()
     host, dev = [], []
@@ -128,7 +130,7 @@ def test_config2_full_batch_sampled(q):
         ub[:, :nx] = torch.from_numpy(u0).cuda()
         host.append(u0)
         dev.append((torch.empty_like(ub), ub, pitch))
-    plan = plan_for(q, shapes, dev, "f32", 4)
+    plan = plan_for(q, shapes, dev, "f32", tile_rows)
     try:
         sy.sy_stencil_batch_start(plan)
         sy.sy_stencil_batch_capture(plan, 100)
