@@ -3,12 +3,14 @@
 // captured into a CUDA graph.
 //
 // Work list: the warp tiles of all grids, concatenated in plan order (each grid's
-// tiles in row-major order).  A persistent grid of SMs x occupancy blocks strides
-// over that list; a warp finds its grid by binary search over the tiles' prefix
-// sums (held in shared memory) and runs the same tile code as the single-field
-// kernel (wave_tile), with the grid's own radius selected at run time.  Grids of
-// every size therefore share the GPU in one launch instead of paying one
-// launch (and one partially filled last wave) per grid.
+// tiles in row-major order), stored once per plan as a table of packed (grid,
+// tile column, tile row) entries.  A persistent grid of SMs x occupancy blocks
+// strides over that table; a warp reads its next entry one tile ahead (a
+// broadcast load that is in flight while the current tile computes), so moving to
+// another grid costs no search and no division, and runs the same tile code as
+// the single-field kernel (wave_tile).  Grids of every size therefore share the
+// GPU in one launch instead of paying one launch (and one partially filled last
+// wave) per grid.
 //
 // Buffers: grid g owns u_a and u_b.  A step with parity 0 reads u_a (u^{n-1})
 // and u_b (u^n) and writes u^{n+1} over u_a; parity 1 swaps the roles.  The
@@ -26,7 +28,6 @@ struct BatchGridDev {
     char* ub;
     int64_t ny, nx, pitch_bytes;
     int64_t tiles_x;
-    int64_t tile_begin;
     int32_t radius;
     float c2;
 };
@@ -37,6 +38,7 @@ struct BatchGridDev {
 struct BatchClass {
     int radius = 0;           // 0 = mixed radii
     int64_t desc_off = 0;     // first descriptor of the class in d_desc
+    int64_t tile_off = 0;     // first entry of the class in d_tiles
     int n = 0;                // grids in the class
     int64_t tiles = 0;
     int blocks = 0;           // persistent grid size of the class's launch
@@ -51,6 +53,7 @@ struct BatchPlan {
     int64_t points = 0;
     std::vector<BatchClass> classes;
     BatchGridDev* d_desc = nullptr;
+    uint64_t* d_tiles = nullptr;             // packed work list, class by class
     unsigned long long* d_stamps = nullptr;  // slot 0: last direct launch; 1..: graph launches
     int64_t stamp_slots = 0;
     std::vector<uint64_t> expected;          // blocks per stamped launch (index = slot)
@@ -64,7 +67,15 @@ struct BatchPlan {
 namespace {
 
 constexpr int kBatchThreads = 128;
-constexpr int kMaxBatchGrids = 4096;  // prefix sums in shared memory: 32 KiB
+constexpr int kMaxBatchGrids = 4096;  // grid index: 12 bits of a work-list entry
+
+// Work-list entry: grid index within its class (bits 52..63), tile row (bits 20..51),
+// tile column (bits 0..19).
+constexpr int kTileXBits = 20, kTileYBits = 32;
+__host__ __device__ __forceinline__ uint64_t pack_tile(int64_t g, int64_t tx, int64_t ty) {
+    return (static_cast<uint64_t>(g) << (kTileXBits + kTileYBits)) | (static_cast<uint64_t>(ty) << kTileXBits) |
+           static_cast<uint64_t>(tx);
+}
 
 template <typename S, int R, int RY, bool START>
 __device__ __forceinline__ void batch_tile(const BatchGridDev& G, int parity, int64_t tx, int64_t ty, int lane) {
@@ -99,45 +110,23 @@ struct ClassRows {
 // independent launch of the same step; with either, completion implies the
 // predecessor's completion.
 template <typename S, int RFIX, int RY, bool START>
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev* __restrict__ grids, int n_grids,
-                                                              int64_t total_tiles, int parity,
-                                                              unsigned long long* stamp, int pdl) {
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev* __restrict__ grids,
+                                                              const uint64_t* __restrict__ work, int64_t total_tiles,
+                                                              int parity, unsigned long long* stamp, int pdl) {
     static_assert(RFIX != 0 || RY != 0, "a mixed-radius kernel needs a tile height");
-    extern __shared__ int64_t s_begin[];  // n_grids + 1 prefix sums
     if (pdl == 1) griddep_wait();
     if (pdl) griddep_launch_dependents();
     stamp_begin(stamp);
-    for (int i = threadIdx.x; i <= n_grids; i += blockDim.x) s_begin[i] = i < n_grids ? grids[i].tile_begin : total_tiles;
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps_per_block = blockDim.x >> 5;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * warps_per_block;
-    int g = -1;
-    int64_t tx = 0, ty = 0, dx = 0, dy = 0, tiles_x = 1;
-    for (int64_t t = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); t < total_tiles;
-         t += nwarps) {
-        if (g >= 0 && t < s_begin[g + 1]) {  // same grid: advance the coordinates
-            tx += dx;
-            ty += dy;
-            if (tx >= tiles_x) {
-                tx -= tiles_x;
-                ++ty;
-            }
-        } else {  // entered another grid: find it (warp-uniform binary search) and divide once
-            int lo = g < 0 ? 0 : g, hi = n_grids - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_begin[mid] <= t) lo = mid;
-                else hi = mid - 1;
-            }
-            g = lo;
-            tiles_x = grids[g].tiles_x;
-            const int64_t local = t - s_begin[g];
-            ty = local / tiles_x;
-            tx = local - ty * tiles_x;
-            dy = nwarps / tiles_x;
-            dx = nwarps - dy * tiles_x;
-        }
+    int64_t t = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5);
+    uint64_t cur = t < total_tiles ? __ldg(work + t) : 0;
+    for (; t < total_tiles; t += nwarps) {
+        const uint64_t next = t + nwarps < total_tiles ? __ldg(work + t + nwarps) : 0;
+        const int g = static_cast<int>(cur >> (kTileXBits + kTileYBits));
+        const int64_t ty = static_cast<int64_t>((cur >> kTileXBits) & ((1ull << kTileYBits) - 1));
+        const int64_t tx = static_cast<int64_t>(cur & ((1ull << kTileXBits) - 1));
         const BatchGridDev& G = grids[g];
         if (RFIX) {
             batch_tile<S, RFIX ? RFIX : 1, ClassRows<S, RFIX ? RFIX : 1>::value, START>(G, parity, tx, ty, lane);
@@ -149,12 +138,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev
                 default: batch_tile<S, 4, RY ? RY : 4, START>(G, parity, tx, ty, lane); break;
             }
         }
+        cur = next;
     }
     stamp_end(stamp);
     if (pdl && threadIdx.x == 0) griddep_wait();
 }
 
-using BatchFn = void (*)(const BatchGridDev*, int, int64_t, int, unsigned long long*, int);
+using BatchFn = void (*)(const BatchGridDev*, const uint64_t*, int64_t, int, unsigned long long*, int);
 
 // radius 1..4: the class kernel of that radius (per-radius plans); radius 0: the
 // mixed-radius kernel with tile_rows-row tiles (2, 4 or 8).
@@ -205,20 +195,20 @@ sy_status launch_batch(BatchPlan* P, bool start, int parity, int64_t slot) {
         const BatchClass& K = P->classes[c];
         if (K.tiles == 0) continue;
         BatchFn fn = batch_fn(P->dtype, P->tile_rows, K.radius, start);
-        const size_t smem = sizeof(int64_t) * static_cast<size_t>(K.n + 1);
         const int pdl = c == 0 ? 1 : 2;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(static_cast<unsigned>(K.blocks));
         cfg.blockDim = dim3(P->threads);
-        cfg.dynamicSmemBytes = smem;
+        cfg.dynamicSmemBytes = 0;
         cfg.stream = q->launch;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        SY_CUDA(cudaLaunchKernelEx(&cfg, fn, static_cast<const BatchGridDev*>(P->d_desc + K.desc_off), K.n, K.tiles,
-                                   parity, stamp, pdl));
+        SY_CUDA(cudaLaunchKernelEx(&cfg, fn, static_cast<const BatchGridDev*>(P->d_desc + K.desc_off),
+                                   static_cast<const uint64_t*>(P->d_tiles + K.tile_off), K.tiles, parity, stamp,
+                                   pdl));
         ++q->launches;
         blocks += static_cast<uint64_t>(K.blocks);
     }
@@ -271,6 +261,7 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
     // classes: per radius (tile_rows == 0) or one mixed class; descriptors class by class
     std::vector<BatchClass> classes;
     std::vector<BatchGridDev> desc;
+    std::vector<uint64_t> work;
     desc.reserve(n_grids);
     const int radii_lo = tile_rows == 0 ? 1 : 0, radii_hi = tile_rows == 0 ? 4 : 0;
     int64_t total_tiles = 0, points = 0;
@@ -278,6 +269,7 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
         BatchClass K;
         K.radius = r;
         K.desc_off = static_cast<int64_t>(desc.size());
+        K.tile_off = static_cast<int64_t>(work.size());
         for (int g = 0; g < n_grids; ++g) {
             const sy_batch_grid& G = grids[g];
             if (r != 0 && G.radius != r) continue;
@@ -288,11 +280,16 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
             D.nx = G.nx;
             D.pitch_bytes = G.pitch * static_cast<int64_t>(esize);
             D.tiles_x = (G.nx + 32 * V - 1) / (32 * V);
-            D.tile_begin = K.tiles;
             D.radius = G.radius;
             D.c2 = G.c2;
             const int rows = rows_for(tile_rows, G.radius, esize);
-            K.tiles += D.tiles_x * ((G.ny + rows - 1) / rows);
+            const int64_t tiles_y = (G.ny + rows - 1) / rows;
+            if (D.tiles_x >= (int64_t(1) << kTileXBits) || tiles_y >= (int64_t(1) << kTileYBits))
+                return fail(SY_ERR_INVALID_ARGUMENT, "grid %d: %lld x %lld is too large for a batched plan", g,
+                            (long long)G.ny, (long long)G.nx);
+            for (int64_t ty = 0; ty < tiles_y; ++ty)
+                for (int64_t tx = 0; tx < D.tiles_x; ++tx) work.push_back(pack_tile(K.n, tx, ty));
+            K.tiles += D.tiles_x * tiles_y;
             points += G.ny * G.nx;
             desc.push_back(D);
             ++K.n;
@@ -316,6 +313,9 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
     cudaError_t e = cudaMalloc(&P->d_desc, sizeof(BatchGridDev) * desc.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(P->d_desc, desc.data(), sizeof(BatchGridDev) * desc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_tiles, sizeof(uint64_t) * work.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->d_tiles, work.data(), sizeof(uint64_t) * work.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         P->stamp_slots = 1;
         e = cudaMalloc(&P->d_stamps, 4 * sizeof(unsigned long long));
@@ -323,10 +323,9 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
     }
     for (BatchClass& K : P->classes) {  // persistent grid per class, sized for its step kernel
         int occ = 0;
-        const size_t smem = sizeof(int64_t) * static_cast<size_t>(K.n + 1);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, reinterpret_cast<const void*>(batch_fn(dtype, tile_rows, K.radius, false)), kBatchThreads, smem);
+                &occ, reinterpret_cast<const void*>(batch_fn(dtype, tile_rows, K.radius, false)), kBatchThreads, 0);
         if (occ < 1) occ = 1;
         const int64_t want = (K.tiles + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
         const int64_t cap = static_cast<int64_t>(occ) * q->sm_count;
@@ -335,6 +334,7 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
     }
     if (e != cudaSuccess) {
         if (P->d_desc) cudaFree(P->d_desc);
+        if (P->d_tiles) cudaFree(P->d_tiles);
         if (P->d_stamps) cudaFree(P->d_stamps);
         delete P;
         return cuda_fail(e, "sy_stencil_batch_plan");
@@ -460,6 +460,7 @@ sy_status sy_stencil_batch_destroy(sy_batch_plan_t ph) {
     cudaStreamSynchronize(P->q->stream);
     if (P->exec) cudaGraphExecDestroy(P->exec);
     if (P->d_desc) cudaFree(P->d_desc);
+    if (P->d_tiles) cudaFree(P->d_tiles);
     if (P->d_stamps) cudaFree(P->d_stamps);
     delete P;
     return SY_OK;
