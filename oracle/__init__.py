@@ -54,6 +54,16 @@ def lib() -> C.CDLL:
             "oracle_mlp_param_count": (_i64, [C.c_int, C.c_int, C.c_int]),
             "oracle_mlp_forward": (C.c_int, [_i64, C.c_int, C.c_int, C.c_int, _p, _p, _p]),
             "oracle_mlp_loss_grad": (C.c_double, [_i64, C.c_int, C.c_int, C.c_int, _p, _p, _p, _p]),
+            "oracle_wave3d_step_f64": (C.c_int, [_i64, _i64, _i64, C.c_int, C.c_double, _p, _p, _p]),
+            "oracle_wave3d_start_f64": (C.c_int, [_i64, _i64, _i64, C.c_int, C.c_double, _p, _p]),
+            "oracle_wave3d_run_f64": (C.c_int, [_i64, _i64, _i64, C.c_int, C.c_double, _i64, _p, _p, _p]),
+            "oracle_wave3d_step_mirror": (C.c_int, [C.c_int, _i64, _i64, _i64, C.c_int, C.c_float, _p, _p, _p]),
+            "oracle_wave3d_start_mirror": (C.c_int, [C.c_int, _i64, _i64, _i64, C.c_int, C.c_float, _p, _p]),
+            "oracle_wave3d_run_mirror": (C.c_int, [C.c_int, _i64, _i64, _i64, C.c_int, C.c_float, _i64, _p, _p,
+                                                   _p]),
+            "oracle_wave3d_energy_f64": (C.c_double, [_i64, _i64, _i64, C.c_int, C.c_double, _p, _p, _p, _p]),
+            "oracle_rm_box": (C.c_int, [C.c_int, _p, C.c_int, _p, _p, _p, _p]),
+            "oracle_rm_box_transfers": (C.c_int, [C.c_int, _p, C.c_int, _p, _p, C.c_int, _p, _p, C.c_int]),
             "oracle_adam_step": (None, [_i64, _p, _p, _p, _p, _i64, C.c_double, C.c_double, C.c_double,
                                         C.c_double]),
         }
@@ -255,6 +265,107 @@ def wave_energy_f64(u_new: np.ndarray, u_old: np.ndarray, r: int, c2: float) -> 
     E = lib().oracle_wave_energy_f64(ny, nx, r, c2, _ptr(un), _ptr(uo), C.addressof(kin), C.addressof(pot),
                                      C.addressof(mag))
     return {"E": E, "kin": kin.value, "pot": pot.value, "abs_sum": mag.value}
+
+
+# --- 8. 3D leapfrog --------------------------------------------------------------
+
+def wave3d_step_f64(u_prev: np.ndarray, u_cur: np.ndarray, r: int, c2: float) -> np.ndarray:
+    up = np.ascontiguousarray(u_prev, np.float64)
+    uc = np.ascontiguousarray(u_cur, np.float64)
+    nz, ny, nx = uc.shape
+    un = np.empty_like(uc)
+    _check(lib().oracle_wave3d_step_f64(nz, ny, nx, r, c2, _ptr(up), _ptr(uc), _ptr(un)), "wave3d_step_f64")
+    return un
+
+
+def wave3d_start_f64(u0: np.ndarray, r: int, c2: float) -> np.ndarray:
+    u0 = np.ascontiguousarray(u0, np.float64)
+    nz, ny, nx = u0.shape
+    um1 = np.empty_like(u0)
+    _check(lib().oracle_wave3d_start_f64(nz, ny, nx, r, c2, _ptr(u0), _ptr(um1)), "wave3d_start_f64")
+    return um1
+
+
+def wave3d_run_f64(u0: np.ndarray, steps: int, r: int, c2: float) -> tuple[np.ndarray, np.ndarray]:
+    u0 = np.ascontiguousarray(u0, np.float64)
+    nz, ny, nx = u0.shape
+    prev, cur = np.empty_like(u0), np.empty_like(u0)
+    _check(lib().oracle_wave3d_run_f64(nz, ny, nx, r, c2, steps, _ptr(u0), _ptr(prev), _ptr(cur)), "wave3d_run_f64")
+    return prev, cur
+
+
+def wave3d_step_mirror(dtype: int, u_prev: np.ndarray, u_cur: np.ndarray, r: int, c2: float) -> np.ndarray:
+    up, uc = _storage(u_prev, dtype), _storage(u_cur, dtype)
+    nz, ny, nx = uc.shape
+    un = np.empty_like(uc)
+    _check(lib().oracle_wave3d_step_mirror(dtype, nz, ny, nx, r, c2, _ptr(up), _ptr(uc), _ptr(un)),
+           "wave3d_step_mirror")
+    return un
+
+
+def wave3d_start_mirror(dtype: int, u0: np.ndarray, r: int, c2: float) -> np.ndarray:
+    u0 = _storage(u0, dtype)
+    nz, ny, nx = u0.shape
+    um1 = np.empty_like(u0)
+    _check(lib().oracle_wave3d_start_mirror(dtype, nz, ny, nx, r, c2, _ptr(u0), _ptr(um1)), "wave3d_start_mirror")
+    return um1
+
+
+def wave3d_run_mirror(dtype: int, u0: np.ndarray, steps: int, r: int, c2: float) -> tuple[np.ndarray, np.ndarray]:
+    u0 = _storage(u0, dtype)
+    nz, ny, nx = u0.shape
+    prev, cur = np.empty_like(u0), np.empty_like(u0)
+    _check(lib().oracle_wave3d_run_mirror(dtype, nz, ny, nx, r, c2, steps, _ptr(u0), _ptr(prev), _ptr(cur)),
+           "wave3d_run_mirror")
+    return prev, cur
+
+
+def wave3d_energy_f64(u_new: np.ndarray, u_old: np.ndarray, r: int, c2: float) -> dict:
+    un = np.ascontiguousarray(u_new, np.float64)
+    uo = np.ascontiguousarray(u_old, np.float64)
+    nz, ny, nx = un.shape
+    kin, pot = C.c_double(), C.c_double()
+    E = lib().oracle_wave3d_energy_f64(nz, ny, nx, r, c2, _ptr(un), _ptr(uo), C.addressof(kin), C.addressof(pot))
+    return {"E": E, "kin": kin.value, "pot": pot.value}
+
+
+# --- 9. Range mappers on boxes ---------------------------------------------------
+
+RM_ONE_TO_ONE, RM_NEIGHBOURHOOD, RM_SLICE, RM_ALL, RM_FIXED = 0, 1, 2, 3, 4
+
+
+def _box(b) -> np.ndarray:
+    """((lo0, lo1, lo2), (hi0, hi1, hi2)) -> int64[6]."""
+    (l0, l1, l2), (h0, h1, h2) = b
+    return np.array([l0, l1, l2, h0, h1, h2], np.int64)
+
+
+def _unbox(a) -> tuple:
+    return (tuple(int(v) for v in a[:3]), tuple(int(v) for v in a[3:6]))
+
+
+def rm_box(kind: int, chunk, extent, radius=(0, 0, 0), dim: int = 0, fixed=((0, 0, 0), (0, 0, 0))) -> tuple:
+    rad = np.array(radius, np.int64)
+    fx, ch, out = _box(fixed), _box(chunk), np.zeros(6, np.int64)
+    ext = np.array(extent, np.int64)
+    _check(lib().oracle_rm_box(kind, _ptr(rad), dim, _ptr(fx), _ptr(ch), _ptr(ext), _ptr(out)), "rm_box")
+    return _unbox(out)
+
+
+def rm_box_transfers(kind: int, chunks, extent, radius=(0, 0, 0), dim: int = 0,
+                     fixed=((0, 0, 0), (0, 0, 0))) -> list:
+    """[(src, dst, box)] in dst-major, src-minor order."""
+    rad = np.array(radius, np.int64)
+    fx = _box(fixed)
+    ch = np.ascontiguousarray(np.concatenate([_box(c) for c in chunks]) if chunks else np.zeros(6, np.int64))
+    ext = np.array(extent, np.int64)
+    cap = max(1, len(chunks) * len(chunks))
+    out = np.zeros(8 * cap, np.int64)
+    n = lib().oracle_rm_box_transfers(kind, _ptr(rad), dim, _ptr(fx), _ptr(ch), len(chunks), _ptr(ext), _ptr(out),
+                                      cap)
+    if n < 0:
+        raise ValueError("oracle rm_box_transfers failed")
+    return [(int(out[8 * t]), int(out[8 * t + 1]), _unbox(out[8 * t + 2: 8 * t + 8])) for t in range(n)]
 
 
 # --- 7. MLP --------------------------------------------------------------------

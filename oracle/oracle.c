@@ -39,8 +39,13 @@
  *        E^{n+1/2} = sum (u^{n+1}-u^n)^2 - c2 * sum u^{n+1} (L u^n)      in FP64.
  *   7. MLP cost model, 3 layers: h1 = silu(W1 x + b1), h2 = silu(W2 h1 + b2),
  *      y = W3 h2 + b3; loss = mean over all outputs of (y - t)^2; Adam.  FP64.
+ *   8. The leapfrog step of sections 4-6 on an nz x ny x nx grid (a second
+ *      workload): the operator is the sum of three one-dimensional second
+ *      differences; FP64, precision mirror and energy.
+ *   9. Range mappers on 3D boxes (one_to_one from paper §3 Listing 2; the
+ *      others are this build's) and the transfers a chunk list implies.
  *
- * The wave workload, the reduced-precision storage and the cost model are not in
+ * The wave workloads, the reduced-precision storage and the cost model are not in
  * the paper; the readings used for them are the ones stated above.
  */
 #include <math.h>
@@ -551,4 +556,271 @@ ORACLE_API void oracle_adam_step(int64_t n, double* params, const double* grad, 
         double vhat = v[i] / bc2;
         params[i] -= lr * mhat / (sqrt(vhat) + eps);
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* 8. Leapfrog wave step in 3D (second workload), FP64 and precision mirror   */
+/* ------------------------------------------------------------------------- */
+/* Grid nz x ny x nx, point (k, i, j) at (k*ny + i)*nx + j.  The operator is the
+ * sum of the three one-dimensional second differences of section 3, each with its
+ * own w_0 term, Dirichlet-zero ghosts in every direction:
+ *   L u = 3 w_0 u + sum_m w_m ( ((u_{k,i-m,j}+u_{k,i+m,j}) + (u_{k,i,j-m}+u_{k,i,j+m}))
+ *                               + (u_{k-m,i,j}+u_{k+m,i,j}) )
+ * The recurrence and the start are those of section 4; the mirror evaluates the
+ * bracketing above in FP32, 3 w_0 rounded once to FP32. */
+
+static inline double ghost3(const double* u, int64_t nz, int64_t ny, int64_t nx, int64_t k, int64_t i, int64_t j) {
+    if (k < 0 || k >= nz || i < 0 || i >= ny || j < 0 || j >= nx) return 0.0;
+    return u[(k * ny + i) * nx + j];
+}
+
+static double lap3_64(const double* u, int64_t nz, int64_t ny, int64_t nx, int r, const double* w, int64_t k,
+                      int64_t i, int64_t j) {
+    double acc = (3.0 * w[0]) * u[(k * ny + i) * nx + j];
+    for (int m = 1; m <= r; ++m) {
+        double vert = ghost3(u, nz, ny, nx, k, i - m, j) + ghost3(u, nz, ny, nx, k, i + m, j);
+        double horz = ghost3(u, nz, ny, nx, k, i, j - m) + ghost3(u, nz, ny, nx, k, i, j + m);
+        double depth = ghost3(u, nz, ny, nx, k - m, i, j) + ghost3(u, nz, ny, nx, k + m, i, j);
+        acc = acc + w[m] * ((vert + horz) + depth);
+    }
+    return acc;
+}
+
+/* u_next may be u_prev; it must not be u_cur. */
+ORACLE_API int oracle_wave3d_step_f64(int64_t nz, int64_t ny, int64_t nx, int r, double c2, const double* u_prev,
+                                      const double* u_cur, double* u_next) {
+    double w[5];
+    if (oracle_d2_weights(r, w)) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t i = 0; i < ny; ++i)
+            for (int64_t j = 0; j < nx; ++j) {
+                int64_t p = (k * ny + i) * nx + j;
+                double u = u_cur[p];
+                u_next[p] = (2.0 * u - u_prev[p]) + c2 * lap3_64(u_cur, nz, ny, nx, r, w, k, i, j);
+            }
+    return 0;
+}
+
+ORACLE_API int oracle_wave3d_start_f64(int64_t nz, int64_t ny, int64_t nx, int r, double c2, const double* u0,
+                                       double* um1) {
+    double w[5];
+    if (oracle_d2_weights(r, w)) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t i = 0; i < ny; ++i)
+            for (int64_t j = 0; j < nx; ++j) {
+                int64_t p = (k * ny + i) * nx + j;
+                um1[p] = u0[p] + (0.5 * c2) * lap3_64(u0, nz, ny, nx, r, w, k, i, j);
+            }
+    return 0;
+}
+
+/* Start, then `steps` steps: prev = u^{steps-1}, cur = u^{steps}. */
+ORACLE_API int oracle_wave3d_run_f64(int64_t nz, int64_t ny, int64_t nx, int r, double c2, int64_t steps,
+                                     const double* u0, double* prev, double* cur) {
+    int64_t n = nz * ny * nx;
+    if (oracle_wave3d_start_f64(nz, ny, nx, r, c2, u0, prev)) return -1;
+    memcpy(cur, u0, (size_t)n * sizeof(double));
+    for (int64_t s = 0; s < steps; ++s) {
+        if (oracle_wave3d_step_f64(nz, ny, nx, r, c2, prev, cur, prev)) return -1;
+        for (int64_t p = 0; p < n; ++p) {
+            double t = prev[p];
+            prev[p] = cur[p];
+            cur[p] = t;
+        }
+    }
+    return 0;
+}
+
+static inline float ghost3_m(int dtype, const void* u, int64_t nz, int64_t ny, int64_t nx, int64_t k, int64_t i,
+                             int64_t j) {
+    if (k < 0 || k >= nz || i < 0 || i >= ny || j < 0 || j >= nx) return 0.0f;
+    return load_storage(dtype, u, (k * ny + i) * nx + j);
+}
+
+static float lap3_m(int dtype, const void* u, int64_t nz, int64_t ny, int64_t nx, int r, const float* wf, float c0x3,
+                    int64_t k, int64_t i, int64_t j) {
+    float acc = c0x3 * load_storage(dtype, u, (k * ny + i) * nx + j);
+    for (int m = 1; m <= r; ++m) {
+        float vert = ghost3_m(dtype, u, nz, ny, nx, k, i - m, j) + ghost3_m(dtype, u, nz, ny, nx, k, i + m, j);
+        float horz = ghost3_m(dtype, u, nz, ny, nx, k, i, j - m) + ghost3_m(dtype, u, nz, ny, nx, k, i, j + m);
+        float depth = ghost3_m(dtype, u, nz, ny, nx, k - m, i, j) + ghost3_m(dtype, u, nz, ny, nx, k + m, i, j);
+        float plane = vert + horz;
+        float pair = plane + depth;
+        float term = wf[m] * pair;
+        acc = acc + term;
+    }
+    return acc;
+}
+
+static int mirror_weights3(int r, float* wf, float* c0x3) {
+    double w[5];
+    if (oracle_d2_weights(r, w)) return -1;
+    for (int m = 1; m <= r; ++m) wf[m] = (float)w[m];
+    *c0x3 = (float)(3.0 * w[0]);
+    return 0;
+}
+
+ORACLE_API int oracle_wave3d_step_mirror(int dtype, int64_t nz, int64_t ny, int64_t nx, int r, float c2,
+                                         const void* u_prev, const void* u_cur, void* u_next) {
+    float wf[5], c0x3;
+    if (mirror_weights3(r, wf, &c0x3)) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t i = 0; i < ny; ++i)
+            for (int64_t j = 0; j < nx; ++j) {
+                int64_t p = (k * ny + i) * nx + j;
+                float u = load_storage(dtype, u_cur, p);
+                float up = load_storage(dtype, u_prev, p);
+                float lap = lap3_m(dtype, u_cur, nz, ny, nx, r, wf, c0x3, k, i, j);
+                float two_u = 2.0f * u;
+                float inertia = two_u - up;
+                float force = c2 * lap;
+                store_storage(dtype, u_next, p, inertia + force);
+            }
+    return 0;
+}
+
+ORACLE_API int oracle_wave3d_start_mirror(int dtype, int64_t nz, int64_t ny, int64_t nx, int r, float c2,
+                                          const void* u0, void* um1) {
+    float wf[5], c0x3;
+    if (mirror_weights3(r, wf, &c0x3)) return -1;
+    float half_c2 = 0.5f * c2;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t i = 0; i < ny; ++i)
+            for (int64_t j = 0; j < nx; ++j) {
+                int64_t p = (k * ny + i) * nx + j;
+                float u = load_storage(dtype, u0, p);
+                float lap = lap3_m(dtype, u0, nz, ny, nx, r, wf, c0x3, k, i, j);
+                float force = half_c2 * lap;
+                store_storage(dtype, um1, p, u + force);
+            }
+    return 0;
+}
+
+ORACLE_API int oracle_wave3d_run_mirror(int dtype, int64_t nz, int64_t ny, int64_t nx, int r, float c2,
+                                        int64_t steps, const void* u0, void* prev, void* cur) {
+    size_t esz = dtype == ORACLE_F32 ? 4 : 2;
+    size_t bytes = (size_t)(nz * ny * nx) * esz;
+    if (oracle_wave3d_start_mirror(dtype, nz, ny, nx, r, c2, u0, prev)) return -1;
+    memcpy(cur, u0, bytes);
+    void* tmp = malloc(bytes ? bytes : 1);
+    if (!tmp) return -2;
+    for (int64_t s = 0; s < steps; ++s) {
+        if (oracle_wave3d_step_mirror(dtype, nz, ny, nx, r, c2, prev, cur, prev)) {
+            free(tmp);
+            return -1;
+        }
+        memcpy(tmp, prev, bytes);
+        memcpy(prev, cur, bytes);
+        memcpy(cur, tmp, bytes);
+    }
+    free(tmp);
+    return 0;
+}
+
+/* Discrete energy of section 6 with the 3D operator. */
+ORACLE_API double oracle_wave3d_energy_f64(int64_t nz, int64_t ny, int64_t nx, int r, double c2, const double* u_new,
+                                           const double* u_old, double* kin_out, double* pot_out) {
+    double w[5];
+    if (oracle_d2_weights(r, w)) return NAN;
+    double kin = 0.0, pot = 0.0;
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t i = 0; i < ny; ++i)
+            for (int64_t j = 0; j < nx; ++j) {
+                int64_t p = (k * ny + i) * nx + j;
+                double d = u_new[p] - u_old[p];
+                kin += d * d;
+                pot += u_new[p] * lap3_64(u_old, nz, ny, nx, r, w, k, i, j);
+            }
+    if (kin_out) *kin_out = kin;
+    if (pot_out) *pot_out = pot;
+    return kin - c2 * pot;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 9. Range mappers on boxes (paper §3: a range mapper ties the chunk of the  */
+/*    execution range a device runs to the part of a buffer it accesses)      */
+/* ------------------------------------------------------------------------- */
+/* A box is [lo_d, hi_d) in each of 3 dimensions, dimension 0 the slowest.  The
+ * paper names one_to_one; neighbourhood, slice, all and fixed are this build's
+ * other mappers:
+ *   one_to_one        chunk -> chunk
+ *   neighbourhood(r)  chunk grown by r_d on both sides of dimension d
+ *   slice(d)          chunk with dimension d widened to the whole buffer
+ *   all               the whole buffer
+ *   fixed(B)          the box B
+ * every result clipped to the buffer [0, extent_d).  An empty box has lo >= hi
+ * in some dimension. */
+enum { ORACLE_RM_ONE_TO_ONE = 0, ORACLE_RM_NEIGHBOURHOOD = 1, ORACLE_RM_SLICE = 2, ORACLE_RM_ALL = 3,
+       ORACLE_RM_FIXED = 4 };
+
+/* box: lo[3], hi[3] as 6 int64 (lo0, lo1, lo2, hi0, hi1, hi2). */
+ORACLE_API int oracle_rm_box(int kind, const int64_t* radius, int dim, const int64_t* fixed, const int64_t* chunk,
+                             const int64_t* extent, int64_t* out) {
+    for (int d = 0; d < 3; ++d) {
+        int64_t lo = chunk[d], hi = chunk[3 + d];
+        switch (kind) {
+            case ORACLE_RM_ONE_TO_ONE: break;
+            case ORACLE_RM_NEIGHBOURHOOD:
+                lo -= radius[d];
+                hi += radius[d];
+                break;
+            case ORACLE_RM_SLICE:
+                if (d == dim) {
+                    lo = 0;
+                    hi = extent[d];
+                }
+                break;
+            case ORACLE_RM_ALL:
+                lo = 0;
+                hi = extent[d];
+                break;
+            case ORACLE_RM_FIXED:
+                lo = fixed[d];
+                hi = fixed[3 + d];
+                break;
+            default: return -1;
+        }
+        out[d] = lo < 0 ? 0 : lo;
+        out[3 + d] = hi > extent[d] ? extent[d] : hi;
+    }
+    return 0;
+}
+
+/* Transfers a chunk list needs before a kernel with this mapper runs, when
+ * chunk c owns (holds the current values of) exactly its own box: for every
+ * ordered pair (src, dst), src != dst, the box rm(chunk_dst) intersected with
+ * chunk_src, if non-empty.  Written in dst-major, src-minor order as
+ * (src, dst, box[6]) records of 8 int64; returns how many, or -1 if more than
+ * max_out. */
+ORACLE_API int oracle_rm_box_transfers(int kind, const int64_t* radius, int dim, const int64_t* fixed,
+                                       const int64_t* chunks, int n, const int64_t* extent, int64_t* out,
+                                       int max_out) {
+    int count = 0;
+    for (int dst = 0; dst < n; ++dst) {
+        int64_t need[6];
+        if (oracle_rm_box(kind, radius, dim, fixed, chunks + 6 * dst, extent, need)) return -1;
+        for (int src = 0; src < n; ++src) {
+            if (src == dst) continue;
+            const int64_t* own = chunks + 6 * src;
+            int64_t box[6];
+            int empty = 0;
+            for (int d = 0; d < 3; ++d) {
+                box[d] = need[d] > own[d] ? need[d] : own[d];
+                box[3 + d] = need[3 + d] < own[3 + d] ? need[3 + d] : own[3 + d];
+                if (box[d] >= box[3 + d]) empty = 1;
+            }
+            if (empty) continue;
+            if (count >= max_out) return -1;
+            int64_t* rec = out + 8 * count;
+            rec[0] = src;
+            rec[1] = dst;
+            for (int q = 0; q < 6; ++q) rec[2 + q] = box[q];
+            ++count;
+        }
+    }
+    return count;
 }

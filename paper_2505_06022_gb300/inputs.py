@@ -72,6 +72,24 @@ def random_field(state: int, ny: int, nx: int) -> np.ndarray:
     return uniform_pm1_f32(state, ny * nx).reshape(ny, nx)
 
 
+def gaussian_pulse_3d(nz: int, ny: int, nx: int, sigma: float, amplitude: float = 1.0) -> np.ndarray:
+    """u0[k, i, j] = A * g(k - nz//2) * g(i - ny//2) * g(j - nx//2), g as in gaussian_pulse, FP64."""
+    g = [np.exp(-((np.arange(n, dtype=np.float64) - n // 2) ** 2) / (2.0 * sigma * sigma)) for n in (nz, ny, nx)]
+    return amplitude * g[0][:, None, None] * g[1][None, :, None] * g[2][None, None, :]
+
+
+def sine_mode_3d(nz: int, ny: int, nx: int, mz: int, my: int, mx: int) -> np.ndarray:
+    """u0[k, i, j] = sin(pi*mz*(k+1)/(nz+1)) sin(pi*my*(i+1)/(ny+1)) sin(pi*mx*(j+1)/(nx+1)), FP64."""
+    s = [np.sin(math.pi * m * np.arange(1, n + 1, dtype=np.float64) / (n + 1)) for n, m in ((nz, mz), (ny, my),
+                                                                                           (nx, mx))]
+    return s[0][:, None, None] * s[1][None, :, None] * s[2][None, None, :]
+
+
+def random_field_3d(state: int, nz: int, ny: int, nx: int) -> np.ndarray:
+    """Uniform [-1, 1) FP32 field (exact values) of shape (nz, ny, nx)."""
+    return uniform_pm1_f32(state, nz * ny * nx).reshape(nz, ny, nx)
+
+
 def to_storage(a64: np.ndarray, dtype: str) -> np.ndarray:
     """Round an FP64 field to its storage format: FP32 (float32 array), or BF16 /
     FP16 bit patterns (uint16 array).  16-bit values are rounded from the FP32

@@ -31,6 +31,13 @@ MUTATIONS = {
     "f16_ties_away": ("double n = nearbyint(a / quantum);", "double n = floor(a / quantum + 0.5);"),
     "energy_sign": ("return kin - c2 * pot;", "return kin + c2 * pot;"),
     "mlp_grad_drop_silu": ("dz1[i] = s * silu_grad(z1[i]);", "dz1[i] = s;"),
+    "wave3d_drop_depth": ("acc = acc + w[m] * ((vert + horz) + depth);", "acc = acc + w[m] * (vert + horz);"),
+    "wave3d_centre_2w0": ("double acc = (3.0 * w[0]) * u[(k * ny + i) * nx + j];",
+                          "double acc = (2.0 * w[0]) * u[(k * ny + i) * nx + j];"),
+    "wave3d_depth_shift": ("ghost3(u, nz, ny, nx, k + m, i, j);", "ghost3(u, nz, ny, nx, k + m, i + 1, j);"),
+    "mirror3d_drop_depth": ("float pair = plane + depth;", "float pair = plane;"),
+    "rm_box_one_sided": ("                hi += radius[d];", "                hi += 0 * radius[d];"),
+    "rm_transfers_no_clip": ("box[d] = need[d] > own[d] ? need[d] : own[d];", "box[d] = need[d];"),
 }
 
 
@@ -68,6 +75,10 @@ def pins_hold(L):
     L.oracle_f32_to_f16.restype = C.c_uint16
     L.oracle_mlp_loss_grad.argtypes = [i64, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.oracle_mlp_loss_grad.restype = dbl
+    L.oracle_wave3d_run_f64.argtypes = [i64, i64, i64, C.c_int, dbl, i64, vp, vp, vp]
+    L.oracle_wave3d_run_mirror.argtypes = [C.c_int, i64, i64, i64, C.c_int, flt, i64, vp, vp, vp]
+    L.oracle_rm_box.argtypes = [C.c_int, vp, C.c_int, vp, vp, vp, vp]
+    L.oracle_rm_box_transfers.argtypes = [C.c_int, vp, C.c_int, vp, vp, C.c_int, vp, vp, C.c_int]
 
     # SAXPY: two single roundings
     x, y = inputs.saxpy_inputs(257, seed=0)
@@ -122,6 +133,63 @@ def pins_hold(L):
         want_b = int(torch.tensor([float(v)], dtype=torch.float32).to(torch.bfloat16).view(torch.int16).item()) & 0xFFFF
         if L.oracle_f32_to_bf16(float(v)) != want_b:
             return False
+    # 3D: closed-form separable mode (r = 1) and the dense Kronecker operator (r = 2)
+    shape = (7, 8, 9)
+    u3 = inputs.sine_mode_3d(*shape, 2, 3, 4)
+    p3, c3 = np.empty_like(u3), np.empty_like(u3)
+    L.oracle_wave3d_run_f64(*shape, 1, 0.125, 12, _p(u3), _p(p3), _p(c3))
+    s2 = sum(math.sin(math.pi * m / (n + 1) / 2) ** 2 for n, m in zip(shape, (2, 3, 4)))
+    if np.max(np.abs(c3 - math.cos(12 * math.acos(1 - 0.25 * s2)) * u3)) > 1e-12:
+        return False
+    from test_oracle_pins_3d import kron3
+
+    shape = (4, 5, 3)
+    r3 = inputs.random_field_3d(5, *shape).astype(np.float64)
+    K = kron3(*shape, 2)
+    a, b = r3.reshape(-1) + 0.0625 * (K @ r3.reshape(-1)), r3.reshape(-1).copy()
+    for _ in range(6):
+        a, b = b, 2 * b - a + 0.125 * (K @ b)
+    p3, c3 = np.empty_like(r3), np.empty_like(r3)
+    L.oracle_wave3d_run_f64(*shape, 2, 0.125, 6, _p(r3), _p(p3), _p(c3))
+    if np.max(np.abs(c3.reshape(-1) - b)) > 1e-12 * max(1.0, np.max(np.abs(b))):
+        return False
+    # 3D mirror: exact on dyadic integers
+    iz = ((inputs.splitmix64(91, 5 * 6 * 7) % np.uint64(129)).astype(np.int64) - 64).astype(np.float64)
+    iz = iz.reshape(5, 6, 7)
+    p64, c64 = np.empty_like(iz), np.empty_like(iz)
+    L.oracle_wave3d_run_f64(5, 6, 7, 1, 0.125, 3, _p(iz), _p(p64), _p(c64))
+    i32 = iz.astype(np.float32)
+    p32, c32 = np.empty_like(i32), np.empty_like(i32)
+    L.oracle_wave3d_run_mirror(0, 5, 6, 7, 1, 0.125, 3, _p(i32), _p(p32), _p(c32))
+    if not np.array_equal(c32.astype(np.float64), c64):
+        return False
+    # box range mappers and transfers against enumerated cells
+    from test_oracle_pins_3d import brute_required, cells
+
+    ext = np.array([6, 5, 7], np.int64)
+    rad = np.array([1, 2, 1], np.int64)
+    fx = np.zeros(6, np.int64)
+    chunk = np.array([2, 1, 3, 4, 3, 5], np.int64)
+    out = np.zeros(6, np.int64)
+    L.oracle_rm_box(1, _p(rad), 0, _p(fx), _p(chunk), _p(ext), _p(out))
+    box = ((int(out[0]), int(out[1]), int(out[2])), (int(out[3]), int(out[4]), int(out[5])))
+    if cells(box) != brute_required(1, ((2, 1, 3), (4, 3, 5)), (6, 5, 7), (1, 2, 1), 0, None):
+        return False
+    chunks = [((0, 0, 0), (3, 5, 7)), ((3, 0, 0), (6, 5, 7))]
+    flat = np.array([v for c in chunks for part in c for v in part], np.int64)
+    recs = np.zeros(8 * 4, np.int64)
+    n = L.oracle_rm_box_transfers(1, _p(rad), 0, _p(fx), _p(flat), 2, _p(ext), _p(recs), 4)
+    got = set()
+    for t in range(max(n, 0)):
+        src, dst, b6 = int(recs[8 * t]), int(recs[8 * t + 1]), recs[8 * t + 2: 8 * t + 8]
+        bx = ((int(b6[0]), int(b6[1]), int(b6[2])), (int(b6[3]), int(b6[4]), int(b6[5])))
+        if not cells(bx) <= cells(chunks[src]):
+            return False
+        got |= {(dst, p) for p in cells(bx)}
+    want = {(d, p) for d, ch in enumerate(chunks)
+            for p in brute_required(1, ch, (6, 5, 7), (1, 2, 1), 0, None) - cells(ch)}
+    if got != want:
+        return False
     # MLP gradient against central differences (first-layer weights, where the mutation bites)
     F, H, O, B = 3, 4, 2, 5
     P = H * F + H + H * H + H + O * H + O
