@@ -425,6 +425,39 @@ def measure_temporal(q, stream, T: int, dtype: str = "f32") -> dict:
             "equivalent_single_step_gb_per_s": 3 * esize * upd / (ms * 1e-3) / 1e9}
 
 
+def measure_wave3d(q, stream, dtype: str = "f32", radius: int = 1) -> dict:
+    """Second workload: the leapfrog step on a 512^3 grid (c2 = 1/8, Gaussian sigma = 16 at the
+    centre), 100 steps in 4 chunks of planes with halo r, one sy_wave3d_run replay per
+    simulation from the resident initial field; 3 x sizeof(storage) bytes per update."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import inputs
+
+    n, steps = 512, 100
+    host = inputs.to_storage(inputs.gaussian_pulse_3d(n, n, n, 16.0), dtype)
+    u0 = torch.from_numpy(host if dtype == "f32" else host.view(np.int16)).cuda().reshape(-1)
+    a, b = torch.empty_like(u0), torch.empty_like(u0)
+    p = sy.stencil3d_params(n, n, n, radius, 0.125, dtype)
+    chunks = sy.sy_split_rows(n, 4)
+    run = lambda: sy.sy_wave3d_run(q.handle, p, u0, a, b, steps, chunks, radius)
+    run()
+    l0 = q.launches
+    run()
+    launches = q.launches - l0
+    reps, ms, joules = _metered(q, stream, run)
+    esize = 4 if dtype == "f32" else 2
+    upd = steps * n ** 3
+    gbs = 3 * esize * upd / (ms * 1e-3) / 1e9
+    peak = measured_peaks()["hbm_gbs"]
+    rows, threads = sy.sy_stencil3d_variant_info(radius, dtype, 0)
+    return {"grid": [n, n, n], "dtype": dtype, "radius": radius, "steps": steps, "chunks": 4,
+            "tile": {"rows": rows, "threads": threads}, "updates_per_s": upd / (ms * 1e-3), "gb_per_s": gbs,
+            "frac_hbm_measured": gbs / peak, "ms_per_sim": ms, "launches_per_sim": launches,
+            "j_per_update": None if not joules else joules / (reps * upd)}
+
+
 def measure_learned(q, stream) -> dict:
     """The learned cost model, end to end on this GPU: the library tunes a reduced
     corpus exhaustively (220 shapes), trains its MLP on 80% of the shapes with its own
@@ -622,6 +655,9 @@ def run_gpu(args) -> None:
         for dt in ("bf16", "f16"):
             forms[dt] = measure_precision_form(q, stream, dt)
         forms["saxpy"] = measure_saxpy(q, stream)
+        forms["wave3d_f32_r1"] = measure_wave3d(q, stream, "f32", 1)
+        forms["wave3d_bf16_r1"] = measure_wave3d(q, stream, "bf16", 1)
+        forms["wave3d_f32_r2"] = measure_wave3d(q, stream, "f32", 2)
         forms["batched"] = measure_batched(q, stream)
         forms["temporal_T2"] = measure_temporal(q, stream, 2)
         forms["temporal_T4"] = measure_temporal(q, stream, 4)

@@ -535,6 +535,96 @@ typedef int (*sy_measure_fn)(void* ctx, uint32_t sm_mhz, double* seconds, double
 sy_status sy_clock_sweep(uint32_t nvml_index, const uint32_t* sm_mhz, int n, sy_measure_fn measure, void* ctx,
                          int target, sy_freq_point* points, int* best);
 
+/* ------------------------------------------------------------------------- */
+/* Range mappers on boxes (paper §3: a range mapper ties the chunk of the     */
+/* execution range a device runs to the part of a buffer it accesses, and the */
+/* runtime infers the data transfers from it; the paper names one_to_one, the */
+/* other kinds are this library's).                                           */
+/* ------------------------------------------------------------------------- */
+/* A box is [lo[d], hi[d]) in each of 3 dimensions, dimension 0 the slowest (a
+ * 1D or 2D range uses extent 1 in the dimensions it lacks).  Empty when
+ * lo[d] >= hi[d] in some dimension. */
+typedef struct sy_box {
+    int64_t lo[3];
+    int64_t hi[3];
+} sy_box;
+
+typedef enum sy_rm_kind {
+    SY_RM_ONE_TO_ONE = 0,    /* the chunk itself */
+    SY_RM_NEIGHBOURHOOD = 1, /* the chunk grown by radius[d] on both sides of dimension d */
+    SY_RM_SLICE = 2,         /* the chunk with dimension `dim` widened to the whole buffer */
+    SY_RM_ALL = 3,           /* the whole buffer */
+    SY_RM_FIXED = 4          /* the box `fixed` */
+} sy_rm_kind;
+
+typedef struct sy_range_mapper {
+    int32_t kind;      /* sy_rm_kind */
+    int32_t dim;       /* SY_RM_SLICE: 0..2 */
+    int64_t radius[3]; /* SY_RM_NEIGHBOURHOOD: >= 0 */
+    sy_box fixed;      /* SY_RM_FIXED */
+} sy_range_mapper;
+
+/* The part of a buffer of `extent` (3 sizes >= 0) that a kernel over `chunk`
+ * accesses under the mapper, clipped to [0, extent).  SY_ERR_INVALID_ARGUMENT
+ * for an unknown kind, a negative radius or extent, or dim outside 0..2. */
+sy_status sy_rm_box(const sy_range_mapper* rm, const sy_box* chunk, const int64_t* extent, sy_box* out);
+
+/* One transfer: `box` (inside chunk src's own box) must reach chunk dst. */
+typedef struct sy_box_transfer {
+    int32_t src, dst;
+    sy_box box;
+} sy_box_transfer;
+
+/* Transfers a kernel with this mapper needs when chunk c holds exactly the
+ * current values of its own box: for each dst, then each src != dst, the
+ * non-empty intersection of rm(chunk_dst) with chunk_src.  The n chunks must
+ * tile the buffer (non-empty, disjoint, covering [0, extent)), else
+ * SY_ERR_BAD_CHUNKS.  *n_out = how many exist; more than max_out gives
+ * SY_ERR_INVALID_ARGUMENT (out then holds the first max_out). */
+sy_status sy_rm_box_transfers(const sy_range_mapper* rm, const sy_box* chunks, int n, const int64_t* extent,
+                              sy_box_transfer* out, int max_out, int* n_out);
+
+/* ------------------------------------------------------------------------- */
+/* Leapfrog step on a 3D grid (a second workload), chunked along planes: a    */
+/* chunk is a range of planes [begin, end) and reads the planes the            */
+/* neighbourhood range mapper (radius along dimension 0) gives it.            */
+/*   L u = 3 w_0 u + sum_{m=1..r} w_m ( ((u[z][y-m][x] + u[z][y+m][x])         */
+/*                   + (u[z][y][x-m] + u[z][y][x+m])) + (u[z-m][y][x] + u[z+m][y][x]) ) */
+/*   u^{n+1} = (2 u^n - u^{n-1}) + c2 * L u^n;  start u^{-1} = u^0 + (c2/2) L u^0 */
+/* with the weights, ghosts, rounding and storage rules of sy_stencil_step.   */
+/* ------------------------------------------------------------------------- */
+typedef struct sy_stencil3d_params {
+    int64_t nz, ny, nx; /* grid: nz planes of ny rows of nx points */
+    int64_t pitch;      /* elements from one row to the next, >= nx */
+    int64_t plane;      /* elements from one plane to the next, >= ny * pitch */
+    int32_t radius;     /* 1..4 */
+    int32_t dtype;      /* storage, sy_dtype */
+    float c2;           /* (c dt / dx)^2; stable for c2 * 12 * sum_k |w_k| <= 4 */
+    int32_t variant;    /* 0 = default tile, 1..sy_stencil3d_variant_count */
+} sy_stencil3d_params;
+
+/* One step of every chunk (chunks = plane ranges tiling [0, nz) in order; one
+ * launch each).  Fields are device buffers of nz x plane elements (caller-owned);
+ * padding is read but never written.  u_next may be u_prev (in place), must not
+ * overlap u_cur.  The
+ * fast path needs 16-byte aligned pointers, row and plane strides; other
+ * element-aligned layouts take a one-point-per-thread kernel.  Events as in
+ * sy_stencil_step. */
+sy_status sy_stencil3d_step(sy_queue_t q, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
+                            void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                            sy_event* chunk_events);
+/* Taylor start: u_m1 = u0 + (c2/2) L u0. */
+sy_status sy_stencil3d_start(sy_queue_t q, const sy_stencil3d_params* p, const void* u0, void* u_m1,
+                             const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* chunk_events);
+/* Start + `steps` steps as one cached CUDA graph, as sy_wave_run. */
+sy_status sy_wave3d_run(sy_queue_t q, const sy_stencil3d_params* p, const void* u0, void* u_a, void* u_b,
+                        int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* events,
+                        const void** prev_out, const void** cur_out);
+/* Tile variants: rows of a warp tile (radius 1-2: 2, 4, 8; radius 3-4: 1, 2, 4)
+ * x threads per block (128, 256); variant 0 is the default. */
+sy_status sy_stencil3d_variant_count(int radius, int dtype, int* count);
+sy_status sy_stencil3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads);
+
 /* Allocation-free form of sy_wave_energy.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the
  * moment they need the energy -- code issuing work while a stream is being

@@ -68,6 +68,26 @@ class Transfer(C.Structure):
     _fields_ = [("src", C.c_int32), ("dst", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64)]
 
 
+class Stencil3dParams(C.Structure):
+    _fields_ = [("nz", C.c_int64), ("ny", C.c_int64), ("nx", C.c_int64), ("pitch", C.c_int64), ("plane", C.c_int64),
+                ("radius", C.c_int32), ("dtype", C.c_int32), ("c2", C.c_float), ("variant", C.c_int32)]
+
+
+class Box(C.Structure):
+    _fields_ = [("lo", C.c_int64 * 3), ("hi", C.c_int64 * 3)]
+
+
+class RangeMapper(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("radius", C.c_int64 * 3), ("fixed", Box)]
+
+
+class BoxTransfer(C.Structure):
+    _fields_ = [("src", C.c_int32), ("dst", C.c_int32), ("box", Box)]
+
+
+SY_RM_ONE_TO_ONE, SY_RM_NEIGHBOURHOOD, SY_RM_SLICE, SY_RM_ALL, SY_RM_FIXED = 0, 1, 2, 3, 4
+
+
 class FreqPoint(C.Structure):
     _fields_ = [("sm_mhz", C.c_uint32), ("seconds", C.c_double), ("joules", C.c_double)]
 
@@ -153,6 +173,13 @@ _SIGS = {
     "sy_stencil_batch_destroy": [_p],
     "sy_stencil_multistep": [_p, _p, C.c_int, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_wave_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
+    "sy_stencil3d_step": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
+    "sy_stencil3d_start": [_p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
+    "sy_wave3d_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
+    "sy_stencil3d_variant_count": [C.c_int, C.c_int, _p],
+    "sy_stencil3d_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p],
+    "sy_rm_box": [_p, _p, _p, _p],
+    "sy_rm_box_transfers": [_p, _p, C.c_int, _p, _p, C.c_int, _p],
     "sy_clock_choose": [C.c_int, _p, C.c_int, _p],
     "sy_clock_nvml_index": [C.c_int, _p],
     "sy_clock_supported": [C.c_uint32, _p, _p, C.c_int, _p],
@@ -736,3 +763,89 @@ def sy_clock_sweep(nvml_index: int, candidates, measure, target: int = SY_TARGET
     best = C.c_int(-1)
     _call("sy_clock_sweep", int(nvml_index), freqs, n, fn, None, int(target), pts, C.byref(best))
     return best.value, [(p.sm_mhz, p.seconds, p.joules) for p in pts[:n]]
+
+
+# ---- 3D leapfrog (chunks of planes) --------------------------------------------------
+
+def stencil3d_params(nz: int, ny: int, nx: int, radius: int, c2: float, dtype: str = "f32", pitch: int | None = None,
+                     plane: int | None = None, variant: int = 0) -> Stencil3dParams:
+    pitch = nx if pitch is None else pitch
+    plane = ny * pitch if plane is None else plane
+    return Stencil3dParams(nz, ny, nx, pitch, plane, radius, DTYPE_CODES[dtype], c2, variant)
+
+
+def sy_stencil3d_step(q: int, p: Stencil3dParams, u_prev, u_cur, u_next, chunks, halo_radius: int,
+                      want_events: bool = False) -> list[int]:
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))()
+    _call("sy_stencil3d_step", q, C.byref(p), _ptr(u_prev), _ptr(u_cur), _ptr(u_next), arr, k, halo_radius,
+          evs if want_events else None)
+    return list(evs[:k]) if want_events else []
+
+
+def sy_stencil3d_start(q: int, p: Stencil3dParams, u0, u_m1, chunks, halo_radius: int,
+                       want_events: bool = False) -> list[int]:
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))()
+    _call("sy_stencil3d_start", q, C.byref(p), _ptr(u0), _ptr(u_m1), arr, k, halo_radius,
+          evs if want_events else None)
+    return list(evs[:k]) if want_events else []
+
+
+def sy_wave3d_run(q: int, p: Stencil3dParams, u0, u_a, u_b, steps: int, chunks, halo_radius: int,
+                  want_events: bool = False):
+    """Start + `steps` steps as one cached graph: (prev_ptr, cur_ptr, events), as sy_wave_run."""
+    arr, k = _chunks(chunks)
+    n_ev = (steps + 1) * k
+    evs = (C.c_uint64 * max(1, n_ev))() if want_events else None
+    pv, cv = C.c_void_p(), C.c_void_p()
+    _call("sy_wave3d_run", q, C.byref(p), _ptr(u0), _ptr(u_a), _ptr(u_b), steps, arr, k, halo_radius, evs,
+          C.byref(pv), C.byref(cv))
+    return pv.value, cv.value, (list(evs[:n_ev]) if want_events else [])
+
+
+def sy_stencil3d_variant_count(radius: int, dtype: str = "f32") -> int:
+    n = C.c_int(0)
+    _call("sy_stencil3d_variant_count", radius, DTYPE_CODES[dtype], C.byref(n))
+    return n.value
+
+
+def sy_stencil3d_variant_info(radius: int, dtype: str, variant: int) -> tuple[int, int]:
+    rows, thr = C.c_int(0), C.c_int(0)
+    _call("sy_stencil3d_variant_info", radius, DTYPE_CODES[dtype], variant, C.byref(rows), C.byref(thr))
+    return rows.value, thr.value
+
+
+# ---- range mappers on boxes ---------------------------------------------------------
+
+def _mk_box(b) -> Box:
+    (l0, l1, l2), (h0, h1, h2) = b
+    return Box((C.c_int64 * 3)(l0, l1, l2), (C.c_int64 * 3)(h0, h1, h2))
+
+
+def _unbox(b: Box) -> tuple:
+    return (tuple(b.lo), tuple(b.hi))
+
+
+def range_mapper(kind: int, radius=(0, 0, 0), dim: int = 0, fixed=((0, 0, 0), (0, 0, 0))) -> RangeMapper:
+    return RangeMapper(kind, dim, (C.c_int64 * 3)(*radius), _mk_box(fixed))
+
+
+def sy_rm_box(rm: RangeMapper, chunk, extent) -> tuple:
+    out = Box()
+    _call("sy_rm_box", C.byref(rm), C.byref(_mk_box(chunk)), (C.c_int64 * 3)(*extent), C.byref(out))
+    return _unbox(out)
+
+
+def sy_rm_box_transfers(rm: RangeMapper, chunks, extent) -> list:
+    """[(src, dst, box)] in dst-major, src-minor order."""
+    arr = (Box * max(1, len(chunks)))(*[_mk_box(c) for c in chunks])
+    n = C.c_int(0)
+    ext = (C.c_int64 * 3)(*extent)
+    L = lib()
+    rc = L.sy_rm_box_transfers(C.byref(rm), arr, len(chunks), ext, None, 0, C.byref(n))
+    if rc not in (0, 1) or (rc == 1 and n.value == 0):
+        raise SyError(rc, L.sy_last_error().decode(errors="replace"))
+    out = (BoxTransfer * max(1, n.value))()
+    _call("sy_rm_box_transfers", C.byref(rm), arr, len(chunks), ext, out, n.value, C.byref(n))
+    return [(t.src, t.dst, _unbox(t.box)) for t in out[: n.value]]

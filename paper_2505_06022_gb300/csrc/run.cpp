@@ -1,102 +1,31 @@
-// sy_wave_run: a whole leapfrog simulation (Taylor start + n chunked steps)
-// captured once into a CUDA graph and replayed.  The chunked launches are the
-// same ones sy_stencil_start / sy_stencil_step issue; capturing them removes the
-// host's per-launch cost and the gaps between stream launches, and the
-// per-chunk timestamps keep working inside the graph (their slots are zeroed
-// by the graph's first node on every replay).
+// sy_wave_run / sy_wave3d_run: a whole leapfrog simulation (Taylor start + n
+// chunked steps) captured once into a CUDA graph and replayed.  The chunked
+// launches are the same ones sy_stencil_start / sy_stencil_step (and their 3D
+// forms) issue; capturing them removes the host's per-launch cost and the gaps
+// between stream launches, and the per-chunk timestamps keep working inside the
+// graph (their slots are zeroed by the graph's first node on every replay).
 #include <cstring>
 
 #include "sy_internal.h"
 
 namespace sy {
-namespace {
 
-bool same_params(const sy_stencil_params& a, const sy_stencil_params& b) {
-    return a.ny == b.ny && a.nx == b.nx && a.pitch == b.pitch && a.radius == b.radius && a.dtype == b.dtype &&
-           a.c2 == b.c2 && a.variant == b.variant;
-}
-
-bool cache_hit(const RunGraph& g, const sy_stencil_params* p, const void* u0, void* ua, void* ub, int64_t steps,
-               const sy_chunk* chunks, int n_chunks, int halo, bool events) {
-    if (!g.valid || !same_params(g.p, *p) || g.u0 != u0 || g.ua != ua || g.ub != ub || g.steps != steps ||
-        g.halo != halo || g.events != events || static_cast<int>(g.chunks.size()) != n_chunks)
-        return false;
-    for (int c = 0; c < n_chunks; ++c)
-        if (g.chunks[c].begin != chunks[c].begin || g.chunks[c].end != chunks[c].end) return false;
-    return true;
-}
-
-// Issue the launches of a run on q->launch.  Fills prev/cur with the buffers
-// holding u^{steps-1} and u^{steps}.
-sy_status issue_run(Queue* q, const sy_stencil_params* p, const void* u0, void* ua, void* ub, int64_t steps,
-                    const sy_chunk* chunks, int n_chunks, int halo, bool events, const void** prev,
-                    const void** cur) {
-    std::vector<sy_event> ev(events ? n_chunks : 0);
-    sy_event* evp = events ? ev.data() : nullptr;
-    // start: u_a = u^{-1}
-    SY_TRY(stencil_common(q, p, nullptr, u0, ua, chunks, n_chunks, halo, evp, true));
-    const void* pv = ua;  // u^{-1}
-    const void* cv = u0;  // u^0
-    if (steps >= 1) {     // u^1 over u^{-1} in u_a (in place)
-        SY_TRY(stencil_common(q, p, ua, u0, ua, chunks, n_chunks, halo, evp, false));
-        pv = u0;
-        cv = ua;
-    }
-    if (steps >= 2) {  // u^2 into u_b, so that u0 is never written
-        SY_TRY(stencil_common(q, p, u0, ua, ub, chunks, n_chunks, halo, evp, false));
-        pv = ua;
-        cv = ub;
-    }
-    for (int64_t s = 2; s < steps; ++s) {  // then in place, alternating u_a / u_b
-        void* nv = const_cast<void*>(pv);
-        SY_TRY(stencil_common(q, p, pv, cv, nv, chunks, n_chunks, halo, evp, false));
-        pv = cv;
-        cv = nv;
-    }
-    *prev = pv;
-    *cur = cv;
-    return SY_OK;
-}
-
-}  // namespace
-}  // namespace sy
-
-using namespace sy;
-
-extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, const void* u0, void* u_a, void* u_b,
-                                 int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius,
-                                 sy_event* events, const void** prev_out, const void** cur_out) {
-    Queue* q;
-    SY_TRY(check_queue(qh, &q));
-    SY_TRY(stencil_param_checks(p));
-    if (steps < 0) return fail(SY_ERR_INVALID_ARGUMENT, "steps = %lld < 0", (long long)steps);
-    if (!u0 || !u_a || !u_b) return fail(SY_ERR_NULL_POINTER, "field pointer is NULL");
-    const size_t bytes = static_cast<size_t>(p->ny) * static_cast<size_t>(p->pitch) * dtype_size(p->dtype);
-    if (ranges_overlap(u0, bytes, u_a, bytes) || ranges_overlap(u0, bytes, u_b, bytes) ||
-        ranges_overlap(u_a, bytes, u_b, bytes))
-        return fail(SY_ERR_ALIAS, "u0, u_a and u_b must not overlap");
-    if (p->ny == 0 || p->nx == 0) return fail(SY_ERR_INVALID_ARGUMENT, "empty grid");
-    SY_TRY(validate_chunks(p->ny, chunks, n_chunks));
-    if (halo_radius < p->radius)
-        return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
-    const bool want = events != nullptr;
-    const uint64_t timed = static_cast<uint64_t>(steps + 1) * static_cast<uint64_t>(n_chunks);
+sy_status graph_run(Queue* q, RunGraph& g, const std::vector<unsigned char>& key, uint64_t timed, bool want,
+                    sy_status (*issue)(Queue*, const void*, const void**, const void**), const void* ctx,
+                    sy_event* events, const void** prev_out, const void** cur_out) {
     if (want && timed > kGraphStampSlots)
         return fail(SY_ERR_INVALID_ARGUMENT, "%llu timed launches exceed %u per run (pass events = NULL)",
                     (unsigned long long)timed, kGraphStampSlots);
     SY_TRY(use_device(q));
-
-    RunGraph& g = q->run;
-    if (!cache_hit(g, p, u0, u_a, u_b, steps, chunks, n_chunks, halo_radius, want)) {
+    if (!g.valid || g.key != key) {
         if (g.exec) {
             SY_CUDA(cudaStreamSynchronize(q->stream));
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
         }
         g.valid = false;
-        // The capture stream must not start before earlier work on the queue: the
-        // graph is launched on q->stream, so capture-time ordering is not needed,
-        // but the capture itself issues nothing until launch.
+        // Captured on the queue's private stream; the graph is launched on q->stream,
+        // which orders it after earlier work on the queue.
         q->capturing = true;
         q->next_graph_slot = 0;
         q->capture_expected.clear();
@@ -106,12 +35,12 @@ extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, cons
         sy_status st = SY_OK;
         if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCapture");
         if (st == SY_OK && want) {
-            e = cudaMemsetAsync(q->d_stamps + 4ull * kStreamStampSlots, 0,
-                                4ull * timed * sizeof(unsigned long long), q->aux);
+            e = cudaMemsetAsync(q->d_stamps + 4ull * kStreamStampSlots, 0, 4ull * timed * sizeof(unsigned long long),
+                                q->aux);
             if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync(stamps)");
         }
         const void *pv = nullptr, *cv = nullptr;
-        if (st == SY_OK) st = issue_run(q, p, u0, u_a, u_b, steps, chunks, n_chunks, halo_radius, want, &pv, &cv);
+        if (st == SY_OK) st = issue(q, ctx, &pv, &cv);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(q->aux, &graph);
         if (st == SY_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
@@ -130,14 +59,7 @@ extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, cons
             return st;
         }
         g.valid = true;
-        g.p = *p;
-        g.u0 = u0;
-        g.ua = u_a;
-        g.ub = u_b;
-        g.steps = steps;
-        g.halo = halo_radius;
-        g.events = want;
-        g.chunks.assign(chunks, chunks + n_chunks);
+        g.key = key;
         g.expected = q->capture_expected;
         g.launches = per_replay;
         g.prev_out = pv;
@@ -162,4 +84,130 @@ extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, cons
     if (prev_out) *prev_out = g.prev_out;
     if (cur_out) *cur_out = g.cur_out;
     return SY_OK;
+}
+
+namespace {
+
+template <class T>
+void append(std::vector<unsigned char>& key, const T& v) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+    key.insert(key.end(), b, b + sizeof(T));
+}
+
+// The arguments of one run, shared by the 2D and 3D forms.
+template <class P>
+struct RunArgs {
+    const P* p;
+    const void* u0;
+    void* ua;
+    void* ub;
+    int64_t steps;
+    const sy_chunk* chunks;
+    int n_chunks;
+    int halo;
+    bool events;
+};
+
+template <class P>
+std::vector<unsigned char> run_key(const RunArgs<P>& a) {
+    std::vector<unsigned char> key;
+    append(key, *a.p);
+    append(key, a.u0);
+    append(key, a.ua);
+    append(key, a.ub);
+    append(key, a.steps);
+    append(key, a.halo);
+    append(key, a.events);
+    for (int c = 0; c < a.n_chunks; ++c) append(key, a.chunks[c]);
+    return key;
+}
+
+sy_status step2(Queue* q, const sy_stencil_params* p, const void* up, const void* uc, void* un, const sy_chunk* ch,
+                int n, int halo, sy_event* ev, bool start) {
+    return stencil_common(q, p, up, uc, un, ch, n, halo, ev, start);
+}
+sy_status step3(Queue* q, const sy_stencil3d_params* p, const void* up, const void* uc, void* un, const sy_chunk* ch,
+                int n, int halo, sy_event* ev, bool start) {
+    return stencil3d_common(q, p, up, uc, un, ch, n, halo, ev, start);
+}
+
+// Start into u_a, step 1 in place over it, step 2 into u_b (u0 is never written),
+// then in place, alternating u_a / u_b.
+template <class P, sy_status (*STEP)(Queue*, const P*, const void*, const void*, void*, const sy_chunk*, int, int,
+                                     sy_event*, bool)>
+sy_status issue_run(Queue* q, const void* ctx, const void** prev, const void** cur) {
+    const RunArgs<P>& a = *static_cast<const RunArgs<P>*>(ctx);
+    std::vector<sy_event> ev(a.events ? a.n_chunks : 0);
+    sy_event* evp = a.events ? ev.data() : nullptr;
+    SY_TRY(STEP(q, a.p, nullptr, a.u0, a.ua, a.chunks, a.n_chunks, a.halo, evp, true));
+    const void* pv = a.ua;  // u^{-1}
+    const void* cv = a.u0;  // u^0
+    if (a.steps >= 1) {
+        SY_TRY(STEP(q, a.p, a.ua, a.u0, a.ua, a.chunks, a.n_chunks, a.halo, evp, false));
+        pv = a.u0;
+        cv = a.ua;
+    }
+    if (a.steps >= 2) {
+        SY_TRY(STEP(q, a.p, a.u0, a.ua, a.ub, a.chunks, a.n_chunks, a.halo, evp, false));
+        pv = a.ua;
+        cv = a.ub;
+    }
+    for (int64_t s = 2; s < a.steps; ++s) {
+        void* nv = const_cast<void*>(pv);
+        SY_TRY(STEP(q, a.p, pv, cv, nv, a.chunks, a.n_chunks, a.halo, evp, false));
+        pv = cv;
+        cv = nv;
+    }
+    *prev = pv;
+    *cur = cv;
+    return SY_OK;
+}
+
+sy_status run_checks(int64_t steps, const void* u0, const void* ua, const void* ub, size_t bytes, bool empty) {
+    if (steps < 0) return fail(SY_ERR_INVALID_ARGUMENT, "steps = %lld < 0", (long long)steps);
+    if (!u0 || !ua || !ub) return fail(SY_ERR_NULL_POINTER, "field pointer is NULL");
+    if (ranges_overlap(u0, bytes, ua, bytes) || ranges_overlap(u0, bytes, ub, bytes) ||
+        ranges_overlap(ua, bytes, ub, bytes))
+        return fail(SY_ERR_ALIAS, "u0, u_a and u_b must not overlap");
+    if (empty) return fail(SY_ERR_INVALID_ARGUMENT, "empty grid");
+    return SY_OK;
+}
+
+}  // namespace
+}  // namespace sy
+
+using namespace sy;
+
+extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, const void* u0, void* u_a, void* u_b,
+                                 int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                                 sy_event* events, const void** prev_out, const void** cur_out) {
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil_param_checks(p));
+    const size_t bytes = static_cast<size_t>(p->ny) * static_cast<size_t>(p->pitch) * dtype_size(p->dtype);
+    SY_TRY(run_checks(steps, u0, u_a, u_b, bytes, p->ny == 0 || p->nx == 0));
+    SY_TRY(validate_chunks(p->ny, chunks, n_chunks));
+    if (halo_radius < p->radius)
+        return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
+    RunArgs<sy_stencil_params> a{p, u0, u_a, u_b, steps, chunks, n_chunks, halo_radius, events != nullptr};
+    const uint64_t timed = static_cast<uint64_t>(steps + 1) * static_cast<uint64_t>(n_chunks);
+    return graph_run(q, q->run, run_key(a), timed, events != nullptr, issue_run<sy_stencil_params, step2>, &a,
+                     events, prev_out, cur_out);
+}
+
+extern "C" sy_status sy_wave3d_run(sy_queue_t qh, const sy_stencil3d_params* p, const void* u0, void* u_a,
+                                   void* u_b, int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                                   sy_event* events, const void** prev_out, const void** cur_out) {
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil3d_param_checks(p));
+    const size_t bytes = static_cast<size_t>(p->nz) * static_cast<size_t>(p->plane) * dtype_size(p->dtype);
+    SY_TRY(run_checks(steps, u0, u_a, u_b, bytes, p->nz == 0 || p->ny == 0 || p->nx == 0));
+    SY_TRY(validate_chunks(p->nz, chunks, n_chunks));
+    if (halo_radius < p->radius)
+        return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
+    RunArgs<sy_stencil3d_params> a{p, u0, u_a, u_b, steps, chunks, n_chunks, halo_radius, events != nullptr};
+    const uint64_t timed = static_cast<uint64_t>(steps + 1) * static_cast<uint64_t>(n_chunks);
+    return graph_run(q, q->run3, run_key(a), timed, events != nullptr, issue_run<sy_stencil3d_params, step3>, &a,
+                     events, prev_out, cur_out);
 }

@@ -64,16 +64,11 @@ struct Window {
 };
 
 // One cached whole-run CUDA graph (sy_wave_run).
+// A cached whole-simulation graph (sy_wave_run, sy_wave3d_run): valid for the
+// exact call it was captured for, identified by the bytes of its arguments.
 struct RunGraph {
     bool valid = false;
-    sy_stencil_params p{};
-    const void* u0 = nullptr;
-    void* ua = nullptr;
-    void* ub = nullptr;
-    int64_t steps = 0;
-    int halo = 0;
-    bool events = false;
-    std::vector<sy_chunk> chunks;
+    std::vector<unsigned char> key;
     cudaGraphExec_t exec = nullptr;
     std::vector<uint64_t> expected;  // per graph stamp slot
     uint64_t launches = 0;           // kernel launches per replay
@@ -116,7 +111,8 @@ struct Queue {
     // scratch owned by the queue (allocated on first use)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    RunGraph run;
+    RunGraph run;    // sy_wave_run
+    RunGraph run3;   // sy_wave3d_run
 };
 
 Queue* as_queue(sy_queue_t q);
@@ -159,6 +155,41 @@ struct WaveLaunch {
     int64_t row_begin, row_end;
 };
 sy_status launch_wave(Queue* q, const WaveLaunch& w);
+namespace wave {
+// Resident blocks per SM of a kernel at `threads` threads (cached per kernel).
+int kernel_occupancy(const void* fn, int threads);
+// Programmatic dependent launch between chunk kernels (SY_PDL=0 turns it off).
+bool launch_overlap_enabled();
+}  // namespace wave
+
+// One chunk of planes of the 3D step (wave3d_*.cu).
+struct WaveLaunch3 {
+    int64_t nz, ny, nx, pitch, plane;  // elements
+    int radius;
+    int dtype;
+    int variant;
+    float c2;
+    bool start;
+    int pdl;
+    const void* u_prev;
+    const void* u_cur;
+    void* u_next;
+    int64_t z_begin, z_end;
+};
+sy_status launch_wave3d(Queue* q, const WaveLaunch3& w);
+bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads);
+constexpr int kWave3dVariants = 6;
+sy_status stencil3d_param_checks(const sy_stencil3d_params* p);
+sy_status stencil3d_common(Queue* q, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
+                           void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                           sy_event* chunk_events, bool start);
+
+// Replays (capturing on first use) the graph of a whole run.  `key` identifies
+// the call; `issue` enqueues its launches on q->launch and reports the buffers
+// holding u^{steps-1} and u^{steps}; `timed` = stamped launches per replay.
+sy_status graph_run(Queue* q, RunGraph& g, const std::vector<unsigned char>& key, uint64_t timed, bool want,
+                    sy_status (*issue)(Queue*, const void*, const void**, const void**), const void* ctx,
+                    sy_event* events, const void** prev_out, const void** cur_out);
 // Argument checks and one launch per chunk, shared by sy_stencil_step/start/run.
 sy_status stencil_common(Queue* q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
                          void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,

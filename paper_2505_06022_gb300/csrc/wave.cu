@@ -20,7 +20,7 @@ namespace {
 std::mutex g_occ_mu;
 std::unordered_map<uint64_t, int> g_occ;
 
-int occupancy(KernelFn fn, int threads) {
+int occupancy(const void* fn, int threads) {
     const uint64_t key = reinterpret_cast<uint64_t>(fn) ^ (static_cast<uint64_t>(threads) << 56);
     {
         std::lock_guard<std::mutex> lock(g_occ_mu);
@@ -46,6 +46,9 @@ bool pdl_enabled() {
     return on;
 }
 }  // namespace
+
+int kernel_occupancy(const void* fn, int threads) { return occupancy(fn, threads); }
+bool launch_overlap_enabled() { return pdl_enabled(); }
 
 sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn scalar_fn, int tile_rows,
                        int threads, int V, size_t esize) {
@@ -73,7 +76,7 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
         a.tiles = a.tiles_x * ((rows + tile_rows - 1) / tile_rows);
         const int64_t wpb = threads / 32;
         int64_t blocks = (a.tiles + wpb - 1) / wpb;
-        const int64_t cap = static_cast<int64_t>(occupancy(vec_fn, threads)) * q->sm_count;
+        const int64_t cap = static_cast<int64_t>(occupancy(reinterpret_cast<const void*>(vec_fn), threads)) * q->sm_count;
         if (blocks > cap) blocks = cap;  // persistent: every block resident at once
         if (w.pdl && pdl_enabled()) {
             a.pdl = w.pdl;

@@ -1,0 +1,13 @@
+// 3D wave-step kernel instantiations for bf16 storage (all radii, tile heights,
+// step and start forms).  The kernels themselves are in wave3d_kernel.cuh.
+#include "wave3d_kernel.cuh"
+
+namespace sy {
+namespace wave3 {
+
+sy_status launch3_bf16(Queue* q, const WaveLaunch3& w, int rows, int threads) {
+    return launch3_dtype<__nv_bfloat16>(q, w, rows, threads);
+}
+
+}  // namespace wave3
+}  // namespace sy

@@ -1,0 +1,309 @@
+// Leapfrog wave step on a 3D grid (radius-r star stencil, Dirichlet-zero ghosts)
+// for one chunk of planes of a field laid out plane by plane, row by row.
+// Included by wave3d_f32.cu, wave3d_bf16.cu and wave3d_f16.cu.
+//
+//   L u = 3 w_0 u + sum_{m=1..r} w_m ( ((u_{z,y-m,x} + u_{z,y+m,x}) + (u_{z,y,x-m} + u_{z,y,x+m}))
+//                                      + (u_{z-m,y,x} + u_{z+m,y,x}) )
+//   u^{n+1} = (2 u^n - u^{n-1}) + c2 * L u^n          (start: u^{-1} = u^0 + (c2/2) L u^0)
+//
+// Every operation is an explicit round-to-nearest FP32 intrinsic in exactly this
+// order; 16-bit storage is widened exactly and the result rounded once.
+//
+// Vector kernel (16-byte aligned rows), HBM-bound at 3 x sizeof(S) bytes per point:
+//   * A warp owns a column of tiles: 32*V columns x RY rows, marched through a
+//     segment of consecutive planes.  It keeps the tile's rows of the 2r+1 planes
+//     z-r .. z+r in registers (a queue shifted by one plane per step), so each
+//     plane of u^n is read once per segment; per plane it loads one new plane of
+//     the tile, the r rows above and below the tile (L2 hits: the neighbouring
+//     tiles read them too), the tile of u^{n-1} and, in lanes 0 and 31, the r
+//     columns beyond the warp's span.
+//   * Horizontal neighbours come from the adjacent lanes by warp shuffles.
+//   * Tasks (tile column x plane segment) are numbered x fastest, then y, then
+//     segment; persistent warps stride over them, so the warps in flight work on
+//     neighbouring tiles of the same few segments and the halo rows they share
+//     are still in L2.  The host sizes the segments so that every warp gets the
+//     same number of tasks.
+// Scalar kernel: rows that are not 16-byte aligned; one point per thread.
+#pragma once
+
+#include "wave_kernel.cuh"
+
+namespace sy {
+namespace wave3 {
+
+using wave::kFull;
+using wave::Traits;
+using wave::wk;
+
+// 3 w_0 rounded once to FP32: r = 1: -6, r = 2: -15/2, r = 3: -49/6, r = 4: -205/24.
+template <int R>
+__device__ __forceinline__ float c0x3();
+template <>
+__device__ __forceinline__ float c0x3<1>() { return -6.0f; }
+template <>
+__device__ __forceinline__ float c0x3<2>() { return -7.5f; }
+template <>
+__device__ __forceinline__ float c0x3<3>() { return static_cast<float>(-49.0 / 6.0); }
+template <>
+__device__ __forceinline__ float c0x3<4>() { return static_cast<float>(-205.0 / 24.0); }
+
+struct Args3 {
+    const char* u_prev;  // unused by the start kernel
+    const char* u_cur;
+    char* u_next;
+    int64_t nz, ny, nx, pitch_bytes, plane_bytes;
+    int64_t z_begin, z_end;    // the chunk's planes
+    int64_t tiles_x, tiles_y;  // warp tiles per plane
+    int64_t seg, segs;         // planes per segment, segments in the chunk
+    int64_t tasks;             // tiles_x * tiles_y * segs
+    float c2;                  // coefficient of L u
+    unsigned long long* stamp;
+    int pdl;  // as in the 2D kernel: 0 none, 1 wait for the predecessor first, 2 independent chunk
+};
+
+template <int R, bool START>
+__device__ __forceinline__ float update3(float u, float up, const float (&vert)[R], const float (&horz)[R],
+                                         const float (&depth)[R], float c2) {
+    float acc = __fmul_rn(c0x3<R>(), u);
+#pragma unroll
+    for (int d = 1; d <= R; ++d)
+        acc = __fadd_rn(acc, __fmul_rn(wk<R>(d), __fadd_rn(__fadd_rn(vert[d - 1], horz[d - 1]), depth[d - 1])));
+    if (START) return __fadd_rn(u, __fmul_rn(c2, acc));
+    return __fadd_rn(__fsub_rn(__fmul_rn(2.0f, u), up), __fmul_rn(c2, acc));
+}
+
+// One warp's task: tile (tx, ty) through the planes of segment sg.  CHECK = false
+// is the interior form: every row the tile reads lies in [0, ny) and every lane's
+// V columns in [0, nx) (planes are always checked against [0, nz)).
+template <typename S, int R, int RY, bool START, bool CHECK>
+__device__ __forceinline__ void column_impl(const Args3& a, int64_t tx, int64_t ty, int64_t sg, int lane) {
+    using T = Traits<S>;
+    constexpr int V = T::V;
+    constexpr int64_t ES = sizeof(S);
+    static_assert(R <= V, "radius must not exceed the vector width");
+    const int64_t pb = a.pitch_bytes, zb = a.plane_bytes;
+    const int64_t x0 = (tx * 32 + lane) * V;
+    const int64_t y0 = ty * RY;
+    const int64_t za = a.z_begin + sg * a.seg;
+    const int64_t ze = za + a.seg < a.z_end ? za + a.seg : a.z_end;
+    const bool col_in = !CHECK || x0 < a.nx;
+    const int nvalid = !CHECK ? V : (col_in ? static_cast<int>(a.nx - x0 < V ? a.nx - x0 : V) : 0);
+    const bool masked = CHECK && nvalid < V;
+    const char* cur_col = a.u_cur + x0 * ES;  // plane 0, row 0, this lane's columns
+    auto row_in = [&](int64_t y) { return !CHECK || (y >= 0 && y < a.ny); };
+    auto load_cur = [&](int64_t z, int64_t y) -> uint4 {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (z >= 0 && z < a.nz && col_in && row_in(y)) {
+            v = __ldg(reinterpret_cast<const uint4*>(cur_col + z * zb + y * pb));
+            if (masked) T::mask(v, nvalid);
+        }
+        return v;
+    };
+
+    // q[m][k]: row y0 + k of plane z - R + m
+    uint4 q[2 * R + 1][RY];
+#pragma unroll
+    for (int m = 1; m <= 2 * R; ++m)
+#pragma unroll
+        for (int k = 0; k < RY; ++k) q[m][k] = load_cur(za - R + (m - 1), y0 + k);
+
+    // lanes 0 and 31 read the R columns beyond the warp's span, one element each
+    const bool edge_lane = lane == 0 || lane == 31;
+    const int64_t edge_col0 = lane == 0 ? x0 - 1 : x0 + V;  // column at distance 1; d steps outwards
+    const int64_t edge_step = lane == 0 ? -1 : 1;
+
+    for (int64_t z = za; z < ze; ++z) {
+#pragma unroll
+        for (int m = 0; m < 2 * R; ++m)
+#pragma unroll
+            for (int k = 0; k < RY; ++k) q[m][k] = q[m + 1][k];
+#pragma unroll
+        for (int k = 0; k < RY; ++k) q[2 * R][k] = load_cur(z + R, y0 + k);
+        // yh[d-1]: row y0 - d;  yh[R + d - 1]: row y0 + RY - 1 + d   (plane z)
+        uint4 yh[2 * R];
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+            yh[d - 1] = load_cur(z, y0 - d);
+            yh[R + d - 1] = load_cur(z, y0 + RY - 1 + d);
+        }
+        uint4 prev[START ? 1 : RY];
+        if (!START) {
+            const char* pbase = a.u_prev + z * zb + y0 * pb + x0 * ES;
+#pragma unroll
+            for (int k = 0; k < RY; ++k) {
+                prev[k] = make_uint4(0u, 0u, 0u, 0u);
+                if (col_in && row_in(y0 + k)) prev[k] = __ldcs(reinterpret_cast<const uint4*>(pbase + k * pb));
+            }
+        }
+        float edge[RY][R];  // edge[k][d-1]: column x0 - d (lane 0) or x0 + V - 1 + d (lane 31)
+        const char* ebase = a.u_cur + z * zb + y0 * pb;
+#pragma unroll
+        for (int k = 0; k < RY; ++k)
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                const int64_t col = edge_col0 + (d - 1) * edge_step;
+                edge[k][d - 1] = 0.0f;
+                if (edge_lane && row_in(y0 + k) && col >= 0 && col < a.nx)
+                    edge[k][d - 1] = T::load1(ebase + k * pb + col * ES);
+            }
+
+        char* nbase = a.u_next + z * zb + y0 * pb + x0 * ES;
+#pragma unroll
+        for (int k = 0; k < RY; ++k) {
+            float ext[V + 2 * R];  // ext[m] holds column x0 - R + m of row y0 + k
+#pragma unroll
+            for (int e = 0; e < V; ++e) ext[R + e] = T::elem(q[R][k], e);
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                float from_left = __shfl_up_sync(kFull, ext[R + V - d], 1);
+                float from_right = __shfl_down_sync(kFull, ext[R + d - 1], 1);
+                ext[R - d] = lane == 0 ? edge[k][d - 1] : from_left;
+                ext[R + V - 1 + d] = lane == 31 ? edge[k][d - 1] : from_right;
+            }
+            float out[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                float vert[R], horz[R], depth[R];
+#pragma unroll
+                for (int d = 1; d <= R; ++d) {
+                    const int up_row = k - d, dn_row = k + d;
+                    const float n = up_row >= 0 ? T::elem(q[R][up_row >= 0 ? up_row : 0], e)
+                                                : T::elem(yh[(-up_row - 1) < R ? (-up_row - 1) : 0], e);
+                    const float s = dn_row < RY ? T::elem(q[R][dn_row < RY ? dn_row : 0], e)
+                                                : T::elem(yh[R + (dn_row - RY < R ? dn_row - RY : 0)], e);
+                    vert[d - 1] = __fadd_rn(n, s);
+                    horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                    depth[d - 1] = __fadd_rn(T::elem(q[R - d][k], e), T::elem(q[R + d][k], e));
+                }
+                const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
+                out[e] = update3<R, START>(ext[R + e], up, vert, horz, depth, a.c2);
+            }
+            if (col_in && row_in(y0 + k)) {
+                char* dst = nbase + k * pb;
+                if (!CHECK || nvalid == V) {
+                    __stcs(reinterpret_cast<uint4*>(dst), T::pack(out));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (e < nvalid) T::store1(dst + e * ES, out[e]);
+                }
+            }
+        }
+    }
+}
+
+template <typename S, int R, int RY, bool START>
+__device__ __forceinline__ void column(const Args3& a, int64_t tx, int64_t ty, int64_t sg, int lane) {
+    constexpr int V = Traits<S>::V;
+    const int64_t y0 = ty * RY;
+    const bool interior = (y0 - R >= 0) && (y0 + RY + R <= a.ny) && ((tx + 1) * 32 * V <= a.nx);
+    if (interior) column_impl<S, R, RY, START, false>(a, tx, ty, sg, lane);
+    else column_impl<S, R, RY, START, true>(a, tx, ty, sg, lane);
+}
+
+// Register cap per tile height (blocks of 256 threads that must fit an SM): the
+// kernel is latency-bound when few warps are resident, and its loads of a plane are
+// consumed in the same step, so resident warps are what keeps HBM busy.
+// Chosen so that no instantiation spills: radius 1 fits 64 / 85 / 128 registers
+// for 1 / 2 / 4 rows, radius 2 one step less; radius 3-4 are left uncapped.
+template <int R, int RY>
+struct MinBlocks3 {
+    static constexpr int value = R == 1 ? (RY == 1 ? 4 : RY == 2 ? 3 : 2) : R == 2 ? (RY == 1 ? 3 : RY == 2 ? 2 : 1) : 1;
+};
+
+template <typename S, int R, int RY, bool START>
+__global__ void __launch_bounds__(256, MinBlocks3<R, RY>::value) wave3d_vec_kernel(Args3 a) {
+    if (a.pdl == 1) griddep_wait();
+    if (a.pdl) griddep_launch_dependents();
+    stamp_begin(a.stamp);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_per_block = blockDim.x >> 5;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * warps_per_block;
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); t < a.tasks;
+         t += nwarps) {
+        const int64_t rest = t / a.tiles_x;
+        const int64_t tx = t - rest * a.tiles_x;
+        const int64_t sg = rest / a.tiles_y;
+        const int64_t ty = rest - sg * a.tiles_y;
+        column<S, R, RY, START>(a, tx, ty, sg, lane);
+    }
+    stamp_end(a.stamp);
+    if (a.pdl && threadIdx.x == 0) griddep_wait();
+}
+
+// One point per thread; any element-aligned layout.
+template <typename S, int R, bool START>
+__global__ void __launch_bounds__(256) wave3d_scalar_kernel(Args3 a) {
+    using T = Traits<S>;
+    stamp_begin(a.stamp);
+    const int64_t planes = a.z_end - a.z_begin;
+    const int64_t per_plane = a.ny * a.nx;
+    const int64_t total = planes * per_plane;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < total; p += stride) {
+        const int64_t z = a.z_begin + p / per_plane;
+        const int64_t r = p - (z - a.z_begin) * per_plane;
+        const int64_t y = r / a.nx;
+        const int64_t x = r - y * a.nx;
+        auto at = [&](int64_t zz, int64_t yy, int64_t xx) -> float {
+            if (zz < 0 || zz >= a.nz || yy < 0 || yy >= a.ny || xx < 0 || xx >= a.nx) return 0.0f;
+            return T::load1(a.u_cur + zz * a.plane_bytes + yy * a.pitch_bytes + xx * static_cast<int64_t>(sizeof(S)));
+        };
+        float vert[R], horz[R], depth[R];
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+            vert[d - 1] = __fadd_rn(at(z, y - d, x), at(z, y + d, x));
+            horz[d - 1] = __fadd_rn(at(z, y, x - d), at(z, y, x + d));
+            depth[d - 1] = __fadd_rn(at(z - d, y, x), at(z + d, y, x));
+        }
+        const int64_t off = z * a.plane_bytes + y * a.pitch_bytes + x * static_cast<int64_t>(sizeof(S));
+        const float up = START ? 0.0f : T::load1_cs(a.u_prev + off);
+        T::store1(a.u_next + off, update3<R, START>(at(z, y, x), up, vert, horz, depth, a.c2));
+    }
+    stamp_end(a.stamp);
+}
+
+using KernelFn3 = void (*)(Args3);
+
+// Tile heights: radius 1-2 {1, 2, 4}, radius 3-4 {1, 2, 4} (the register queue
+// holds (2r+1) x RY vectors); variant v (1-based) = (rows[(v-1) % 3], threads[(v-1) / 3]).
+constexpr int kRows12[3] = {1, 2, 4};
+constexpr int kRows34[3] = {1, 2, 4};
+constexpr int kThreads3[2] = {128, 256};
+constexpr int kVariants3 = 6;
+
+template <typename S, int R, bool START>
+KernelFn3 pick_vec3(int rows) {
+    switch (rows) {
+        case 1: return wave3d_vec_kernel<S, R, 1, START>;
+        case 2: return wave3d_vec_kernel<S, R, 2, START>;
+        default: return wave3d_vec_kernel<S, R, 4, START>;
+    }
+}
+
+sy_status launch3_typed(Queue* q, const WaveLaunch3& w, KernelFn3 vec_fn, KernelFn3 scalar_fn, int rows, int threads,
+                        int V, size_t esize);
+
+template <typename S, int R>
+sy_status launch3_r(Queue* q, const WaveLaunch3& w, int rows, int threads) {
+    KernelFn3 vec = w.start ? pick_vec3<S, R, true>(rows) : pick_vec3<S, R, false>(rows);
+    KernelFn3 sca = w.start ? wave3d_scalar_kernel<S, R, true> : wave3d_scalar_kernel<S, R, false>;
+    return launch3_typed(q, w, vec, sca, rows, threads, Traits<S>::V, sizeof(S));
+}
+
+template <typename S>
+sy_status launch3_dtype(Queue* q, const WaveLaunch3& w, int rows, int threads) {
+    switch (w.radius) {
+        case 1: return launch3_r<S, 1>(q, w, rows, threads);
+        case 2: return launch3_r<S, 2>(q, w, rows, threads);
+        case 3: return launch3_r<S, 3>(q, w, rows, threads);
+        default: return launch3_r<S, 4>(q, w, rows, threads);
+    }
+}
+
+sy_status launch3_f32(Queue* q, const WaveLaunch3& w, int rows, int threads);
+sy_status launch3_bf16(Queue* q, const WaveLaunch3& w, int rows, int threads);
+sy_status launch3_f16(Queue* q, const WaveLaunch3& w, int rows, int threads);
+
+}  // namespace wave3
+}  // namespace sy
