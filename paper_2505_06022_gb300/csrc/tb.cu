@@ -160,15 +160,34 @@ __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_b
             ext[R + V - 1 + d] = Tr::elem(rv, d - 1);
         }
         float out[V];
+        if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions (packed FP32 adds)
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            float vert[R], horz[R];
+            for (int e = 0; e < V; e += 2) {
+                float2 vert[R], horz[R];
 #pragma unroll
-            for (int d = 1; d <= R; ++d) {
-                vert[d - 1] = __fadd_rn(Tr::elem(win[R - d], e), Tr::elem(win[R + d], e));
-                horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                for (int d = 1; d <= R; ++d) {
+                    vert[d - 1] = wave::add2_rn(make_float2(Tr::elem(win[R - d], e), Tr::elem(win[R - d], e + 1)),
+                                                make_float2(Tr::elem(win[R + d], e), Tr::elem(win[R + d], e + 1)));
+                    horz[d - 1] = wave::add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]),
+                                                make_float2(ext[R + e + d], ext[R + e + 1 + d]));
+                }
+                const float2 o = wave::update2<R, false>(make_float2(ext[R + e], ext[R + e + 1]),
+                                                         make_float2(Tr::elem(pv, e), Tr::elem(pv, e + 1)), vert,
+                                                         horz, c2);
+                out[e] = o.x;
+                out[e + 1] = o.y;
             }
-            out[e] = wave::update<R, false>(ext[R + e], Tr::elem(pv, e), vert, horz, c2);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                float vert[R], horz[R];
+#pragma unroll
+                for (int d = 1; d <= R; ++d) {
+                    vert[d - 1] = __fadd_rn(Tr::elem(win[R - d], e), Tr::elem(win[R + d], e));
+                    horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                }
+                out[e] = wave::update<R, false>(ext[R + e], Tr::elem(pv, e), vert, horz, c2);
+            }
         }
         if (!interior) {  // ghosts outside the grid stay zero
             const int64_t gy = static_cast<int64_t>(y_buf0) + r;

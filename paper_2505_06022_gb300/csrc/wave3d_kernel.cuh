@@ -72,6 +72,22 @@ __device__ __forceinline__ float update3(float u, float up, const float (&vert)[
     return __fadd_rn(__fsub_rn(__fmul_rn(2.0f, u), up), __fmul_rn(c2, acc));
 }
 
+// update3 for two neighbouring points, additions paired (wave::add2_rn; the
+// multiplications stay scalar, see wave_kernel.cuh): bit-identical to update3.
+template <int R, bool START>
+__device__ __forceinline__ float2 update3_2(float2 u, float2 up, const float2 (&vert)[R], const float2 (&horz)[R],
+                                            const float2 (&depth)[R], float c2) {
+    using wave::add2_rn;
+    using wave::mul2_scalar;
+    float2 acc = mul2_scalar(c0x3<R>(), u);
+#pragma unroll
+    for (int d = 1; d <= R; ++d)
+        acc = add2_rn(acc, mul2_scalar(wk<R>(d), add2_rn(add2_rn(vert[d - 1], horz[d - 1]), depth[d - 1])));
+    if (START) return add2_rn(u, mul2_scalar(c2, acc));
+    const float2 inertia = add2_rn(mul2_scalar(2.0f, u), make_float2(-up.x, -up.y));
+    return add2_rn(inertia, mul2_scalar(c2, acc));
+}
+
 // One warp's task: tile (tx, ty) through the planes of segment sg.  CHECK = false
 // is the interior form: every row the tile reads lies in [0, ny) and every lane's
 // V columns in [0, nx) (planes are always checked against [0, nz)).
@@ -161,22 +177,53 @@ __device__ __forceinline__ void column_impl(const Args3& a, int64_t tx, int64_t 
                 ext[R + V - 1 + d] = lane == 31 ? edge[k][d - 1] : from_right;
             }
             float out[V];
+            if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-                float vert[R], horz[R], depth[R];
+                for (int e = 0; e < V; e += 2) {
+                    float2 vert[R], horz[R], depth[R];
 #pragma unroll
-                for (int d = 1; d <= R; ++d) {
-                    const int up_row = k - d, dn_row = k + d;
-                    const float n = up_row >= 0 ? T::elem(q[R][up_row >= 0 ? up_row : 0], e)
-                                                : T::elem(yh[(-up_row - 1) < R ? (-up_row - 1) : 0], e);
-                    const float s = dn_row < RY ? T::elem(q[R][dn_row < RY ? dn_row : 0], e)
-                                                : T::elem(yh[R + (dn_row - RY < R ? dn_row - RY : 0)], e);
-                    vert[d - 1] = __fadd_rn(n, s);
-                    horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
-                    depth[d - 1] = __fadd_rn(T::elem(q[R - d][k], e), T::elem(q[R + d][k], e));
+                    for (int d = 1; d <= R; ++d) {
+                        float n2[2], s2[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int up_row = k - d, dn_row = k + d;
+                            n2[h] = up_row >= 0 ? T::elem(q[R][up_row >= 0 ? up_row : 0], e + h)
+                                                : T::elem(yh[(-up_row - 1) < R ? (-up_row - 1) : 0], e + h);
+                            s2[h] = dn_row < RY ? T::elem(q[R][dn_row < RY ? dn_row : 0], e + h)
+                                                : T::elem(yh[R + (dn_row - RY < R ? dn_row - RY : 0)], e + h);
+                        }
+                        vert[d - 1] = wave::add2_rn(make_float2(n2[0], n2[1]), make_float2(s2[0], s2[1]));
+                        horz[d - 1] = wave::add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]),
+                                                    make_float2(ext[R + e + d], ext[R + e + 1 + d]));
+                        depth[d - 1] = wave::add2_rn(make_float2(T::elem(q[R - d][k], e), T::elem(q[R - d][k], e + 1)),
+                                                     make_float2(T::elem(q[R + d][k], e), T::elem(q[R + d][k], e + 1)));
+                    }
+                    const float2 up = START ? make_float2(0.0f, 0.0f)
+                                            : make_float2(T::elem(prev[START ? 0 : k], e),
+                                                          T::elem(prev[START ? 0 : k], e + 1));
+                    const float2 o = update3_2<R, START>(make_float2(ext[R + e], ext[R + e + 1]), up, vert, horz,
+                                                         depth, a.c2);
+                    out[e] = o.x;
+                    out[e + 1] = o.y;
                 }
-                const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
-                out[e] = update3<R, START>(ext[R + e], up, vert, horz, depth, a.c2);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    float vert[R], horz[R], depth[R];
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        const int up_row = k - d, dn_row = k + d;
+                        const float n = up_row >= 0 ? T::elem(q[R][up_row >= 0 ? up_row : 0], e)
+                                                    : T::elem(yh[(-up_row - 1) < R ? (-up_row - 1) : 0], e);
+                        const float s = dn_row < RY ? T::elem(q[R][dn_row < RY ? dn_row : 0], e)
+                                                    : T::elem(yh[R + (dn_row - RY < R ? dn_row - RY : 0)], e);
+                        vert[d - 1] = __fadd_rn(n, s);
+                        horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                        depth[d - 1] = __fadd_rn(T::elem(q[R - d][k], e), T::elem(q[R + d][k], e));
+                    }
+                    const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
+                    out[e] = update3<R, START>(ext[R + e], up, vert, horz, depth, a.c2);
+                }
             }
             if (col_in && row_in(y0 + k)) {
                 char* dst = nbase + k * pb;

@@ -207,6 +207,39 @@ __device__ __forceinline__ float update(float u, float up, const float (&vert)[R
     return __fadd_rn(__fsub_rn(__fmul_rn(2.0f, u), up), __fmul_rn(c2, acc));
 }
 
+// The same update for two neighbouring points at once.  The additions use
+// Blackwell's packed FP32 add (add.rn.f32x2, written as PTX: each half one IEEE
+// round-to-nearest addition, bit-identical to __fadd_rn); a - b is evaluated as
+// a + (-b), which IEEE 754 defines to be the same operation.  The multiplications
+// stay scalar __fmul_rn: a packed multiply feeding a packed add was measured to be
+// contracted into a fused multiply-add despite the explicit rounding mode, which
+// would change the results, while scalar multiplies are never contracted in the
+// translation units that use this (built with -fmad=false).
+__device__ __forceinline__ float2 add2_rn(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 mul2_scalar(float w, float2 x) {
+    return make_float2(__fmul_rn(w, x.x), __fmul_rn(w, x.y));
+}
+
+template <int R, bool START>
+__device__ __forceinline__ float2 update2(float2 u, float2 up, const float2 (&vert)[R], const float2 (&horz)[R],
+                                          float c2) {
+    float2 acc = mul2_scalar(c0x2<R>(), u);
+#pragma unroll
+    for (int d = 1; d <= R; ++d) acc = add2_rn(acc, mul2_scalar(wk<R>(d), add2_rn(vert[d - 1], horz[d - 1])));
+    if (START) return add2_rn(u, mul2_scalar(c2, acc));
+    const float2 inertia = add2_rn(mul2_scalar(2.0f, u), make_float2(-up.x, -up.y));
+    return add2_rn(inertia, mul2_scalar(c2, acc));
+}
+
 // One warp's tile: columns [(tx*32 + lane)*V, +V) of each lane, rows
 // [row_begin + ty*RY, +RY) of the chunk [row_begin, row_end), for a field laid
 // out as in `a`.  CHECK = false is the interior form, valid when every row the
@@ -285,16 +318,35 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
             ext[R + V - 1 + d] = lane == 31 ? T::elem(edge[k], d - 1) : from_right;
         }
         float out[V];
+        if constexpr (sizeof(S) == 2) {  // 16-bit storage: twice the arithmetic per byte; pair the additions
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            float vert[R], horz[R];
+            for (int e = 0; e < V; e += 2) {
+                float2 vert[R], horz[R];
 #pragma unroll
-            for (int d = 1; d <= R; ++d) {
-                vert[d - 1] = __fadd_rn(T::elem(cur[k + R - d], e), T::elem(cur[k + R + d], e));
-                horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                for (int d = 1; d <= R; ++d) {
+                    vert[d - 1] = add2_rn(make_float2(T::elem(cur[k + R - d], e), T::elem(cur[k + R - d], e + 1)),
+                                          make_float2(T::elem(cur[k + R + d], e), T::elem(cur[k + R + d], e + 1)));
+                    horz[d - 1] = add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]),
+                                          make_float2(ext[R + e + d], ext[R + e + 1 + d]));
+                }
+                const float2 up = START ? make_float2(0.0f, 0.0f)
+                                        : make_float2(T::elem(prev[START ? 0 : k], e), T::elem(prev[START ? 0 : k], e + 1));
+                const float2 o = update2<R, START>(make_float2(ext[R + e], ext[R + e + 1]), up, vert, horz, a.c2);
+                out[e] = o.x;
+                out[e + 1] = o.y;
             }
-            const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
-            out[e] = update<R, START>(ext[R + e], up, vert, horz, a.c2);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                float vert[R], horz[R];
+#pragma unroll
+                for (int d = 1; d <= R; ++d) {
+                    vert[d - 1] = __fadd_rn(T::elem(cur[k + R - d], e), T::elem(cur[k + R + d], e));
+                    horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                }
+                const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
+                out[e] = update<R, START>(ext[R + e], up, vert, horz, a.c2);
+            }
         }
         if (!CHECK || (col_in && y0 + k < a.row_end)) {
             char* dst = next_base + k * pb;
