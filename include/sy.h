@@ -620,7 +620,12 @@ sy_status sy_stencil3d_start(sy_queue_t q, const sy_stencil3d_params* p, const v
 sy_status sy_wave3d_run(sy_queue_t q, const sy_stencil3d_params* p, const void* u0, void* u_a, void* u_b,
                         int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* events,
                         const void** prev_out, const void** cur_out);
-/* Tile variants: rows of a warp tile (radius 1-2: 2, 4, 8; radius 3-4: 1, 2, 4)
+/* Discrete energy of the 3D scheme, E^{n+1/2} = sum (u_new - u_old)^2 - c2 *
+ * sum u_new * (L u_old), in FP64 with a fixed reduction shape (as sy_wave_energy,
+ * whose scratch buffer it shares). */
+sy_status sy_wave3d_energy(sy_queue_t q, const sy_stencil3d_params* p, const void* u_new, const void* u_old,
+                           double* energy, double* kinetic, double* potential);
+/* Tile variants: rows of a warp tile (radius 1-2: 1, 2, 4; radius 3-4: 1, 2, 4)
  * x threads per block (128, 256); variant 0 is the default. */
 sy_status sy_stencil3d_variant_count(int radius, int dtype, int* count);
 sy_status sy_stencil3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads);

@@ -177,6 +177,7 @@ _SIGS = {
     "sy_stencil3d_start": [_p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_wave3d_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
     "sy_stencil3d_variant_count": [C.c_int, C.c_int, _p],
+    "sy_wave3d_energy": [_p, _p, _p, _p, _p, _p, _p],
     "sy_stencil3d_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p],
     "sy_rm_box": [_p, _p, _p, _p],
     "sy_rm_box_transfers": [_p, _p, C.c_int, _p, _p, C.c_int, _p],
@@ -802,6 +803,13 @@ def sy_wave3d_run(q: int, p: Stencil3dParams, u0, u_a, u_b, steps: int, chunks, 
     _call("sy_wave3d_run", q, C.byref(p), _ptr(u0), _ptr(u_a), _ptr(u_b), steps, arr, k, halo_radius, evs,
           C.byref(pv), C.byref(cv))
     return pv.value, cv.value, (list(evs[:n_ev]) if want_events else [])
+
+
+def sy_wave3d_energy(q: int, p: Stencil3dParams, u_new, u_old) -> tuple[float, float, float]:
+    """(E, kinetic, potential) of the 3D scheme, FP64, fixed reduction shape."""
+    e, k, pt = C.c_double(), C.c_double(), C.c_double()
+    _call("sy_wave3d_energy", q, C.byref(p), _ptr(u_new), _ptr(u_old), C.byref(e), C.byref(k), C.byref(pt))
+    return e.value, k.value, pt.value
 
 
 def sy_stencil3d_variant_count(radius: int, dtype: str = "f32") -> int:

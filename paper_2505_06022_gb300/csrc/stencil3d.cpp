@@ -82,6 +82,35 @@ sy_status sy_stencil3d_start(sy_queue_t qh, const sy_stencil3d_params* p, const 
     return stencil3d_common(q, p, nullptr, u0, u_m1, chunks, n_chunks, halo_radius, chunk_events, true);
 }
 
+sy_status sy_wave3d_energy(sy_queue_t qh, const sy_stencil3d_params* p, const void* u_new, const void* u_old,
+                           double* energy, double* kinetic, double* potential) {
+    clear_error();
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil3d_param_checks(p));
+    if (!energy) return fail(SY_ERR_NULL_POINTER, "energy out is NULL");
+    if (p->nz == 0 || p->ny == 0 || p->nx == 0) {
+        *energy = 0.0;
+        if (kinetic) *kinetic = 0.0;
+        if (potential) *potential = 0.0;
+        return SY_OK;
+    }
+    if (!u_new || !u_old) return fail(SY_ERR_NULL_POINTER, "field pointer is NULL");
+    SY_TRY(use_device(q));
+    void* scratch = nullptr;
+    SY_TRY(queue_scratch(q, sizeof(double) * (2 * kEnergyBlocks + 3), &scratch));
+    double* partials = static_cast<double*>(scratch);
+    double* out3 = partials + 2 * kEnergyBlocks;
+    SY_TRY(launch_wave3d_energy(q, p, u_new, u_old, partials, out3));
+    double host[3];
+    SY_CUDA(cudaMemcpyAsync(host, out3, sizeof host, cudaMemcpyDeviceToHost, q->stream));
+    SY_CUDA(cudaStreamSynchronize(q->stream));
+    *energy = host[0];
+    if (kinetic) *kinetic = host[1];
+    if (potential) *potential = host[2];
+    return SY_OK;
+}
+
 sy_status sy_stencil3d_variant_count(int radius, int dtype, int* count) {
     clear_error();
     if (!count) return fail(SY_ERR_NULL_POINTER, "count is NULL");

@@ -216,5 +216,11 @@ sy_status launch_tb(Queue* q, const TBLaunch& w);
 sy_status launch_wave_energy(Queue* q, const sy_stencil_params* p, const void* u_new, const void* u_old,
                              double* partials, int n_partials, double* out3_device);
 constexpr int kEnergyBlocks = 1024;
+// Second stage of the fixed-shape FP64 energy reduction: sums 2 x kEnergyBlocks
+// partials (kinetic, potential) and writes (kin - c2 pot, kin, pot) to out3.
+sy_status launch_energy_final(cudaStream_t stream, const double* partials, double c2, double* out3);
+// The 3D energy: first stage (wave3d.cu) then launch_energy_final, on q->launch.
+sy_status launch_wave3d_energy(Queue* q, const sy_stencil3d_params* p, const void* u_new, const void* u_old,
+                               double* partials, double* out3_device);
 
 }  // namespace sy

@@ -275,6 +275,12 @@ sy_status launch_energy_on(cudaStream_t stream, const sy_stencil_params* p, cons
 
 }  // namespace
 
+sy_status launch_energy_final(cudaStream_t stream, const double* partials, double c2, double* out3) {
+    energy::energy_final_kernel<<<1, kEnergyBlocks, 0, stream>>>(partials, c2, out3);
+    SY_CUDA(cudaGetLastError());
+    return SY_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free energy reduction (sy_wave_energy_static)
 // ---------------------------------------------------------------------------

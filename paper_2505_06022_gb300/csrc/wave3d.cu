@@ -1,6 +1,9 @@
 // Launch logic of the 3D wave step: layout checks, the variant table, and the
 // choice of plane-segment length that gives every persistent warp the same
-// number of tasks.
+// number of tasks; and the FP64 discrete energy of the 3D scheme,
+//   E^{n+1/2} = sum (u_new - u_old)^2 - c2 * sum u_new * (L u_old),
+// with the fixed reduction shape of the 2D one (kEnergyBlocks x 256 threads, fixed
+// trees), so repeated calls give identical bits.
 #include "wave3d_kernel.cuh"
 
 namespace sy {
@@ -93,7 +96,111 @@ sy_status launch3_typed(Queue* q, const WaveLaunch3& w, KernelFn3 vec_fn, Kernel
     return SY_OK;
 }
 
+namespace energy3 {
+
+constexpr int kThreads = 256;
+
+// FP64 weights: 3 w_0 and w_k of the order-2r second difference (rationals rounded once).
+template <int R>
+__device__ __forceinline__ double c0x3_64() {
+    return R == 1 ? -6.0 : R == 2 ? -7.5 : R == 3 ? -49.0 / 6.0 : -205.0 / 24.0;
+}
+template <int R>
+__device__ __forceinline__ double wk64(int k) {
+    if (R == 1) return 1.0;
+    if (R == 2) return k == 1 ? 4.0 / 3.0 : -1.0 / 12.0;
+    if (R == 3) return k == 1 ? 1.5 : k == 2 ? -3.0 / 20.0 : 1.0 / 90.0;
+    return k == 1 ? 8.0 / 5.0 : k == 2 ? -1.0 / 5.0 : k == 3 ? 8.0 / 315.0 : -1.0 / 560.0;
+}
+
+struct EArgs3 {
+    const char* u_new;
+    const char* u_old;
+    int64_t nz, ny, nx, pitch_bytes, plane_bytes;
+};
+
+template <typename S, int R>
+__global__ void __launch_bounds__(kThreads) energy3_partials_kernel(EArgs3 a, double* partials) {
+    using T = Traits<S>;
+    auto at = [&](const char* base, int64_t z, int64_t y, int64_t x) -> double {
+        if (z < 0 || z >= a.nz || y < 0 || y >= a.ny || x < 0 || x >= a.nx) return 0.0;
+        return static_cast<double>(
+            T::load1(base + z * a.plane_bytes + y * a.pitch_bytes + x * static_cast<int64_t>(sizeof(S))));
+    };
+    double kin = 0.0, pot = 0.0;
+    const int64_t per_plane = a.ny * a.nx;
+    const int64_t total = a.nz * per_plane;
+    const int64_t stride = static_cast<int64_t>(kEnergyBlocks) * kThreads;
+    for (int64_t p = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; p < total; p += stride) {
+        const int64_t z = p / per_plane;
+        const int64_t rem = p - z * per_plane;
+        const int64_t y = rem / a.nx, x = rem - y * a.nx;
+        const double un = at(a.u_new, z, y, x), uo = at(a.u_old, z, y, x);
+        double lap = __dmul_rn(c0x3_64<R>(), uo);
+#pragma unroll
+        for (int k = 1; k <= R; ++k) {
+            const double vert = __dadd_rn(at(a.u_old, z, y - k, x), at(a.u_old, z, y + k, x));
+            const double horz = __dadd_rn(at(a.u_old, z, y, x - k), at(a.u_old, z, y, x + k));
+            const double depth = __dadd_rn(at(a.u_old, z - k, y, x), at(a.u_old, z + k, y, x));
+            lap = __dadd_rn(lap, __dmul_rn(wk64<R>(k), __dadd_rn(__dadd_rn(vert, horz), depth)));
+        }
+        const double d = __dsub_rn(un, uo);
+        kin = __dadd_rn(kin, __dmul_rn(d, d));
+        pot = __dadd_rn(pot, __dmul_rn(un, lap));
+    }
+    __shared__ double sk[kThreads], sp[kThreads];
+    sk[threadIdx.x] = kin;
+    sp[threadIdx.x] = pot;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sk[threadIdx.x] = __dadd_rn(sk[threadIdx.x], sk[threadIdx.x + s]);
+            sp[threadIdx.x] = __dadd_rn(sp[threadIdx.x], sp[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = sk[0];
+        partials[2 * blockIdx.x + 1] = sp[0];
+    }
+}
+
+template <typename S>
+void launch_partials(int radius, EArgs3 a, double* partials, cudaStream_t s) {
+    switch (radius) {
+        case 1: energy3_partials_kernel<S, 1><<<kEnergyBlocks, kThreads, 0, s>>>(a, partials); break;
+        case 2: energy3_partials_kernel<S, 2><<<kEnergyBlocks, kThreads, 0, s>>>(a, partials); break;
+        case 3: energy3_partials_kernel<S, 3><<<kEnergyBlocks, kThreads, 0, s>>>(a, partials); break;
+        default: energy3_partials_kernel<S, 4><<<kEnergyBlocks, kThreads, 0, s>>>(a, partials); break;
+    }
+}
+
+}  // namespace energy3
 }  // namespace wave3
+
+sy_status launch_wave3d_energy(Queue* q, const sy_stencil3d_params* p, const void* u_new, const void* u_old,
+                               double* partials, double* out3_device) {
+    const size_t esize = dtype_size(p->dtype);
+    if ((reinterpret_cast<uintptr_t>(u_new) % esize) || (reinterpret_cast<uintptr_t>(u_old) % esize))
+        return fail(SY_ERR_INVALID_ARGUMENT, "field pointers must be aligned to the element size");
+    wave3::energy3::EArgs3 a;
+    a.u_new = static_cast<const char*>(u_new);
+    a.u_old = static_cast<const char*>(u_old);
+    a.nz = p->nz;
+    a.ny = p->ny;
+    a.nx = p->nx;
+    a.pitch_bytes = p->pitch * static_cast<int64_t>(esize);
+    a.plane_bytes = p->plane * static_cast<int64_t>(esize);
+    switch (p->dtype) {
+        case SY_F32: wave3::energy3::launch_partials<float>(p->radius, a, partials, q->launch); break;
+        case SY_BF16: wave3::energy3::launch_partials<__nv_bfloat16>(p->radius, a, partials, q->launch); break;
+        default: wave3::energy3::launch_partials<__half>(p->radius, a, partials, q->launch); break;
+    }
+    SY_CUDA(cudaGetLastError());
+    SY_TRY(launch_energy_final(q->launch, partials, static_cast<double>(p->c2), out3_device));
+    q->launches += 2;
+    return SY_OK;
+}
 
 bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads) {
     if (radius < 1 || radius > 4 || dtype_size(dtype) == 0 || variant < 0 || variant > wave3::kVariants3)

@@ -210,3 +210,39 @@ def test_3d_256_sampled_light_cone(q, dtype):
         _, sub = oracle.wave3d_run_mirror(DT[dtype], sub0, steps, r, C2)
         assert bits(np.asarray(cur[pt]).reshape(1))[0] == bits(sub[pt[0] - lo[0], pt[1] - lo[1], pt[2] - lo[2]]
                                                                .reshape(1))[0], pt
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_3d_energy_matches_oracle(q, dtype, r):
+    torch = torch_cuda()
+    shape = (11, 23, 140)
+    u_new, u_old = field(shape, dtype, seed=21), field(shape, dtype, seed=22)
+    up = lambda u: torch.from_numpy(u if dtype == "f32" else u.view(np.int16)).cuda().reshape(-1)
+    p = sy.stencil3d_params(*shape, r, C2, dtype)
+    E, kin, pot = sy.sy_wave3d_energy(q, p, up(u_new), up(u_old))
+    code = DT[dtype]
+    un, uo = oracle.storage_to_f64(u_new, code), oracle.storage_to_f64(u_old, code)
+    want = oracle.wave3d_energy_f64(un, uo, r, C2)
+    lap = oracle.wave3d_step_f64(2 * uo, uo, r, 1.0)  # (2u - 2u) + L u = L u exactly
+    abs_sum = ((un - uo) ** 2).sum() + C2 * np.abs(un * lap).sum()
+    # same FP64 terms summed in another order: |difference| <= 2 N eps sum|terms|
+    tol = 2 * np.prod(shape) * 2.0 ** -53 * abs_sum
+    assert abs(E - want["E"]) <= tol and abs(kin - want["kin"]) <= tol and abs(pot - want["pot"]) <= tol / C2
+    assert sy.sy_wave3d_energy(q, p, up(u_new), up(u_old)) == (E, kin, pot)  # fixed reduction shape
+
+
+def test_3d_energy_conserved_full_size(q):
+    """512^3 FP32 r = 1, 100 steps through the graph: the FP64 discrete energy of the FP32 fields
+    drifts only by rounding."""
+    torch = torch_cuda()
+    n, steps = 512, 100
+    u0 = torch.from_numpy(inputs.to_storage(inputs.gaussian_pulse_3d(n, n, n, 16.0), "f32")).cuda().reshape(-1)
+    a, b = torch.empty_like(u0), torch.empty_like(u0)
+    p = sy.stencil3d_params(n, n, n, 1, C2, "f32")
+    chunks = sy.sy_split_rows(n, 4)
+    pv, cv, _ = sy.sy_wave3d_run(q, p, u0, a, b, 0, chunks, 1)  # start only: prev = u^{-1}, cur = u^0
+    E0 = sy.sy_wave3d_energy(q, p, cv, pv)[0]
+    pv, cv, _ = sy.sy_wave3d_run(q, p, u0, a, b, steps, chunks, 1)
+    E1 = sy.sy_wave3d_energy(q, p, cv, pv)[0]
+    assert E0 > 0 and abs(E1 - E0) / E0 < 1e-3
