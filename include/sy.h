@@ -402,6 +402,8 @@ sy_status sy_mlp_forward(sy_mlp_t m, const float* d_X, int64_t B, float* d_Y);
  * (and then the call synchronises).  The reduction over samples has a fixed shape,
  * so the gradient is bit-reproducible. */
 sy_status sy_mlp_loss_grad(sy_mlp_t m, const float* d_X, const float* d_T, int64_t B, float* loss);
+/* The backward pass under its own name: identical to sy_mlp_loss_grad. */
+sy_status sy_mlp_backward(sy_mlp_t m, const float* d_X, const float* d_T, int64_t B, float* loss);
 /* One Adam step with the current gradient. */
 sy_status sy_mlp_adam_step(sy_mlp_t m, float lr, float beta1, float beta2, float eps);
 /* Train on host arrays X (n x F) and T (n x O): the inputs and targets are
@@ -629,6 +631,23 @@ sy_status sy_wave3d_energy(sy_queue_t q, const sy_stencil3d_params* p, const voi
  * x threads per block (128, 256); variant 0 is the default. */
 sy_status sy_stencil3d_variant_count(int radius, int dtype, int* count);
 sy_status sy_stencil3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads);
+
+/* Exhaustive tuner of the 3D step (as sy_tune_stencil): its tile variants x chunk counts (plane chunks). */
+sy_status sy_tune_stencil3d(sy_queue_t q, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
+                            void* u_next, const int* chunk_counts, int n_counts, int reps, sy_tune_record* out,
+                            int max_out, int* n_out);
+/* Exhaustive search over every candidate of one kernel kind, the baseline the
+ * cost model's regret is measured against: kind SY_TUNE_SAXPY (n elements;
+ * in0 = x, in1 = y, out_buf = z; params unused), SY_TUNE_STENCIL (params = a
+ * sy_stencil_params; in0 = u_prev, in1 = u_cur, out_buf = u_next) or
+ * SY_TUNE_STENCIL3D (params = a sy_stencil3d_params; same buffers).  Records as
+ * the per-kind tuners above; *best = index of the fastest record. */
+#define SY_TUNE_SAXPY 0
+#define SY_TUNE_STENCIL 1
+#define SY_TUNE_STENCIL3D 2
+sy_status sy_tune_exhaustive(sy_queue_t q, int kind, const void* params, int64_t n, const void* in0, const void* in1,
+                             void* out_buf, const int* chunk_counts, int n_counts, int reps, sy_tune_record* out,
+                             int max_out, int* n_out, int* best);
 
 /* Allocation-free form of sy_wave_energy.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the

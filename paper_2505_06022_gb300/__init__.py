@@ -178,6 +178,9 @@ _SIGS = {
     "sy_wave3d_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
     "sy_stencil3d_variant_count": [C.c_int, C.c_int, _p],
     "sy_wave3d_energy": [_p, _p, _p, _p, _p, _p, _p],
+    "sy_tune_stencil3d": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p],
+    "sy_tune_exhaustive": [_p, C.c_int, _p, _i64, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p, _p],
+    "sy_mlp_backward": [_p, _p, _p, _i64, _p],
     "sy_stencil3d_variant_info": [C.c_int, C.c_int, C.c_int, _p, _p],
     "sy_rm_box": [_p, _p, _p, _p],
     "sy_rm_box_transfers": [_p, _p, C.c_int, _p, _p, C.c_int, _p],
@@ -857,3 +860,24 @@ def sy_rm_box_transfers(rm: RangeMapper, chunks, extent) -> list:
     out = (BoxTransfer * max(1, n.value))()
     _call("sy_rm_box_transfers", C.byref(rm), arr, len(chunks), ext, out, n.value, C.byref(n))
     return [(t.src, t.dst, _unbox(t.box)) for t in out[: n.value]]
+
+
+SY_TUNE_SAXPY, SY_TUNE_STENCIL, SY_TUNE_STENCIL3D = 0, 1, 2
+
+
+def sy_tune_exhaustive(q: int, kind: int, params, n: int, in0, in1, out_buf, chunk_counts, reps: int = 3):
+    """Every candidate of one kernel kind timed on the caller's buffers: (records, best index),
+    records as (variant, tile_rows, tile_cols, threads, chunks, ms)."""
+    counts = (C.c_int * max(1, len(chunk_counts)))(*chunk_counts)
+    cap = 64 * max(1, len(chunk_counts))
+    recs = (TuneRecord * cap)()
+    n_out, best = C.c_int(0), C.c_int(-1)
+    _call("sy_tune_exhaustive", q, int(kind), None if params is None else C.byref(params), int(n), _ptr(in0),
+          _ptr(in1), _ptr(out_buf), counts, len(chunk_counts), int(reps), recs, cap, C.byref(n_out), C.byref(best))
+    return [(r.variant, r.tile_rows, r.tile_cols, r.threads, r.chunks, r.ms) for r in recs[: n_out.value]], best.value
+
+
+def sy_mlp_backward(m, d_X, d_T, B: int, want_loss: bool = True):
+    loss = C.c_float(0.0)
+    _call("sy_mlp_backward", m, _ptr(d_X), _ptr(d_T), int(B), C.byref(loss) if want_loss else None)
+    return loss.value if want_loss else None

@@ -513,6 +513,10 @@ sy_status sy_mlp_forward(sy_mlp_t h, const float* d_X, int64_t B, float* d_Y) {
     return forward(M, d_X, B, d_Y, false);
 }
 
+sy_status sy_mlp_backward(sy_mlp_t h, const float* d_X, const float* d_T, int64_t B, float* loss) {
+    return sy_mlp_loss_grad(h, d_X, d_T, B, loss);
+}
+
 sy_status sy_mlp_loss_grad(sy_mlp_t h, const float* d_X, const float* d_T, int64_t B, float* loss) {
     if (!h) return fail(SY_ERR_NULL_POINTER, "model is NULL");
     if (B < 1) return fail(SY_ERR_INVALID_ARGUMENT, "B < 1");

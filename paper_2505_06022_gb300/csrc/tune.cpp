@@ -1,8 +1,8 @@
 // Exhaustive autotuner and cost-model features.
 //
 // The tuner times every candidate configuration of a kernel on the caller's
-// buffers -- tile variant x chunk count for the stencil, launch variant x chunk
-// count for SAXPY -- using the launches' own device timestamps (no event
+// buffers -- tile variant x chunk count for the 2D and 3D stencils, launch
+// variant x chunk count for SAXPY -- using the launches' own device timestamps (no event
 // records between launches), and reports the median of `reps` timed runs after
 // one warm-up run.  A run's time is the span from the first chunk's first block
 // to the last chunk's last block.  It is both the fallback of the learned cost
@@ -166,6 +166,78 @@ sy_status sy_tune_saxpy(sy_queue_t qh, int64_t n, const float* x, const float* y
             rec.ms = median(runs);
         }
     }
+    return SY_OK;
+}
+
+sy_status sy_tune_stencil3d(sy_queue_t qh, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
+                            void* u_next, const int* chunk_counts, int n_counts, int reps, sy_tune_record* out,
+                            int max_out, int* n_out) {
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil3d_param_checks(p));
+    if (!out || !n_out) return fail(SY_ERR_NULL_POINTER, "out or n_out is NULL");
+    if (reps < 1) return fail(SY_ERR_INVALID_ARGUMENT, "reps < 1");
+    if (p->nz < 1 || p->ny < 1 || p->nx < 1) return fail(SY_ERR_INVALID_ARGUMENT, "empty grid");
+    SY_TRY(validate_counts(chunk_counts, n_counts, p->nz));
+    const int nv = kWave3dVariants;
+    if (max_out < nv * n_counts) return fail(SY_ERR_INVALID_ARGUMENT, "out holds %d, need %d", max_out, nv * n_counts);
+    *n_out = 0;
+    std::vector<sy_chunk> chunks;
+    for (int ci = 0; ci < n_counts; ++ci) {
+        const int k = chunk_counts[ci];
+        chunks.resize(k);
+        SY_TRY(sy_split_rows(p->nz, k, chunks.data()));
+        for (int v = 1; v <= nv; ++v) {
+            sy_stencil3d_params pv = *p;
+            pv.variant = v;
+            std::vector<double> runs;
+            std::vector<sy_event> evs(k);
+            for (int r = 0; r <= reps; ++r) {  // run 0 warms up
+                SY_TRY(stencil3d_common(q, &pv, u_prev, u_cur, u_next, chunks.data(), k, p->radius, evs.data(),
+                                        false));
+                SY_CUDA(cudaStreamSynchronize(q->stream));
+                double ms = 0.0;
+                SY_TRY(span_ms(q, evs, &ms));
+                if (r > 0) runs.push_back(ms);
+            }
+            sy_tune_record& rec = out[(*n_out)++];
+            rec.variant = v;
+            wave3d_variant_info(p->radius, p->dtype, v, &rec.tile_rows, &rec.threads);
+            rec.tile_cols = 32 * static_cast<int32_t>(16 / dtype_size(p->dtype));
+            rec.chunks = k;
+            rec.ms = median(runs);
+        }
+    }
+    return SY_OK;
+}
+
+sy_status sy_tune_exhaustive(sy_queue_t q, int kind, const void* params, int64_t n, const void* in0, const void* in1,
+                             void* out_buf, const int* chunk_counts, int n_counts, int reps, sy_tune_record* out,
+                             int max_out, int* n_out, int* best) {
+    if (!best || !n_out) return fail(SY_ERR_NULL_POINTER, "best or n_out is NULL");
+    sy_status st;
+    switch (kind) {
+        case SY_TUNE_SAXPY:
+            st = sy_tune_saxpy(q, n, static_cast<const float*>(in0), static_cast<const float*>(in1),
+                               static_cast<float*>(out_buf), chunk_counts, n_counts, reps, out, max_out, n_out);
+            break;
+        case SY_TUNE_STENCIL:
+            if (!params) return fail(SY_ERR_NULL_POINTER, "params is NULL");
+            st = sy_tune_stencil(q, static_cast<const sy_stencil_params*>(params), in0, in1, out_buf, chunk_counts,
+                                 n_counts, reps, out, max_out, n_out);
+            break;
+        case SY_TUNE_STENCIL3D:
+            if (!params) return fail(SY_ERR_NULL_POINTER, "params is NULL");
+            st = sy_tune_stencil3d(q, static_cast<const sy_stencil3d_params*>(params), in0, in1, out_buf,
+                                   chunk_counts, n_counts, reps, out, max_out, n_out);
+            break;
+        default: return fail(SY_ERR_INVALID_ARGUMENT, "unknown tuning kind %d", kind);
+    }
+    if (st != SY_OK) return st;
+    int b = 0;
+    for (int i = 1; i < *n_out; ++i)
+        if (out[i].ms < out[b].ms) b = i;
+    *best = b;
     return SY_OK;
 }
 

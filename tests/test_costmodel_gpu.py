@@ -67,3 +67,29 @@ def test_learned_model_beats_the_default_on_held_out_shapes(queue):
     assert res["model"]["mean"] <= 0.10, res
     assert res["model"]["mean"] < res["default"]["mean"], res
     assert res["model"]["mean"] < 0.1 * res["random_expected_mean"], res
+
+
+def test_exhaustive_tuner_every_kind(queue):
+    """sy_tune_exhaustive: the complete candidate list of each kind (SAXPY, 2D step, 3D step) and
+    the index of the fastest record."""
+    torch = torch_cuda()
+    x, y, z = (torch.zeros(1 << 20, device="cuda") for _ in range(3))
+    recs, best = sy.sy_tune_exhaustive(queue.handle, sy.SY_TUNE_SAXPY, None, 1 << 20, x, y, z, (1, 2), reps=2)
+    assert len(recs) == 2 * sy.sy_saxpy_variant_count()
+    ny, nx = 512, 1024
+    a, b, c = (torch.zeros(ny, nx, device="cuda") for _ in range(3))
+    p = sy.stencil_params(ny, nx, 1, 0.25, "f32")
+    recs2, best2 = sy.sy_tune_exhaustive(queue.handle, sy.SY_TUNE_STENCIL, p, 0, a, b, c, (1, 4), reps=2)
+    assert len(recs2) == 2 * sy.sy_stencil_variant_count(1, sy.SY_F32)
+    n3 = 128
+    a3, b3, c3 = (torch.zeros(n3 * n3 * n3, device="cuda") for _ in range(3))
+    p3 = sy.stencil3d_params(n3, n3, n3, 1, 0.125, "f32")
+    recs3, best3 = sy.sy_tune_exhaustive(queue.handle, sy.SY_TUNE_STENCIL3D, p3, 0, a3, b3, c3, (1, 4), reps=2)
+    assert len(recs3) == 2 * sy.sy_stencil3d_variant_count(1, "f32")
+    assert {(r[0], r[4]) for r in recs3} == {(v, k) for v in range(1, 7) for k in (1, 4)}
+    for rs, bi in ((recs, best), (recs2, best2), (recs3, best3)):
+        assert all(r[5] > 0 for r in rs)
+        assert rs[bi][5] == min(r[5] for r in rs)
+    with pytest.raises(sy.SyError) as e:
+        sy.sy_tune_exhaustive(queue.handle, 7, None, 1, x, y, z, (1,), reps=1)
+    assert e.value.name == "SY_ERR_INVALID_ARGUMENT"

@@ -55,8 +55,10 @@ def test_forward_and_gradients_match_oracle(q, B):
                              ("W3", H * F + 2 * H + H * H, H * F + 2 * H + H * H + O * H)]:
             seg, seg64 = g[lo:hi], g64[lo:hi]
             assert np.max(np.abs(seg - seg64)) <= 1e-4 * max(np.max(np.abs(seg64)), 1e-12), name
-        # fixed-shape reductions: bit-reproducible
+        # fixed-shape reductions: bit-reproducible (also under the backward pass's own name)
         sy.sy_mlp_loss_grad(m, dX, dT, B, want_loss=False)
+        assert np.array_equal(sy.sy_mlp_get_grad(m).view(np.uint32), g.view(np.uint32))
+        assert sy.sy_mlp_backward(m, dX, dT, B) == loss
         assert np.array_equal(sy.sy_mlp_get_grad(m).view(np.uint32), g.view(np.uint32))
     finally:
         sy.sy_mlp_destroy(m)
