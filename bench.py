@@ -356,7 +356,7 @@ def measure_batched(q, stream) -> dict:
 
 def measure_saxpy(q, stream) -> dict:
     """SAXPY (the paper's Listing 1): N = 2^20, alpha = 2.5, seed 0 (the configured case,
-    latency-bound: 12.6 MB per call), and N = 2^28 (3.2 GB per call, HBM-bound); elements/s
+    latency-bound: 12.6 MB per call), and N = 2^24, 2^26, 2^28 (up to 3.2 GB per call, HBM-bound); elements/s
     and GB/s (12 B per element) over back-to-back calls, and the result checked bit for bit
     against fl(fl(alpha x) + y) computed on the host in FP64 (exact for these inputs)."""
     import numpy as np
@@ -366,12 +366,12 @@ def measure_saxpy(q, stream) -> dict:
     from paper_2505_06022_gb300 import inputs
 
     out = {}
-    for log2n in (20, 28):
+    for log2n in (20, 24, 26, 28):
         n = 1 << log2n
         x, y = inputs.saxpy_inputs(n, seed=0)
         xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
         zd = torch.empty_like(xd)
-        calls = 2000 if log2n == 20 else 40
+        calls = {20: 2000, 24: 400, 26: 100, 28: 40}[log2n]
         run = lambda: [sy.sy_saxpy(q.handle, n, 2.5, xd, yd, zd) for _ in range(calls)]
         run()
         reps, ms, joules = _metered(q, stream, run, min_seconds=0.5)
@@ -612,10 +612,34 @@ def run_gpu(args) -> None:
                 "stamp_avg_chunk_ms": statistics.mean(stamp_ms),
                 "stamp_chunk_gbs": chunk_bytes / (statistics.mean(stamp_ms) * 1e-3) / 1e9}
     energy = None
-    if have_energy and joules is not None and joules > 0:
-        kern_j = [sy.sy_kernel_energy(q.handle, e) for e in events[CHUNKS:]]
-        energy = {"joules": joules, "window_s": seconds, "j_per_update": joules / (args.steps * updates_per_step),
-                  "avg_power_w": joules / seconds, "chunk_kernel_j_mean": statistics.mean(kern_j)}
+    if have_energy and joules is not None:
+        # J/update over a window of >= 2 s (20 periods of NVML's 100 ms energy counter):
+        # the timed region when it is that long, else a dedicated window of whole
+        # simulations right after it; idle power from a 2 s window with the GPU idle.
+        sims = args.steps
+        if seconds < 2.0:
+            torch.cuda.synchronize()
+            sy.sy_meter_begin(q.handle)
+            sims, t0 = 0, time.perf_counter()
+            while sims < 3 or time.perf_counter() - t0 < 2.0:
+                _, _, events = simulate(u0, True)
+                sims += 1
+                if sims % 4 == 0:
+                    torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            joules, seconds = sy.sy_meter_end(q.handle)
+        torch.cuda.synchronize()
+        sy.sy_meter_begin(q.handle)
+        time.sleep(2.0)
+        idle_j, idle_s = sy.sy_meter_end(q.handle)
+        if joules > 0:
+            idle_w = idle_j / idle_s
+            kern_j = [sy.sy_kernel_energy(q.handle, e) for e in events[CHUNKS:]]
+            energy = {"joules": joules, "window_s": seconds, "simulations": sims,
+                      "j_per_update": joules / (sims * updates_per_step), "avg_power_w": joules / seconds,
+                      "idle_w": idle_w,
+                      "j_per_update_above_idle": (joules - idle_w * seconds) / (sims * updates_per_step),
+                      "chunk_kernel_j_mean": statistics.mean(kern_j)}
 
     # ---- e2e: host (pinned) initial field in, final field out, through the same API ----
     e2e = None
@@ -665,7 +689,18 @@ def run_gpu(args) -> None:
     if dist:
         dist.barrier()
     if rank == 0:
-        cpu = oracle_sample(args.cpu_seconds) if (world == 1 and args.cpu_seconds > 0) else None
+        cpu = None
+        if world == 1 and args.cpu_seconds > 0:
+            import oracle
+
+            cpu = oracle_sample(args.cpu_seconds)
+            all_cores = oracle.threads()
+            oracle.set_threads(1)  # the same sample on one host core, for the per-core rate
+            try:
+                one = oracle_sample(max(2.0, args.cpu_seconds / 4))
+            finally:
+                oracle.set_threads(all_cores)
+            cpu["single_thread_value"] = one["value"]
         line = {
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -683,7 +718,7 @@ def run_gpu(args) -> None:
             "forms": forms,
             "clocks": clk,
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
-                                                                          "sample")},
+                                                                          "sample", "single_thread_value")},
         }
         print(json.dumps(line), flush=True)
     q.close()
