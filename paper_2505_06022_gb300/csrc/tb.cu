@@ -29,8 +29,7 @@
 namespace sy {
 namespace tb {
 
-constexpr int kThreads = 256;
-constexpr int BX = 128;
+constexpr int kThreads = 256;  // 8 warps: one row-lane each
 constexpr int BY = 32;
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
@@ -52,11 +51,13 @@ struct Geo {
     static constexpr int ES = sizeof(S);
     static constexpr int VEC = 16 / ES;                                     // elements per 16 bytes
     static constexpr int PAD = ((T * R + VEC - 1) / VEC) * VEC;             // 16-byte aligned x halo
-    static constexpr int W = BX + 2 * PAD;                                  // box / row width (elements)
+    static constexpr int W = 32 * VEC;                                      // box / row width: one warp's span
+    static constexpr int BX = W - 2 * PAD;                                  // output columns of a tile
     static constexpr int H = BY + 2 * T * R;                                // box height
     static constexpr int BUF = ((W * H * ES + 127) / 128) * 128;            // one field, 128-byte aligned
     static constexpr int SMEM = 4 * BUF + 2 * 8;                            // 2 stages x 2 fields + 2 barriers
     static constexpr unsigned TX = 2u * W * H * ES;                         // bytes a stage receives
+    static_assert(BX > 0 && BX % VEC == 0, "tile width");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -120,44 +121,44 @@ template <>
 __device__ __forceinline__ __half to_s<__half>(float v) { return __float2half_rn(v); }
 
 // One step over buffer rows [k*R, H - k*R) and every column of the W-wide
-// buffers: X holds u^m, Y holds u^{m-1} and receives u^{m+1}.  Each thread owns one
-// 16-byte column group and a contiguous run of rows; the 2R+1 rows of its group
-// around the current row stay in registers (a rolling window), the groups left
-// and right of it supply the horizontal neighbours.  Results in the outer PAD
-// columns are computed from partial neighbourhoods, but the needed region of
-// step k, [PAD - (T-k)R, PAD + BX + (T-k)R), lies inside [k R, W - k R) where
-// every value is exact (PAD >= T R).  Points outside the grid are set to zero
-// (interior tiles skip the test).
+// buffers: X holds u^m, Y holds u^{m-1} and receives u^{m+1}.  A row is exactly
+// one warp wide: lane g owns the 16-byte column group g, and each warp owns a
+// contiguous run of rows; the 2R+1 rows of its group around the current row
+// stay in registers (a rolling window), and the horizontal neighbours come from
+// lanes g-1 and g+1 by shuffles (zeros beyond the buffer's outer columns).  Results
+// in the outer PAD columns are computed from partial neighbourhoods, but the
+// needed region of step k, [PAD - (T-k)R, PAD + BX + (T-k)R), lies inside
+// [k R, W - k R) where every value is exact (PAD >= T R).  Points outside the grid
+// are set to zero (interior tiles skip the test).
 template <typename S, int R, int T>
 __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_buf0, int x_buf0, bool interior,
                                         int64_t ny, int64_t nx, float c2) {
     using G = Geo<S, R, T>;
     using Tr = wave::Traits<S>;
     constexpr int V = Tr::V;
-    constexpr int NG = G::W / V;               // 16-byte groups per row
-    constexpr int NRL = kThreads / NG;         // row lanes
-    const int g = threadIdx.x % NG, rl = threadIdx.x / NG;
-    if (rl >= NRL) return;
+    constexpr int NG = 32;                     // 16-byte groups per row = lanes
+    constexpr int NRL = kThreads / 32;         // row lanes = warps
+    const int g = threadIdx.x & 31, rl = threadIdx.x >> 5;
     const int r_lo = k * R, r_hi = G::H - k * R;
     const int per = (r_hi - r_lo + NRL - 1) / NRL;
     const int r0 = r_lo + rl * per;
     const int r1 = r0 + per < r_hi ? r0 + per : r_hi;
-    if (r0 >= r1) return;
+    if (r0 >= r1) return;  // warp-uniform
     uint4 win[2 * R + 1];  // rows r - R .. r + R of group g
 #pragma unroll
     for (int d = 0; d < 2 * R; ++d) win[d] = X[(r0 - R + d) * NG + g];
     for (int r = r0; r < r1; ++r) {
         win[2 * R] = X[(r + R) * NG + g];
-        const uint4 lv = X[r * NG + g - 1];  // previous group (in bounds: r >= R >= 1)
-        const uint4 rv = X[r * NG + g + 1];  // next group (in bounds: r + 1 <= H - 1)
         const uint4 pv = Y[r * NG + g];
         float ext[V + 2 * R];                // columns g*V - R .. g*V + V + R - 1
 #pragma unroll
         for (int e = 0; e < V; ++e) ext[R + e] = Tr::elem(win[R], e);
 #pragma unroll
         for (int d = 1; d <= R; ++d) {
-            ext[R - d] = Tr::elem(lv, V - d);
-            ext[R + V - 1 + d] = Tr::elem(rv, d - 1);
+            const float from_left = __shfl_up_sync(wave::kFull, ext[R + V - d], 1);
+            const float from_right = __shfl_down_sync(wave::kFull, ext[R + d - 1], 1);
+            ext[R - d] = g == 0 ? 0.0f : from_left;
+            ext[R + V - 1 + d] = g == 31 ? 0.0f : from_right;
         }
         float out[V];
         if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions (packed FP32 adds)
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant
     // copies of tile t into stage s: u^n box into field 0, u^{n-1} box into field 1
     auto issue = [&](int64_t t, int s, bool skip) {
         const int64_t ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
-        const int x = static_cast<int>(tx * BX) - G::PAD;
+        const int x = static_cast<int>(tx * G::BX) - G::PAD;
         const int y = static_cast<int>(a.row_begin + ty * BY) - T * R;
         unsigned char* base = smem + 2 * s * G::BUF;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic writes to this stage
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant
         uint4* X = reinterpret_cast<uint4*>(smem + 2 * s * G::BUF);  // u^{m}
         uint4* Y = reinterpret_cast<uint4*>(smem + 2 * s * G::BUF + G::BUF);  // u^{m-1} -> u^{m+1}
         const int64_t ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
-        const int64_t y0 = a.row_begin + ty * BY, x0 = tx * BX;
+        const int64_t y0 = a.row_begin + ty * BY, x0 = tx * G::BX;
         const int y_buf0 = static_cast<int>(y0) - T * R;  // global row of buffer row 0
         const int x_buf0 = static_cast<int>(x0) - G::PAD;  // global column of buffer column 0
         const bool interior = y_buf0 >= 0 && y_buf0 + G::H <= a.ny && x_buf0 >= 0 && x_buf0 + G::W <= a.nx;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant
         }
         // X = u^{n+T} and Y = u^{n+T-1} on the tile: write the tile's rows of the chunk,
         // one 16-byte group per thread (element stores at the right edge of the grid)
-        constexpr int TG = BX / V;  // groups per tile row
+        constexpr int TG = G::BX / V;  // groups per tile row
         for (int idx = tid; idx < BY * TG; idx += kThreads) {
             const int i = idx / TG, gg = idx - i * TG;
             const int64_t gy = y0 + i;
@@ -363,7 +364,7 @@ sy_status launch_tb(Queue* q, const TBLaunch& w) {
     a.pitch_bytes = w.pitch_bytes;
     a.row_begin = w.row_begin;
     a.row_end = w.row_end;
-    a.tiles_x = (w.nx + BX - 1) / BX;
+    a.tiles_x = (w.nx + G::BX - 1) / G::BX;
     a.tiles = a.tiles_x * ((w.row_end - w.row_begin + BY - 1) / BY);
     a.c2 = w.c2;
     a.err = q->d_flags;
