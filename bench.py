@@ -383,6 +383,29 @@ def measure_saxpy(q, stream) -> dict:
                                "us_per_call": per * 1e3, "bit_exact": bool(np.array_equal(z.view(np.uint32),
                                                                                          want.view(np.uint32))),
                                "j_per_element": None if not joules else joules / (reps * calls * n)}
+        if log2n == 20:
+            # the same calls captured into one CUDA graph (100 per replay): the device-side rate,
+            # without the Python-to-C call in front of every launch
+            side = torch.cuda.Stream()
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                qs = sy.Queue(q.device, side)
+                sy.sy_saxpy(qs.handle, n, 2.5, xd, yd, zd)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                for _ in range(100):
+                    sy.sy_saxpy(qs.handle, n, 2.5, xd, yd, zd)
+            zd.zero_()
+            g.replay()
+            reps_g, ms_g, _ = _metered(q, stream, g.replay, min_seconds=0.3)
+            zg = zd.cpu().numpy()
+            out["n_2^20"]["graph"] = {"elements_per_s": n / (ms_g / 100 * 1e-3),
+                                      "gb_per_s": 12 * n / (ms_g / 100 * 1e-3) / 1e9,
+                                      "us_per_call": ms_g / 100 * 1e3, "calls_per_replay": 100,
+                                      "bit_exact": bool(np.array_equal(zg.view(np.uint32), want.view(np.uint32)))}
+            del g
+            qs.close()
         del xd, yd, zd
     return out
 
