@@ -618,6 +618,14 @@ sy_status sy_stencil3d_step(sy_queue_t q, const sy_stencil3d_params* p, const vo
 /* Taylor start: u_m1 = u0 + (c2/2) L u0. */
 sy_status sy_stencil3d_start(sy_queue_t q, const sy_stencil3d_params* p, const void* u0, void* u_m1,
                              const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* chunk_events);
+/* One chunk of planes on its own: step planes [plane_begin, plane_end) of the
+ * grid in p, reading the planes the neighbourhood range mapper gives them, with
+ * no requirement that other chunks exist -- the kernel a device runs on the
+ * chunk it holds (its halo planes brought in by the caller).  start != 0 runs
+ * the Taylor start (u_prev unused).  Same aliasing rules as sy_stencil3d_step. */
+sy_status sy_stencil3d_step_planes(sy_queue_t q, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
+                                   void* u_next, int64_t plane_begin, int64_t plane_end, int halo_radius, int start,
+                                   sy_event* ev);
 /* Start + `steps` steps as one cached CUDA graph, as sy_wave_run. */
 sy_status sy_wave3d_run(sy_queue_t q, const sy_stencil3d_params* p, const void* u0, void* u_a, void* u_b,
                         int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* events,

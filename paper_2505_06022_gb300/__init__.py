@@ -178,6 +178,7 @@ _SIGS = {
     "sy_wave3d_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
     "sy_stencil3d_variant_count": [C.c_int, C.c_int, _p],
     "sy_wave3d_energy": [_p, _p, _p, _p, _p, _p, _p],
+    "sy_stencil3d_step_planes": [_p, _p, _p, _p, _p, _i64, _i64, C.c_int, C.c_int, _p],
     "sy_tune_stencil3d": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p],
     "sy_tune_exhaustive": [_p, C.c_int, _p, _i64, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p, _p],
     "sy_mlp_backward": [_p, _p, _p, _i64, _p],
@@ -794,6 +795,12 @@ def sy_stencil3d_start(q: int, p: Stencil3dParams, u0, u_m1, chunks, halo_radius
     _call("sy_stencil3d_start", q, C.byref(p), _ptr(u0), _ptr(u_m1), arr, k, halo_radius,
           evs if want_events else None)
     return list(evs[:k]) if want_events else []
+
+
+def sy_stencil3d_step_planes(q: int, p: Stencil3dParams, u_prev, u_cur, u_next, plane_begin: int, plane_end: int,
+                             halo_radius: int, start: bool = False) -> None:
+    _call("sy_stencil3d_step_planes", q, C.byref(p), _ptr(u_prev), _ptr(u_cur), _ptr(u_next), int(plane_begin),
+          int(plane_end), halo_radius, 1 if start else 0, None)
 
 
 def sy_wave3d_run(q: int, p: Stencil3dParams, u0, u_a, u_b, steps: int, chunks, halo_radius: int,

@@ -82,6 +82,47 @@ sy_status sy_stencil3d_start(sy_queue_t qh, const sy_stencil3d_params* p, const 
     return stencil3d_common(q, p, nullptr, u0, u_m1, chunks, n_chunks, halo_radius, chunk_events, true);
 }
 
+sy_status sy_stencil3d_step_planes(sy_queue_t qh, const sy_stencil3d_params* p, const void* u_prev,
+                                   const void* u_cur, void* u_next, int64_t plane_begin, int64_t plane_end,
+                                   int halo_radius, int start, sy_event* ev) {
+    clear_error();
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil3d_param_checks(p));
+    if (plane_begin < 0 || plane_end < plane_begin || plane_end > p->nz)
+        return fail(SY_ERR_BAD_CHUNKS, "planes [%lld, %lld) outside [0, %lld)", (long long)plane_begin,
+                    (long long)plane_end, (long long)p->nz);
+    if (halo_radius < p->radius)
+        return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
+    if (!u_cur || !u_next || (!start && !u_prev)) return fail(SY_ERR_NULL_POINTER, "field pointer is NULL");
+    const size_t bytes = static_cast<size_t>(p->nz) * static_cast<size_t>(p->plane) * dtype_size(p->dtype);
+    if (ranges_overlap(u_next, bytes, u_cur, bytes)) return fail(SY_ERR_ALIAS, "u_next overlaps u_cur");
+    if (!start && u_next != u_prev && ranges_overlap(u_next, bytes, u_prev, bytes))
+        return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
+    SY_TRY(use_device(q));
+    EventRecord* rec;
+    SY_TRY(begin_event(q, ev, &rec));
+    WaveLaunch3 w;
+    w.nz = p->nz;
+    w.ny = p->ny;
+    w.nx = p->nx;
+    w.pitch = p->pitch;
+    w.plane = p->plane;
+    w.radius = p->radius;
+    w.dtype = p->dtype;
+    w.variant = p->variant;
+    w.c2 = start ? 0.5f * p->c2 : p->c2;
+    w.start = start != 0;
+    w.u_prev = start ? u_cur : u_prev;
+    w.u_cur = u_cur;
+    w.u_next = u_next;
+    w.z_begin = plane_begin;
+    w.z_end = plane_end;
+    w.pdl = 0;
+    SY_TRY(launch_wave3d(q, w));
+    return end_event(q, rec);
+}
+
 sy_status sy_wave3d_energy(sy_queue_t qh, const sy_stencil3d_params* p, const void* u_new, const void* u_old,
                            double* energy, double* kinetic, double* potential) {
     clear_error();

@@ -2,8 +2,9 @@
 devices (§3) with the data transfers inferred from the neighbourhood range
 mapper.
 
-Rank k holds chunk k of the row split in a buffer of its own (the split-buffer
-layout: halo_lo rows above its rows, halo_hi below).  Before every step the
+Rank k holds chunk k of the row split (of the plane split, for the 3D grid) in a
+buffer of its own (the split-buffer layout: halo_lo rows or planes before its
+own, halo_hi after).  Before every step the
 halo rows of u^n are exchanged with point-to-point messages
 (torch.distributed batch_isend_irecv: NCCL between GPUs, gloo between CPU
 processes); which rows go where is `sy_rm_transfers`, the same inference the
@@ -14,7 +15,8 @@ from __future__ import annotations
 
 from typing import Callable
 
-from . import stencil_params, sy_rm_transfers, sy_split_layout, sy_split_rows, sy_stencil_step_rows
+from . import (stencil3d_params, stencil_params, sy_rm_transfers, sy_split_layout, sy_split_rows,
+               sy_stencil3d_step_planes, sy_stencil_step_rows)
 
 
 class RankChunk:
@@ -73,3 +75,24 @@ class GpuRankChunk(RankChunk):
         self.exchange(cur, dist)
         sy_stencil_step_rows(self.q.handle, self.params, None if start else prev, cur, nxt, self.own[0],
                              self.own[1], self.halo, start=start)
+
+
+class GpuRankChunk3d(RankChunk):
+    """The 3D grid split into chunks of planes, one per rank: the same exchange along
+    dimension 0 (whole planes), stepping with the library's 3D kernel on this rank's
+    planes.  Local buffers are (planes, ny, pitch) tensors."""
+
+    def __init__(self, queue, nz: int, ny: int, nx: int, radius: int, halo: int, rank: int, world: int, c2: float,
+                 dtype: str = "f32", pitch: int | None = None):
+        super().__init__(ny=nz, nx=nx, radius=radius, halo=halo, rank=rank, world=world, pitch=pitch)
+        self.nz, self.ny3 = nz, ny
+        self.q = queue
+        self.params = stencil3d_params(self.rows, ny, nx, radius, c2, dtype, pitch=self.pitch)
+
+    def step(self, prev, cur, nxt, dist, step_fn=None, start: bool = False) -> None:
+        self.exchange(cur, dist)
+        if step_fn is not None:
+            step_fn(prev, cur, nxt, self.own[0], self.own[1], start)
+            return
+        sy_stencil3d_step_planes(self.q.handle, self.params, None if start else prev, cur, nxt, self.own[0],
+                                 self.own[1], self.halo, start=start)

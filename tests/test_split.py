@@ -107,3 +107,53 @@ def test_gloo_rank_chunks_equal_whole_grid(tmp_path, world, ny, nx, r, h, steps)
     u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 3.0) + 0.1 * inputs.random_field(7, ny, nx), "f32")
     _, want = oracle.wave_run_mirror(oracle.F32, u0, steps, r, 0.25)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+# ---- the 3D grid split into chunks of planes ---------------------------------------
+
+def _rank_main_3d(rank, world, port, nz, ny, nx, r, h, steps, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_06022_gb300.distributed import GpuRankChunk3d
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    rc = GpuRankChunk3d(None, nz, ny, nx, r, h, rank, world, 0.125)  # no GPU: the oracle steps (below)
+    u0 = inputs.to_storage(inputs.gaussian_pulse_3d(nz, ny, nx, 2.0) + 0.1 * inputs.random_field_3d(7, nz, ny, nx),
+                           "f32")
+    a, b = rc.chunks[rank]
+    cur = torch.zeros(rc.rows, ny, nx, dtype=torch.float32)
+    cur[rc.own[0]: rc.own[1]] = torch.from_numpy(u0[a:b])
+    prev = torch.zeros_like(cur)
+
+    def oracle_step(p_, c_, n_, z0, z1, start):
+        # CPU stand-in for the 3D kernel on the local buffer, own planes kept
+        if start:
+            full = oracle.wave3d_start_mirror(oracle.F32, c_.numpy().copy(), r, 0.125)
+        else:
+            full = oracle.wave3d_step_mirror(oracle.F32, p_.numpy().copy(), c_.numpy().copy(), r, 0.125)
+        n_[z0:z1] = torch.from_numpy(full[z0:z1])
+
+    rc.step(None, cur, prev, dist, oracle_step, start=True)
+    for _ in range(steps):
+        rc.step(prev, cur, prev, dist, oracle_step)
+        prev, cur = cur, prev
+    np.save(os.path.join(out_dir, f"rank{rank}.npy"), cur[rc.own[0]: rc.own[1]].numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,nz,ny,nx,r,h,steps", [(2, 9, 7, 6, 1, 1, 6), (3, 11, 5, 9, 2, 3, 5),
+                                                      (4, 6, 6, 5, 2, 2, 4)])
+def test_gloo_plane_chunks_equal_whole_grid(tmp_path, world, nz, ny, nx, r, h, steps):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+
+    port = _free_port()
+    mp.start_processes(_rank_main_3d, args=(world, port, nz, ny, nx, r, h, steps, str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    got = np.concatenate([np.load(tmp_path / f"rank{k}.npy") for k in range(world)])
+    u0 = inputs.to_storage(inputs.gaussian_pulse_3d(nz, ny, nx, 2.0) + 0.1 * inputs.random_field_3d(7, nz, ny, nx),
+                           "f32")
+    _, want = oracle.wave3d_run_mirror(oracle.F32, u0, steps, r, 0.125)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))

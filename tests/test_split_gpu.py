@@ -83,3 +83,33 @@ def test_step_rows_matches_chunked_step(q):
     with pytest.raises(sy.SyError) as e:
         sy.sy_stencil_step_rows(q, p, prev, cur, nxt, 0, 10, 1)
     assert e.value.name == "SY_ERR_HALO_TOO_SMALL"
+
+
+def test_step_planes_matches_chunked_3d_step(q):
+    """sy_stencil3d_step_planes on plane ranges equals the chunked 3D step, and a rank's local
+    buffer (its planes plus halo planes) stepped on its own planes equals the whole grid."""
+    torch = torch_cuda()
+    nz, ny, nx, r = 14, 20, 140, 2
+    u0 = inputs.to_storage(inputs.gaussian_pulse_3d(nz, ny, nx, 3.0), "f32")
+    cur = torch.from_numpy(u0).cuda()
+    prev = torch.empty_like(cur)
+    p = sy.stencil3d_params(nz, ny, nx, r, 0.125, "f32")
+    for a, b in [(0, 5), (5, 6), (6, 14)]:
+        sy.sy_stencil3d_step_planes(q, p, None, cur, prev, a, b, r, start=True)
+    nxt = torch.empty_like(cur)
+    for a, b in [(0, 7), (7, 14)]:
+        sy.sy_stencil3d_step_planes(q, p, prev, cur, nxt, a, b, r)
+    torch.cuda.synchronize()
+    _, oc = oracle.wave3d_run_mirror(oracle.F32, u0, 1, r, 0.125)
+    assert np.array_equal(nxt.cpu().numpy().view(np.uint32), oc.view(np.uint32))
+    # a local buffer holding planes [4, 10) plus 2 halo planes each side: stepping its own planes
+    lo, hi = 4 - r, 10 + r
+    lp, lc = prev[lo:hi].contiguous(), cur[lo:hi].contiguous()
+    ln = torch.empty_like(lc)
+    pl = sy.stencil3d_params(hi - lo, ny, nx, r, 0.125, "f32")
+    sy.sy_stencil3d_step_planes(q, pl, lp, lc, ln, r, r + 6, r)
+    torch.cuda.synchronize()
+    assert np.array_equal(ln[r: r + 6].cpu().numpy().view(np.uint32), oc[4:10].view(np.uint32))
+    with pytest.raises(sy.SyError) as e:
+        sy.sy_stencil3d_step_planes(q, p, prev, cur, nxt, 3, 15, r)
+    assert e.value.name == "SY_ERR_BAD_CHUNKS"
