@@ -635,8 +635,10 @@ sy_status sy_wave3d_run(sy_queue_t q, const sy_stencil3d_params* p, const void* 
  * whose scratch buffer it shares). */
 sy_status sy_wave3d_energy(sy_queue_t q, const sy_stencil3d_params* p, const void* u_new, const void* u_old,
                            double* energy, double* kinetic, double* potential);
-/* Tile variants: rows of a warp tile (radius 1-2: 1, 2, 4; radius 3-4: 1, 2, 4)
- * x threads per block (128, 256); variant 0 is the default. */
+/* Tile variants 1-6: rows of a warp's tile (1, 2, 4) x threads per block (128,
+ * 256); variants 7-8: a block of 8 warps marching a strip of 8 or 16 rows with
+ * the strip's centre plane in shared memory (tile_rows reports the strip,
+ * threads 256); variant 0 is the default. */
 sy_status sy_stencil3d_variant_count(int radius, int dtype, int* count);
 sy_status sy_stencil3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads);
 

@@ -55,15 +55,18 @@ sy_status launch3_typed(Queue* q, const WaveLaunch3& w, KernelFn3 vec_fn, Kernel
                         (a.pitch_bytes % 16) == 0 && (a.plane_bytes % 16) == 0;
     if (vec_ok) {
         const int64_t span = 32 * static_cast<int64_t>(V);
+        const bool slab = rows < 0;
+        const int64_t tile_rows = slab ? -rows : rows;
         a.tiles_x = (w.nx + span - 1) / span;
-        a.tiles_y = (w.ny + rows - 1) / rows;
-        const int64_t wpb = threads / 32;
+        a.tiles_y = (w.ny + tile_rows - 1) / tile_rows;
+        // a task is one warp's (warp-column kernel) or one block's (slab kernel)
+        const int64_t tasks_per_block = slab ? 1 : threads / 32;
         const int64_t cap = static_cast<int64_t>(wave::kernel_occupancy(reinterpret_cast<const void*>(vec_fn),
                                                                         threads)) * q->sm_count;
-        a.seg = choose_seg(a.tiles_x * a.tiles_y, planes, cap * wpb, w.radius);
+        a.seg = choose_seg(a.tiles_x * a.tiles_y, planes, cap * tasks_per_block, w.radius);
         a.segs = (planes + a.seg - 1) / a.seg;
         a.tasks = a.tiles_x * a.tiles_y * a.segs;
-        int64_t blocks = (a.tasks + wpb - 1) / wpb;
+        int64_t blocks = (a.tasks + tasks_per_block - 1) / tasks_per_block;
         if (blocks > cap) blocks = cap;  // persistent: every block resident at once
         if (w.pdl && wave::launch_overlap_enabled()) {
             a.pdl = w.pdl;
@@ -202,23 +205,37 @@ sy_status launch_wave3d_energy(Queue* q, const sy_stencil3d_params* p, const voi
     return SY_OK;
 }
 
+namespace {
+// The default variant per radius: the fastest of a sweep at 512^3 (FP32) on GB300
+// (radius 1: 5.1e11 updates/s, radius 2: 4.1e11, radius 4: 2.1e11).  Warp columns
+// of one row for radius 1 and 3-4 (the register queue, (2r+1) x rows vectors per
+// lane, sets how many warps stay resident), of two rows for radius 2; the slab
+// variants measured slower (a block waits at every plane's barrier for its halo loads).
+constexpr int kDefaultVariant3[4] = {1, 2, 1, 1};
+
+// Resolved variant -> (rows, threads, slab).
+bool variant3(int radius, int variant, int* rows, int* threads, bool* slab) {
+    const int v = variant == 0 ? kDefaultVariant3[radius - 1] : variant;
+    if (v <= wave3::kColumnVariants3) {
+        const int* table = radius <= 2 ? wave3::kRows12 : wave3::kRows34;
+        *rows = table[(v - 1) % 3];
+        *threads = wave3::kThreads3[(v - 1) / 3];
+        *slab = false;
+    } else {
+        *rows = wave3::kSlabWarps * (v - wave3::kColumnVariants3);
+        *threads = wave3::kSlabWarps * 32;
+        *slab = true;
+    }
+    return true;
+}
+}  // namespace
+
 bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads) {
     if (radius < 1 || radius > 4 || dtype_size(dtype) == 0 || variant < 0 || variant > wave3::kVariants3)
         return false;
-    int rows, thr;
-    if (variant == 0) {
-        // Default per radius: the fastest tile of a sweep at 512^3 (FP32) on GB300.
-        // One-row tiles win at radius 1: the register queue ((2r+1) x rows vectors
-        // per lane) sets how many warps stay resident, and the extra halo rows
-        // ((rows + 2r) / rows) come from L2.
-        static const int kDefault[4] = {1, 2, 2, 2};
-        rows = kDefault[radius - 1];
-        thr = 128;
-    } else {
-        const int* table = radius <= 2 ? wave3::kRows12 : wave3::kRows34;
-        rows = table[(variant - 1) % 3];
-        thr = wave3::kThreads3[(variant - 1) / 3];
-    }
+    int rows = 0, thr = 0;
+    bool slab = false;
+    variant3(radius, variant, &rows, &thr, &slab);
     if (tile_rows) *tile_rows = rows;
     if (threads) *threads = thr;
     return true;
@@ -226,8 +243,11 @@ bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int
 
 sy_status launch_wave3d(Queue* q, const WaveLaunch3& w) {
     int rows = 0, threads = 0;
-    if (!wave3d_variant_info(w.radius, w.dtype, w.variant, &rows, &threads))
+    bool slab = false;
+    if (!wave3d_variant_info(w.radius, w.dtype, w.variant, nullptr, nullptr))
         return fail(SY_ERR_INVALID_ARGUMENT, "bad 3D stencil variant %d", w.variant);
+    variant3(w.radius, w.variant, &rows, &threads, &slab);
+    if (slab) rows = -rows;
     switch (w.dtype) {
         case SY_F32: return wave3::launch3_f32(q, w, rows, threads);
         case SY_BF16: return wave3::launch3_bf16(q, w, rows, threads);

@@ -88,6 +88,60 @@ __device__ __forceinline__ float2 update3_2(float2 u, float2 up, const float2 (&
     return add2_rn(inertia, mul2_scalar(c2, acc));
 }
 
+// One row of a lane's V points: c is the row itself, up[d-1] / dn[d-1] the rows d
+// above / below, zm[d-1] / zp[d-1] the same row d planes before / after, pv its
+// u^{n-1}; edge[d-1] the column d beyond the warp's span (lane 0: left, lane 31:
+// right).  Horizontal neighbours inside the span come from the adjacent lanes.
+template <typename S, int R, bool START>
+__device__ __forceinline__ void row_update(const uint4& c, const uint4 (&up)[R], const uint4 (&dn)[R],
+                                           const uint4 (&zm)[R], const uint4 (&zp)[R], const uint4& pv,
+                                           const float (&edge)[R], int lane, float c2,
+                                           float (&out)[Traits<S>::V]) {
+    using T = Traits<S>;
+    constexpr int V = T::V;
+    float ext[V + 2 * R];  // ext[m] holds column x0 - R + m
+#pragma unroll
+    for (int e = 0; e < V; ++e) ext[R + e] = T::elem(c, e);
+#pragma unroll
+    for (int d = 1; d <= R; ++d) {
+        const float from_left = __shfl_up_sync(kFull, ext[R + V - d], 1);
+        const float from_right = __shfl_down_sync(kFull, ext[R + d - 1], 1);
+        ext[R - d] = lane == 0 ? edge[d - 1] : from_left;
+        ext[R + V - 1 + d] = lane == 31 ? edge[d - 1] : from_right;
+    }
+    if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions
+#pragma unroll
+        for (int e = 0; e < V; e += 2) {
+            float2 vert[R], horz[R], depth[R];
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                vert[d - 1] = wave::add2_rn(make_float2(T::elem(up[d - 1], e), T::elem(up[d - 1], e + 1)),
+                                            make_float2(T::elem(dn[d - 1], e), T::elem(dn[d - 1], e + 1)));
+                horz[d - 1] = wave::add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]),
+                                            make_float2(ext[R + e + d], ext[R + e + 1 + d]));
+                depth[d - 1] = wave::add2_rn(make_float2(T::elem(zm[d - 1], e), T::elem(zm[d - 1], e + 1)),
+                                             make_float2(T::elem(zp[d - 1], e), T::elem(zp[d - 1], e + 1)));
+            }
+            const float2 u2 = START ? make_float2(0.0f, 0.0f) : make_float2(T::elem(pv, e), T::elem(pv, e + 1));
+            const float2 o = update3_2<R, START>(make_float2(ext[R + e], ext[R + e + 1]), u2, vert, horz, depth, c2);
+            out[e] = o.x;
+            out[e + 1] = o.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            float vert[R], horz[R], depth[R];
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                vert[d - 1] = __fadd_rn(T::elem(up[d - 1], e), T::elem(dn[d - 1], e));
+                horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                depth[d - 1] = __fadd_rn(T::elem(zm[d - 1], e), T::elem(zp[d - 1], e));
+            }
+            out[e] = update3<R, START>(ext[R + e], START ? 0.0f : T::elem(pv, e), vert, horz, depth, c2);
+        }
+    }
+}
+
 // One warp's task: tile (tx, ty) through the planes of segment sg.  CHECK = false
 // is the interior form: every row the tile reads lies in [0, ny) and every lane's
 // V columns in [0, nx) (planes are always checked against [0, nz)).
@@ -166,65 +220,18 @@ __device__ __forceinline__ void column_impl(const Args3& a, int64_t tx, int64_t 
         char* nbase = a.u_next + z * zb + y0 * pb + x0 * ES;
 #pragma unroll
         for (int k = 0; k < RY; ++k) {
-            float ext[V + 2 * R];  // ext[m] holds column x0 - R + m of row y0 + k
-#pragma unroll
-            for (int e = 0; e < V; ++e) ext[R + e] = T::elem(q[R][k], e);
+            uint4 up[R], dn[R], zm[R], zp[R];
 #pragma unroll
             for (int d = 1; d <= R; ++d) {
-                float from_left = __shfl_up_sync(kFull, ext[R + V - d], 1);
-                float from_right = __shfl_down_sync(kFull, ext[R + d - 1], 1);
-                ext[R - d] = lane == 0 ? edge[k][d - 1] : from_left;
-                ext[R + V - 1 + d] = lane == 31 ? edge[k][d - 1] : from_right;
+                const int up_row = k - d, dn_row = k + d;
+                up[d - 1] = up_row >= 0 ? q[R][up_row >= 0 ? up_row : 0] : yh[(-up_row - 1) < R ? (-up_row - 1) : 0];
+                dn[d - 1] = dn_row < RY ? q[R][dn_row < RY ? dn_row : 0]
+                                        : yh[R + (dn_row - RY < R ? dn_row - RY : 0)];
+                zm[d - 1] = q[R - d][k];
+                zp[d - 1] = q[R + d][k];
             }
             float out[V];
-            if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions
-#pragma unroll
-                for (int e = 0; e < V; e += 2) {
-                    float2 vert[R], horz[R], depth[R];
-#pragma unroll
-                    for (int d = 1; d <= R; ++d) {
-                        float n2[2], s2[2];
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int up_row = k - d, dn_row = k + d;
-                            n2[h] = up_row >= 0 ? T::elem(q[R][up_row >= 0 ? up_row : 0], e + h)
-                                                : T::elem(yh[(-up_row - 1) < R ? (-up_row - 1) : 0], e + h);
-                            s2[h] = dn_row < RY ? T::elem(q[R][dn_row < RY ? dn_row : 0], e + h)
-                                                : T::elem(yh[R + (dn_row - RY < R ? dn_row - RY : 0)], e + h);
-                        }
-                        vert[d - 1] = wave::add2_rn(make_float2(n2[0], n2[1]), make_float2(s2[0], s2[1]));
-                        horz[d - 1] = wave::add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]),
-                                                    make_float2(ext[R + e + d], ext[R + e + 1 + d]));
-                        depth[d - 1] = wave::add2_rn(make_float2(T::elem(q[R - d][k], e), T::elem(q[R - d][k], e + 1)),
-                                                     make_float2(T::elem(q[R + d][k], e), T::elem(q[R + d][k], e + 1)));
-                    }
-                    const float2 up = START ? make_float2(0.0f, 0.0f)
-                                            : make_float2(T::elem(prev[START ? 0 : k], e),
-                                                          T::elem(prev[START ? 0 : k], e + 1));
-                    const float2 o = update3_2<R, START>(make_float2(ext[R + e], ext[R + e + 1]), up, vert, horz,
-                                                         depth, a.c2);
-                    out[e] = o.x;
-                    out[e + 1] = o.y;
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    float vert[R], horz[R], depth[R];
-#pragma unroll
-                    for (int d = 1; d <= R; ++d) {
-                        const int up_row = k - d, dn_row = k + d;
-                        const float n = up_row >= 0 ? T::elem(q[R][up_row >= 0 ? up_row : 0], e)
-                                                    : T::elem(yh[(-up_row - 1) < R ? (-up_row - 1) : 0], e);
-                        const float s = dn_row < RY ? T::elem(q[R][dn_row < RY ? dn_row : 0], e)
-                                                    : T::elem(yh[R + (dn_row - RY < R ? dn_row - RY : 0)], e);
-                        vert[d - 1] = __fadd_rn(n, s);
-                        horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
-                        depth[d - 1] = __fadd_rn(T::elem(q[R - d][k], e), T::elem(q[R + d][k], e));
-                    }
-                    const float up = START ? 0.0f : T::elem(prev[START ? 0 : k], e);
-                    out[e] = update3<R, START>(ext[R + e], up, vert, horz, depth, a.c2);
-                }
-            }
+            row_update<S, R, START>(q[R][k], up, dn, zm, zp, prev[START ? 0 : k], edge[k], lane, a.c2, out);
             if (col_in && row_in(y0 + k)) {
                 char* dst = nbase + k * pb;
                 if (!CHECK || nvalid == V) {
@@ -278,6 +285,150 @@ __global__ void __launch_bounds__(256, MinBlocks3<R, RY>::value) wave3d_vec_kern
     if (a.pdl && threadIdx.x == 0) griddep_wait();
 }
 
+// Slab form (radius 2-4 pays for it): a block of 8 warps marches a strip of
+// RB = 8*RYW consecutive rows (warp w owns rows w*RYW ..) through the planes of a
+// segment together.  Each warp keeps its rows' plane queue in registers as above,
+// but the rows above and below a row come from a shared-memory slab holding the
+// centre plane of the whole strip plus its R-row halo (loaded by the first and
+// last warp), so a strip reads 2R halo rows per plane instead of every warp
+// reading 2R.  The slab is double-buffered by plane: one barrier per plane.
+constexpr int kSlabWarps = 8;
+
+template <int R, int RYW>
+struct Slab {
+    static constexpr int RB = kSlabWarps * RYW;                   // rows of the strip
+    static constexpr int SR = RB + 2 * R;                         // slab rows (with halo)
+    static constexpr int BYTES = 2 * SR * 32 * sizeof(uint4);     // two planes of slab
+};
+
+template <typename S, int R, int RYW, bool START, bool CHECK>
+__device__ __forceinline__ void strip_impl(const Args3& a, int64_t tx, int64_t tb, int64_t sg, uint4* slab,
+                                           int warp, int lane) {
+    using T = Traits<S>;
+    using SL = Slab<R, RYW>;
+    constexpr int V = T::V;
+    constexpr int64_t ES = sizeof(S);
+    const int64_t pb = a.pitch_bytes, zb = a.plane_bytes;
+    const int64_t x0 = (tx * 32 + lane) * V;
+    const int64_t yb = tb * SL::RB;          // first row of the strip
+    const int64_t y0 = yb + warp * RYW;      // this warp's first row
+    const int64_t za = a.z_begin + sg * a.seg;
+    const int64_t ze = za + a.seg < a.z_end ? za + a.seg : a.z_end;
+    const bool col_in = !CHECK || x0 < a.nx;
+    const int nvalid = !CHECK ? V : (col_in ? static_cast<int>(a.nx - x0 < V ? a.nx - x0 : V) : 0);
+    const bool masked = CHECK && nvalid < V;
+    const char* cur_col = a.u_cur + x0 * ES;
+    auto row_in = [&](int64_t y) { return !CHECK || (y >= 0 && y < a.ny); };
+    auto load_cur = [&](int64_t z, int64_t y) -> uint4 {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (z >= 0 && z < a.nz && col_in && row_in(y)) {
+            v = __ldg(reinterpret_cast<const uint4*>(cur_col + z * zb + y * pb));
+            if (masked) T::mask(v, nvalid);
+        }
+        return v;
+    };
+    uint4 q[2 * R + 1][RYW];  // q[m][k]: row y0 + k of plane z - R + m
+#pragma unroll
+    for (int m = 1; m <= 2 * R; ++m)
+#pragma unroll
+        for (int k = 0; k < RYW; ++k) q[m][k] = load_cur(za - R + (m - 1), y0 + k);
+    const bool edge_lane = lane == 0 || lane == 31;
+    const int64_t edge_col0 = lane == 0 ? x0 - 1 : x0 + V;
+    const int64_t edge_step = lane == 0 ? -1 : 1;
+
+    for (int64_t z = za; z < ze; ++z) {
+#pragma unroll
+        for (int m = 0; m < 2 * R; ++m)
+#pragma unroll
+            for (int k = 0; k < RYW; ++k) q[m][k] = q[m + 1][k];
+#pragma unroll
+        for (int k = 0; k < RYW; ++k) q[2 * R][k] = load_cur(z + R, y0 + k);
+        // slab row j holds strip row j - R of plane z
+        uint4* sl = slab + ((z - za) & 1) * (SL::SR * 32);
+#pragma unroll
+        for (int k = 0; k < RYW; ++k) sl[(R + warp * RYW + k) * 32 + lane] = q[R][k];
+        if (warp == 0) {
+#pragma unroll
+            for (int d = 1; d <= R; ++d) sl[(R - d) * 32 + lane] = load_cur(z, yb - d);
+        } else if (warp == kSlabWarps - 1) {
+#pragma unroll
+            for (int d = 1; d <= R; ++d) sl[(R + SL::RB - 1 + d) * 32 + lane] = load_cur(z, yb + SL::RB - 1 + d);
+        }
+        uint4 prev[START ? 1 : RYW];
+        if (!START) {
+            const char* pbase = a.u_prev + z * zb + y0 * pb + x0 * ES;
+#pragma unroll
+            for (int k = 0; k < RYW; ++k) {
+                prev[k] = make_uint4(0u, 0u, 0u, 0u);
+                if (col_in && row_in(y0 + k)) prev[k] = __ldcs(reinterpret_cast<const uint4*>(pbase + k * pb));
+            }
+        }
+        float edge[RYW][R];
+        const char* ebase = a.u_cur + z * zb + y0 * pb;
+#pragma unroll
+        for (int k = 0; k < RYW; ++k)
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                const int64_t col = edge_col0 + (d - 1) * edge_step;
+                edge[k][d - 1] = 0.0f;
+                if (edge_lane && row_in(y0 + k) && col >= 0 && col < a.nx)
+                    edge[k][d - 1] = T::load1(ebase + k * pb + col * ES);
+            }
+        __syncthreads();  // the strip's plane z is in the slab (the other buffer is still being read by none)
+
+        char* nbase = a.u_next + z * zb + y0 * pb + x0 * ES;
+#pragma unroll
+        for (int k = 0; k < RYW; ++k) {
+            uint4 up[R], dn[R], zm[R], zp[R];
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                const int ru = k - d, rd = k + d;  // rows relative to this warp's first row
+                up[d - 1] = ru >= 0 ? q[R][ru >= 0 ? ru : 0] : sl[(R + warp * RYW + ru) * 32 + lane];
+                dn[d - 1] = rd < RYW ? q[R][rd < RYW ? rd : 0] : sl[(R + warp * RYW + rd) * 32 + lane];
+                zm[d - 1] = q[R - d][k];
+                zp[d - 1] = q[R + d][k];
+            }
+            float out[V];
+            row_update<S, R, START>(q[R][k], up, dn, zm, zp, prev[START ? 0 : k], edge[k], lane, a.c2, out);
+            if (col_in && row_in(y0 + k)) {
+                char* dst = nbase + k * pb;
+                if (!CHECK || nvalid == V) {
+                    __stcs(reinterpret_cast<uint4*>(dst), T::pack(out));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (e < nvalid) T::store1(dst + e * ES, out[e]);
+                }
+            }
+        }
+    }
+    __syncthreads();  // the slab is free for the block's next task
+}
+
+// Tasks are (tile column, strip, segment), x fastest; persistent blocks stride over them.
+template <typename S, int R, int RYW, bool START>
+__global__ void __launch_bounds__(kSlabWarps * 32) wave3d_slab_kernel(Args3 a) {
+    __shared__ uint4 slab[Slab<R, RYW>::BYTES / sizeof(uint4)];
+    if (a.pdl == 1) griddep_wait();
+    if (a.pdl) griddep_launch_dependents();
+    stamp_begin(a.stamp);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int V = Traits<S>::V;
+    constexpr int RB = Slab<R, RYW>::RB;
+    for (int64_t t = blockIdx.x; t < a.tasks; t += gridDim.x) {  // block-uniform
+        const int64_t rest = t / a.tiles_x;
+        const int64_t tx = t - rest * a.tiles_x;
+        const int64_t sg = rest / a.tiles_y;
+        const int64_t tb = rest - sg * a.tiles_y;
+        const int64_t yb = tb * RB;
+        const bool interior = (yb - R >= 0) && (yb + RB + R <= a.ny) && ((tx + 1) * 32 * V <= a.nx);
+        if (interior) strip_impl<S, R, RYW, START, false>(a, tx, tb, sg, slab, warp, lane);
+        else strip_impl<S, R, RYW, START, true>(a, tx, tb, sg, slab, warp, lane);
+    }
+    stamp_end(a.stamp);
+    if (a.pdl && threadIdx.x == 0) griddep_wait();
+}
+
 // One point per thread; any element-aligned layout.
 template <typename S, int R, bool START>
 __global__ void __launch_bounds__(256) wave3d_scalar_kernel(Args3 a) {
@@ -312,22 +463,28 @@ __global__ void __launch_bounds__(256) wave3d_scalar_kernel(Args3 a) {
 
 using KernelFn3 = void (*)(Args3);
 
-// Tile heights: radius 1-2 {1, 2, 4}, radius 3-4 {1, 2, 4} (the register queue
-// holds (2r+1) x RY vectors); variant v (1-based) = (rows[(v-1) % 3], threads[(v-1) / 3]).
+// Warp-column variants 1-6: tile heights {1, 2, 4} (the register queue holds
+// (2r+1) x RY vectors) x {128, 256} threads, variant v = (rows[(v-1) % 3],
+// threads[(v-1) / 3]).  Slab variants 7-8: strips of 8 x {1, 2} rows, 256 threads.
 constexpr int kRows12[3] = {1, 2, 4};
 constexpr int kRows34[3] = {1, 2, 4};
 constexpr int kThreads3[2] = {128, 256};
-constexpr int kVariants3 = 6;
+constexpr int kColumnVariants3 = 6;
+constexpr int kVariants3 = 8;
 
+// rows < 0: the slab kernel with strips of -rows rows
 template <typename S, int R, bool START>
 KernelFn3 pick_vec3(int rows) {
     switch (rows) {
         case 1: return wave3d_vec_kernel<S, R, 1, START>;
         case 2: return wave3d_vec_kernel<S, R, 2, START>;
-        default: return wave3d_vec_kernel<S, R, 4, START>;
+        case 4: return wave3d_vec_kernel<S, R, 4, START>;
+        case -8: return wave3d_slab_kernel<S, R, 1, START>;
+        default: return wave3d_slab_kernel<S, R, 2, START>;
     }
 }
 
+// rows > 0: warp-column kernel with rows-row tiles; rows < 0: slab kernel, strips of -rows rows.
 sy_status launch3_typed(Queue* q, const WaveLaunch3& w, KernelFn3 vec_fn, KernelFn3 scalar_fn, int rows, int threads,
                         int V, size_t esize);
 

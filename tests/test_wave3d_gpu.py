@@ -86,8 +86,8 @@ def test_3d_bit_exact_vs_oracle(q, dtype, r):
     assert np.array_equal(bits(c), bits(oc)) and np.array_equal(bits(p), bits(op))
 
 
-@pytest.mark.parametrize("r", [1, 2, 4])
-@pytest.mark.parametrize("variant", range(0, 7))
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", range(0, 9))
 def test_3d_every_variant(q, r, variant):
     shape = (20, 45, 260)
     u0 = field(shape, "f32", seed=4)
@@ -113,6 +113,17 @@ def test_3d_unaligned_layout_takes_the_scalar_path(q):
     u0 = field(shape, "f32", seed=6)
     p, c = run3d(q, u0, 3, 1, "f32", [(0, 3), (3, 6)], offset=1)  # rows not 16-byte aligned
     op, oc = oracle.wave3d_run_mirror(oracle.F32, u0, 3, 1, C2)
+    assert np.array_equal(bits(c), bits(oc)) and np.array_equal(bits(p), bits(op))
+
+
+@pytest.mark.parametrize("variant", [7, 8])
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_3d_slab_variants_16bit_ragged(q, variant, dtype):
+    # strips of 8 / 16 rows over a grid whose rows are not a multiple of either, 16-bit storage
+    shape = (9, 53, 300)
+    u0 = field(shape, dtype, seed=12)
+    p, c = run3d(q, u0, 4, 2, dtype, [(0, 4), (4, 9)], variant=variant)
+    op, oc = oracle.wave3d_run_mirror(DT[dtype], u0, 4, 2, C2)
     assert np.array_equal(bits(c), bits(oc)) and np.array_equal(bits(p), bits(op))
 
 
@@ -156,7 +167,7 @@ def test_3d_errors(q):
              ((sy.stencil3d_params(8, 8, 8, 5, C2, "f32"), a, b, c, [(0, 8)], 5), "SY_ERR_INVALID_ARGUMENT"),
              ((sy.stencil3d_params(8, 8, 8, 1, C2, "f32", plane=63), a, b, c, [(0, 8)], 1),
               "SY_ERR_INVALID_ARGUMENT"),
-             ((sy.stencil3d_params(8, 8, 8, 1, C2, "f32", variant=7), a, b, c, [(0, 8)], 1),
+             ((sy.stencil3d_params(8, 8, 8, 1, C2, "f32", variant=9), a, b, c, [(0, 8)], 1),
               "SY_ERR_INVALID_ARGUMENT")]
     for args, name in cases:
         with pytest.raises(sy.SyError) as e:
