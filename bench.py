@@ -516,8 +516,10 @@ def measure_learned(q, stream) -> dict:
     """The learned cost model, end to end on this GPU: the library tunes a reduced
     corpus exhaustively (220 shapes), trains its MLP on 80% of the shapes with its own
     kernels, and reports regret on the held-out 20% for the model and for the default
-    configuration; then the model picks the tile variant of the headline workload
-    (8192^2 FP32, radius 1, 4 chunks) and both picks are timed as whole simulations."""
+    configuration, and the held-out shapes' total throughput under each; then the model picks
+    the tile variant of the headline workload (8192^2 FP32, radius 1, 4 chunks) -- its argmin,
+    and the fastest of its top three timed once each on the workload -- and the picks and the
+    default are timed as whole simulations."""
     import numpy as np
     import torch
 
@@ -538,12 +540,28 @@ def measure_learned(q, stream) -> dict:
     infos = [sy.sy_stencil_variant_info(1, sy.SY_F32, v) for v in range(1, nv + 1)]
     feats = np.stack([sy.sy_cost_features(1, sy.SY_F32, 1, NY, NX, r, c, t, CHUNKS) for r, c, t in infos])
     pick = 1 + sy.sy_cost_model_choose(model, feats, 0)
+    ranked = [1 + int(i) for i in np.argsort(sy.sy_cost_model_predict(model, feats)[:, 0])]
     sy.sy_mlp_destroy(model)
     u0 = torch.from_numpy(inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), "f32")).cuda()
     A, B = torch.empty_like(u0), torch.empty_like(u0)
     chunks = sy.sy_split_rows(NY, CHUNKS)
+    # the model's ranking, verified: the top three candidates each timed once on the workload itself
+    # (three simulations instead of an exhaustive sweep over every variant)
+    def one_sim_ms(variant):
+        p = sy.stencil_params(NY, NX, 1, C2, "f32", variant=variant)
+        sy.sy_wave_run(q.handle, p, u0, A, B, STEPS, chunks, HALO)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sy.sy_wave_run(q.handle, p, u0, A, B, STEPS, chunks, HALO)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    top3 = ranked[:3]
+    verified = min(top3, key=one_sim_ms)
     timing = {}
-    for name, variant in (("default", 0), ("learned", pick)):
+    for name, variant in (("default", 0), ("learned", pick), ("learned_top3_verified", verified)):
         p = sy.stencil_params(NY, NX, 1, C2, "f32", variant=variant)
         run = lambda: sy.sy_wave_run(q.handle, p, u0, A, B, STEPS, chunks, HALO)
         run()
@@ -551,10 +569,12 @@ def measure_learned(q, stream) -> dict:
         upd = STEPS * NY * NX
         timing[name] = {"variant": variant, "updates_per_s": upd / (ms * 1e-3),
                         "j_per_update": None if not joules else joules / (reps * upd)}
+    timing["learned_top3_verified"]["candidates"] = top3
     rows, cols, thr = infos[pick - 1]
     return {"corpus_rows": int(corpus["X"].shape[0]), "corpus_shapes": len(shapes), "measure_s": t_measure,
             "train_s": t_train, "held_out_shapes": int(test_ids.size), "regret_model": res["model"],
             "regret_default": res["default"], "regret_random_expected": res["random_expected_mean"],
+            "held_out_totals": res["held_out_totals"],
             "headline_pick": {"variant": pick, "tile_rows": rows, "threads": thr}, "headline": timing}
 
 

@@ -173,6 +173,25 @@ def evaluate(q: Queue, model: int, shapes, corpus, test_ids) -> dict:
         return None
 
     res = {"model": regret(shapes, sub, model_pick), "default": regret(shapes, sub, default_pick)}
+    # the same picks as whole-corpus throughput: work of every held-out shape (grid points of one
+    # step, or SAXPY elements) over the summed measured time of the chosen configurations
+    totals = {}
+    for kind, name in ((1, "stencil"), (0, "saxpy")):
+        work = t_model = t_default = t_best = 0.0
+        for sid in np.unique(sub["shape"]):
+            s = shapes[sid]
+            if s["kind"] != kind:
+                continue
+            rows = np.nonzero(sub["shape"] == sid)[0]
+            t = np.exp(sub["logt"][rows]) * 1e-3
+            work += s["ny"] * s["nx"] if kind == 1 else s["n"]
+            t_model += t[model_pick(sid, rows)]
+            t_default += t[default_pick(sid, rows)]
+            t_best += t.min()
+        if work:
+            totals[name] = {"per_s_model": work / t_model, "per_s_default": work / t_default,
+                            "per_s_best": work / t_best, "model_over_default": t_default / t_model}
+    res["held_out_totals"] = totals
     # expected regret of a random candidate
     rr = []
     for sid in np.unique(sub["shape"]):

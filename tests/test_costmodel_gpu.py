@@ -67,6 +67,9 @@ def test_learned_model_beats_the_default_on_held_out_shapes(queue):
     assert res["model"]["mean"] <= 0.10, res
     assert res["model"]["mean"] < res["default"]["mean"], res
     assert res["model"]["mean"] < 0.1 * res["random_expected_mean"], res
+    # and as whole-corpus throughput: the model's picks beat the default's over the held-out stencils
+    tot = res["held_out_totals"]["stencil"]
+    assert tot["per_s_model"] > tot["per_s_default"] and tot["per_s_model"] <= tot["per_s_best"] * (1 + 1e-12), tot
 
 
 def test_exhaustive_tuner_every_kind(queue):
