@@ -638,7 +638,8 @@ sy_status sy_wave3d_energy(sy_queue_t q, const sy_stencil3d_params* p, const voi
 /* Tile variants 1-6: rows of a warp's tile (1, 2, 4) x threads per block (128,
  * 256); variants 7-8: a block of 8 warps marching a strip of 8 or 16 rows with
  * the strip's centre plane in shared memory (tile_rows reports the strip,
- * threads 256); variant 0 is the default. */
+ * threads 256); variants 9-10: the same strips with every plane copied into a
+ * shared-memory ring by TMA ahead of use; variant 0 is the default. */
 sy_status sy_stencil3d_variant_count(int radius, int dtype, int* count);
 sy_status sy_stencil3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads);
 

@@ -178,7 +178,7 @@ struct WaveLaunch3 {
 };
 sy_status launch_wave3d(Queue* q, const WaveLaunch3& w);
 bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads);
-constexpr int kWave3dVariants = 8;
+constexpr int kWave3dVariants = 10;
 sy_status stencil3d_param_checks(const sy_stencil3d_params* p);
 sy_status stencil3d_common(Queue* q, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
                            void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,

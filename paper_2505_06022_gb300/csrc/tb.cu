@@ -25,6 +25,7 @@
 #include <cstdlib>
 #include <mutex>
 
+#include "tma.cuh"
 #include "wave_kernel.cuh"
 
 namespace sy {
@@ -37,7 +38,6 @@ constexpr int BY = 32;
 // blocks fit an SM, whose computing blocks hide the others' copies -- measured
 // faster (T = 4: 9.8e11 -> 1.13e12 updates/s FP32, 1.20e12 -> 1.34e12 BF16).
 constexpr int kStages = 1;
-constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
 struct TBArgs {
     char* out_prev;  // u^{n+T-1}
@@ -66,45 +66,10 @@ struct Geo {
     static_assert(BX > 0 && BX % VEC == 0, "tile width");
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Bounded wait: true when the phase completed, false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
+using tma::kWaitCycles;
+using tma::mbar_expect_tx;
+using tma::mbar_init;
+using tma::mbar_wait_bounded;
 
 template <typename S>
 __device__ __forceinline__ float ld_s(const S* buf, int idx);
@@ -239,11 +204,11 @@ __global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant
         const int x = static_cast<int>(tx * G::BX) - G::PAD;
         const int y = static_cast<int>(a.row_begin + ty * BY) - T * R;
         unsigned char* base = smem + 2 * s * G::BUF;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic writes to this stage
+        tma::fence_proxy_async();  // earlier generic writes to this stage
         mbar_expect_tx(&bars[s], G::TX);
         if (!skip) {
-            tma_load_2d(base, &map_cur, x, y, &bars[s]);
-            tma_load_2d(base + G::BUF, &map_prev, x, y, &bars[s]);
+            tma::load_2d(base, &map_cur, x, y, &bars[s]);
+            tma::load_2d(base + G::BUF, &map_prev, x, y, &bars[s]);
         }
     };
 
@@ -318,24 +283,10 @@ __global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant
 }
 
 // ---- host ----------------------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static std::once_flag once;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult qr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
-                cudaSuccess &&
-            qr == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
 template <typename S, int R, int T>
 sy_status make_map(const void* base, int64_t ny, int64_t nx, int64_t pitch_bytes, CUtensorMap* map) {
     using G = Geo<S, R, T>;
-    auto enc = encode_fn();
+    auto enc = tma::encoder();
     if (!enc) return fail(SY_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
     const CUtensorMapDataType dt = sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     const cuuint64_t dims[2] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny)};

@@ -4,23 +4,25 @@
 //   E^{n+1/2} = sum (u_new - u_old)^2 - c2 * sum u_new * (L u_old),
 // with the fixed reduction shape of the 2D one (kEnergyBlocks x 256 threads, fixed
 // trees), so repeated calls give identical bits.
-#include "wave3d_kernel.cuh"
+#include "wave3d_tma.cuh"
 
 namespace sy {
 namespace wave3 {
 
 namespace {
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+}  // namespace
 
-// Planes per segment: minimises the busiest warp's plane loads, rounds x (seg + R)
+// Planes per segment: minimises the busiest worker's plane loads, rounds x (seg + R)
 // (a segment's first 2R planes are re-read, mostly from L2, where the previous
-// segment's warp has just read them); ties go to the longer segment.
-int64_t choose_seg(int64_t tiles_xy, int64_t planes, int64_t nwarps, int R) {
+// segment's worker has just read them); ties go to the longer segment.  A worker
+// is a warp (warp-column kernel) or a block (slab and TMA kernels).
+int64_t choose_seg(int64_t tiles_xy, int64_t planes, int64_t workers, int R) {
     int64_t best = planes, best_cost = -1;
     const int64_t hi = planes < 64 ? planes : 64;
     for (int64_t seg = 1; seg <= hi; ++seg) {
         const int64_t segs = (planes + seg - 1) / seg;
-        const int64_t rounds = (tiles_xy * segs + nwarps - 1) / nwarps;
+        const int64_t rounds = (tiles_xy * segs + workers - 1) / workers;
         const int64_t cost = rounds * (seg + R);
         if (best_cost < 0 || cost < best_cost || (cost == best_cost && seg > best)) {
             best = seg;
@@ -29,7 +31,6 @@ int64_t choose_seg(int64_t tiles_xy, int64_t planes, int64_t nwarps, int R) {
     }
     return best;
 }
-}  // namespace
 
 sy_status launch3_typed(Queue* q, const WaveLaunch3& w, KernelFn3 vec_fn, KernelFn3 scalar_fn, int rows, int threads,
                         int V, size_t esize) {
@@ -213,18 +214,24 @@ namespace {
 // variants measured slower (a block waits at every plane's barrier for its halo loads).
 constexpr int kDefaultVariant3[4] = {1, 2, 1, 1};
 
-// Resolved variant -> (rows, threads, slab).
-bool variant3(int radius, int variant, int* rows, int* threads, bool* slab) {
+enum class Form3 { column, slab, tma };
+
+// Resolved variant -> (rows, threads, form).
+bool variant3(int radius, int variant, int* rows, int* threads, Form3* form) {
     const int v = variant == 0 ? kDefaultVariant3[radius - 1] : variant;
     if (v <= wave3::kColumnVariants3) {
         const int* table = radius <= 2 ? wave3::kRows12 : wave3::kRows34;
         *rows = table[(v - 1) % 3];
         *threads = wave3::kThreads3[(v - 1) / 3];
-        *slab = false;
-    } else {
+        *form = Form3::column;
+    } else if (v <= wave3::kColumnVariants3 + 2) {
         *rows = wave3::kSlabWarps * (v - wave3::kColumnVariants3);
         *threads = wave3::kSlabWarps * 32;
-        *slab = true;
+        *form = Form3::slab;
+    } else {
+        *rows = 2 * wave3::kTmaWarps * (v - wave3::kColumnVariants3 - 2);  // strips of 16 or 32 rows
+        *threads = wave3::kTmaWarps * 32;
+        *form = Form3::tma;
     }
     return true;
 }
@@ -234,8 +241,8 @@ bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int
     if (radius < 1 || radius > 4 || dtype_size(dtype) == 0 || variant < 0 || variant > wave3::kVariants3)
         return false;
     int rows = 0, thr = 0;
-    bool slab = false;
-    variant3(radius, variant, &rows, &thr, &slab);
+    Form3 form = Form3::column;
+    variant3(radius, variant, &rows, &thr, &form);
     if (tile_rows) *tile_rows = rows;
     if (threads) *threads = thr;
     return true;
@@ -243,11 +250,29 @@ bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int
 
 sy_status launch_wave3d(Queue* q, const WaveLaunch3& w) {
     int rows = 0, threads = 0;
-    bool slab = false;
+    Form3 form = Form3::column;
     if (!wave3d_variant_info(w.radius, w.dtype, w.variant, nullptr, nullptr))
         return fail(SY_ERR_INVALID_ARGUMENT, "bad 3D stencil variant %d", w.variant);
-    variant3(w.radius, w.variant, &rows, &threads, &slab);
-    if (slab) rows = -rows;
+    variant3(w.radius, w.variant, &rows, &threads, &form);
+    if (form == Form3::tma) {
+        const size_t es = dtype_size(w.dtype);
+        const bool tma_ok = wave3::aligned(w.u_cur, 16) && wave3::aligned(w.u_next, 16) &&
+                            (w.start || wave3::aligned(w.u_prev, 16)) &&
+                            (w.pitch * es) % 16 == 0 && (w.plane * es) % 16 == 0;
+        const int64_t planes = w.z_end - w.z_begin;
+        if (planes <= 0 || w.ny == 0 || w.nx == 0) return SY_OK;
+        if (tma_ok) {
+            switch (w.dtype) {
+                case SY_F32: return wave3::launch3_tma_f32(q, w, rows);
+                case SY_BF16: return wave3::launch3_tma_bf16(q, w, rows);
+                case SY_F16: return wave3::launch3_tma_f16(q, w, rows);
+            }
+        }
+        rows = 1;  // unaligned layouts: the one-point-per-thread kernel of the column family
+        threads = 128;
+        form = Form3::column;
+    }
+    if (form == Form3::slab) rows = -rows;
     switch (w.dtype) {
         case SY_F32: return wave3::launch3_f32(q, w, rows, threads);
         case SY_BF16: return wave3::launch3_bf16(q, w, rows, threads);

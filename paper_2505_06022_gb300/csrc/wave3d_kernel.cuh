@@ -470,7 +470,7 @@ constexpr int kRows12[3] = {1, 2, 4};
 constexpr int kRows34[3] = {1, 2, 4};
 constexpr int kThreads3[2] = {128, 256};
 constexpr int kColumnVariants3 = 6;
-constexpr int kVariants3 = 8;
+constexpr int kVariants3 = 10;  // + TMA variants 9-10 (wave3d_tma.cuh): strips of 8 x {2, 4} rows
 
 // rows < 0: the slab kernel with strips of -rows rows
 template <typename S, int R, bool START>

@@ -89,7 +89,7 @@ def test_exhaustive_tuner_every_kind(queue):
     p3 = sy.stencil3d_params(n3, n3, n3, 1, 0.125, "f32")
     recs3, best3 = sy.sy_tune_exhaustive(queue.handle, sy.SY_TUNE_STENCIL3D, p3, 0, a3, b3, c3, (1, 4), reps=2)
     assert len(recs3) == 2 * sy.sy_stencil3d_variant_count(1, "f32")
-    assert {(r[0], r[4]) for r in recs3} == {(v, k) for v in range(1, 9) for k in (1, 4)}
+    assert {(r[0], r[4]) for r in recs3} == {(v, k) for v in range(1, 11) for k in (1, 4)}
     for rs, bi in ((recs, best), (recs2, best2), (recs3, best3)):
         assert all(r[5] > 0 for r in rs)
         assert rs[bi][5] == min(r[5] for r in rs)

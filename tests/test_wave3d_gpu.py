@@ -87,7 +87,7 @@ def test_3d_bit_exact_vs_oracle(q, dtype, r):
 
 
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
-@pytest.mark.parametrize("variant", range(0, 9))
+@pytest.mark.parametrize("variant", range(0, 11))
 def test_3d_every_variant(q, r, variant):
     shape = (20, 45, 260)
     u0 = field(shape, "f32", seed=4)
@@ -116,7 +116,7 @@ def test_3d_unaligned_layout_takes_the_scalar_path(q):
     assert np.array_equal(bits(c), bits(oc)) and np.array_equal(bits(p), bits(op))
 
 
-@pytest.mark.parametrize("variant", [7, 8])
+@pytest.mark.parametrize("variant", [7, 8, 9, 10])
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 def test_3d_slab_variants_16bit_ragged(q, variant, dtype):
     # strips of 8 / 16 rows over a grid whose rows are not a multiple of either, 16-bit storage
@@ -167,7 +167,7 @@ def test_3d_errors(q):
              ((sy.stencil3d_params(8, 8, 8, 5, C2, "f32"), a, b, c, [(0, 8)], 5), "SY_ERR_INVALID_ARGUMENT"),
              ((sy.stencil3d_params(8, 8, 8, 1, C2, "f32", plane=63), a, b, c, [(0, 8)], 1),
               "SY_ERR_INVALID_ARGUMENT"),
-             ((sy.stencil3d_params(8, 8, 8, 1, C2, "f32", variant=9), a, b, c, [(0, 8)], 1),
+             ((sy.stencil3d_params(8, 8, 8, 1, C2, "f32", variant=11), a, b, c, [(0, 8)], 1),
               "SY_ERR_INVALID_ARGUMENT")]
     for args, name in cases:
         with pytest.raises(sy.SyError) as e:
@@ -257,3 +257,41 @@ def test_3d_energy_conserved_full_size(q):
     pv, cv, _ = sy.sy_wave3d_run(q, p, u0, a, b, steps, chunks, 1)
     E1 = sy.sy_wave3d_energy(q, p, cv, pv)[0]
     assert E0 > 0 and abs(E1 - E0) / E0 < 1e-3
+
+
+def test_3d_tma_unaligned_layout_falls_back(q):
+    shape = (6, 11, 19)
+    u0 = field(shape, "f32", seed=6)
+    p, c = run3d(q, u0, 3, 1, "f32", [(0, 3), (3, 6)], variant=9, offset=1)
+    op, oc = oracle.wave3d_run_mirror(oracle.F32, u0, 3, 1, C2)
+    assert np.array_equal(bits(c), bits(oc)) and np.array_equal(bits(p), bits(op))
+
+
+def test_3d_tma_bounded_wait_times_out_and_context_survives(q):
+    """Host-injected fault: each block announces its first plane copy but never issues it; every
+    wait is bounded, so the blocks give up, the flag comes back as SY_ERR_TIMEOUT and the context
+    keeps working."""
+    import os
+
+    torch = torch_cuda()
+    shape = (12, 20, 140)
+    u0 = field(shape, "f32", seed=13)
+    d0 = torch.from_numpy(u0).cuda().reshape(-1)
+    prev = torch.empty_like(d0)
+    p = sy.stencil3d_params(*shape, 1, C2, "f32", variant=9)
+    old = os.environ.get("SY_FAULT")
+    os.environ["SY_FAULT"] = "w3_timeout"
+    try:
+        sy.sy_stencil3d_start(q, p, d0, prev, [(0, 12)], 1)
+        with pytest.raises(sy.SyError) as e:
+            sy.sy_queue_sync(q)
+        assert e.value.name == "SY_ERR_TIMEOUT"
+    finally:
+        if old is None:
+            del os.environ["SY_FAULT"]
+        else:
+            os.environ["SY_FAULT"] = old
+    sy.sy_queue_sync(q)  # reported once and cleared
+    pv, cv = run3d(q, u0, 3, 1, "f32", [(0, 6), (6, 12)], variant=9)
+    op, oc = oracle.wave3d_run_mirror(oracle.F32, u0, 3, 1, C2)
+    assert np.array_equal(bits(cv), bits(oc)) and np.array_equal(bits(pv), bits(op))
