@@ -207,18 +207,18 @@ sy_status launch_wave3d_energy(Queue* q, const sy_stencil3d_params* p, const voi
 }
 
 namespace {
-// The default variant per radius: the fastest of a sweep at 512^3 (FP32) on GB300
-// (radius 1: 5.1e11 updates/s, radius 2: 4.1e11, radius 4: 2.1e11).  Warp columns
-// of one row for radius 1 and 3-4 (the register queue, (2r+1) x rows vectors per
-// lane, sets how many warps stay resident), of two rows for radius 2; the slab
-// variants measured slower (a block waits at every plane's barrier for its halo loads).
-constexpr int kDefaultVariant3[4] = {1, 2, 1, 1};
+// The default variant per storage class and radius: the fastest of a sweep at 512^3 on
+// GB300 (FP32 radius 1 / 2 / 4: 5.1e11 / 4.1e11 / 2.1e11 updates/s; BF16 radius 1 / 2:
+// 8.9e11 / 6.0e11).  Warp columns of one row except FP32 radius 2 (two rows): the
+// register queue, (2r+1) x rows vectors per lane, sets how many warps stay resident;
+// the slab and TMA variants measured slower (see their kernels).
+constexpr int kDefaultVariant3[2][4] = {{1, 2, 1, 1}, {1, 4, 1, 1}};
 
 enum class Form3 { column, slab, tma };
 
 // Resolved variant -> (rows, threads, form).
-bool variant3(int radius, int variant, int* rows, int* threads, Form3* form) {
-    const int v = variant == 0 ? kDefaultVariant3[radius - 1] : variant;
+bool variant3(int radius, int dtype, int variant, int* rows, int* threads, Form3* form) {
+    const int v = variant == 0 ? kDefaultVariant3[dtype == SY_F32 ? 0 : 1][radius - 1] : variant;
     if (v <= wave3::kColumnVariants3) {
         const int* table = radius <= 2 ? wave3::kRows12 : wave3::kRows34;
         *rows = table[(v - 1) % 3];
@@ -242,7 +242,7 @@ bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int
         return false;
     int rows = 0, thr = 0;
     Form3 form = Form3::column;
-    variant3(radius, variant, &rows, &thr, &form);
+    variant3(radius, dtype, variant, &rows, &thr, &form);
     if (tile_rows) *tile_rows = rows;
     if (threads) *threads = thr;
     return true;
@@ -253,7 +253,7 @@ sy_status launch_wave3d(Queue* q, const WaveLaunch3& w) {
     Form3 form = Form3::column;
     if (!wave3d_variant_info(w.radius, w.dtype, w.variant, nullptr, nullptr))
         return fail(SY_ERR_INVALID_ARGUMENT, "bad 3D stencil variant %d", w.variant);
-    variant3(w.radius, w.variant, &rows, &threads, &form);
+    variant3(w.radius, w.dtype, w.variant, &rows, &threads, &form);
     if (form == Form3::tma) {
         const size_t es = dtype_size(w.dtype);
         const bool tma_ok = wave3::aligned(w.u_cur, 16) && wave3::aligned(w.u_next, 16) &&
