@@ -142,6 +142,7 @@ sy_status sy_meter_end(sy_queue_t q, double* joules, double* seconds);
  * issued inside a window that has since been closed. */
 sy_status sy_kernel_energy(sy_queue_t q, sy_event ev, double* joules);
 
+
 /* ------------------------------------------------------------------------- */
 /* SAXPY (paper §2 Listing 1; §3 Listing 2 with one_to_one range mappers)     */
 /* ------------------------------------------------------------------------- */
@@ -220,6 +221,20 @@ typedef struct sy_stencil_params {
 sy_status sy_stencil_step(sy_queue_t q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
                           void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
                           sy_event* chunk_events);
+
+/* Per-chunk statistics of one stepped chunk list (the events sy_stencil_step
+ * returned for `chunks`, in order): device time, algorithmic bytes (read u^n and
+ * u^{n-1}, write u^{n+1}: 3 x sizeof(storage) per point), grid-point updates and
+ * energy (sy_kernel_energy; -1 when the launch lies in no closed metering
+ * window or NVML is unavailable).  SY_ERR_NOT_READY until the launches complete. */
+typedef struct sy_chunk_stats {
+    double ms;
+    double bytes;
+    double joules;
+    double updates;
+} sy_chunk_stats;
+sy_status sy_chunk_stats_read(sy_queue_t q, const sy_stencil_params* p, const sy_chunk* chunks,
+                              const sy_event* events, int n, sy_chunk_stats* out);
 
 /* Taylor start for zero initial velocity: u_m1 = u0 + (c2 / 2) * L u0, evaluated
  * as fl(u0 + fl((c2/2) * L u0)) with L as above (bit-identical to a step with c2

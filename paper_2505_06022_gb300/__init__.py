@@ -178,6 +178,7 @@ _SIGS = {
     "sy_wave3d_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
     "sy_stencil3d_variant_count": [C.c_int, C.c_int, _p],
     "sy_wave3d_energy": [_p, _p, _p, _p, _p, _p, _p],
+    "sy_chunk_stats_read": [_p, _p, _p, _p, C.c_int, _p],
     "sy_stencil3d_step_planes": [_p, _p, _p, _p, _p, _i64, _i64, C.c_int, C.c_int, _p],
     "sy_tune_stencil3d": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p],
     "sy_tune_exhaustive": [_p, C.c_int, _p, _i64, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p, _p],
@@ -888,3 +889,16 @@ def sy_mlp_backward(m, d_X, d_T, B: int, want_loss: bool = True):
     loss = C.c_float(0.0)
     _call("sy_mlp_backward", m, _ptr(d_X), _ptr(d_T), int(B), C.byref(loss) if want_loss else None)
     return loss.value if want_loss else None
+
+
+class ChunkStats(C.Structure):
+    _fields_ = [("ms", C.c_double), ("bytes", C.c_double), ("joules", C.c_double), ("updates", C.c_double)]
+
+
+def sy_chunk_stats_read(q: int, p: StencilParams, chunks, events) -> list[dict]:
+    """Per chunk: device ms, algorithmic bytes, joules (-1 outside a closed metering window), updates."""
+    arr, k = _chunks(chunks)
+    evs = (C.c_uint64 * max(1, k))(*events)
+    out = (ChunkStats * max(1, k))()
+    _call("sy_chunk_stats_read", q, C.byref(p), arr, evs, k, out)
+    return [{"ms": s.ms, "bytes": s.bytes, "joules": s.joules, "updates": s.updates} for s in out[:k]]

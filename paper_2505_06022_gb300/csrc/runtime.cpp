@@ -546,6 +546,30 @@ sy_status sy_kernel_energy(sy_queue_t qh, sy_event ev, double* joules) {
     return SY_OK;
 }
 
+sy_status sy_chunk_stats_read(sy_queue_t qh, const sy_stencil_params* p, const sy_chunk* chunks,
+                              const sy_event* events, int n, sy_chunk_stats* out) {
+    Queue* q;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil_param_checks(p));
+    if (n < 0) return fail(SY_ERR_INVALID_ARGUMENT, "n = %d < 0", n);
+    if (n == 0) return SY_OK;
+    if (!chunks || !events || !out) return fail(SY_ERR_NULL_POINTER, "chunks, events or out is NULL");
+    std::vector<double> ms(static_cast<size_t>(n));
+    SY_TRY(sy_events_elapsed(qh, events, n, ms.data()));
+    const double es = static_cast<double>(dtype_size(p->dtype));
+    for (int c = 0; c < n; ++c) {
+        const double updates = static_cast<double>(chunks[c].end - chunks[c].begin) * static_cast<double>(p->nx);
+        out[c].ms = ms[c];
+        out[c].updates = updates;
+        out[c].bytes = 3.0 * es * updates;  // algorithmic: read u^n and u^{n-1}, write u^{n+1}
+        double j = -1.0;
+        if (sy_kernel_energy(qh, events[c], &j) != SY_OK) j = -1.0;  // no closed metering window
+        out[c].joules = j;
+    }
+    clear_error();
+    return SY_OK;
+}
+
 // ---- range mappers ---------------------------------------------------------------------
 sy_status sy_split_rows(int64_t n, int k, sy_chunk* out) {
     if (!out) return fail(SY_ERR_NULL_POINTER, "out is NULL");

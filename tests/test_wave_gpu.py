@@ -385,6 +385,11 @@ def test_stream_events_and_energy_window(q):
         kj = [sy.sy_kernel_energy(q, e) for e in evs[:8]]
         assert all(j > 0 for j in kj)
         assert sum(sy.sy_kernel_energy(q, e) for e in evs) <= joules * 1.01
+    # per-chunk statistics of the first stepped chunk list: time, bytes, updates (and energy)
+    stats = sy.sy_chunk_stats_read(q, p, chunks, evs[:4])
+    assert [st["updates"] for st in stats] == [(b - a) * nx for a, b in chunks]
+    assert all(st["bytes"] == 12 * st["updates"] and st["ms"] == m for st, m in zip(stats, ms[:4]))
+    assert all((st["joules"] > 0) if metered else (st["joules"] == -1.0) for st in stats)
 
 
 def test_energy_counter_ticks(q):
