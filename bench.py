@@ -54,6 +54,21 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def device_info(index: int) -> dict:
+    """GPU name, driver version and the host's core count, for the record."""
+    import torch
+
+    info = {"name": torch.cuda.get_device_name(index), "host_cores": os.cpu_count()}
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=driver_version,memory.total",
+                              "--format=csv,noheader"], capture_output=True, text=True, timeout=20).stdout.strip()
+        driver, mem = [v.strip() for v in out.split(",")[:2]]
+        info.update({"driver": driver, "memory_total": mem})
+    except Exception:
+        pass
+    return info
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -861,6 +876,7 @@ def run_gpu(args) -> None:
             "gpu_launches": launches,
             "forms": forms,
             "clocks": clk,
+            "device": device_info(local),
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
                                                                           "sample", "single_thread_value")},
         }
