@@ -675,6 +675,18 @@ sy_status sy_tune_exhaustive(sy_queue_t q, int kind, const void* params, int64_t
                              void* out_buf, const int* chunk_counts, int n_counts, int reps, sy_tune_record* out,
                              int max_out, int* n_out, int* best);
 
+/* Checkpoint / resume of a 2D simulation: the two time levels the recurrence
+ * needs and the step count.  Save synchronises the queue and writes u_prev, u_cur
+ * (rows without pitch padding) and `step` to `path`; load checks that the file
+ * holds the grid, storage, radius and c2 of p (else SY_ERR_INVALID_ARGUMENT),
+ * fills u_prev, u_cur (any pitch) and *step, and synchronises.  Stepping on from
+ * a loaded checkpoint gives the bits of an uninterrupted run.  SY_ERR_IO for
+ * unreadable, foreign or truncated files. */
+sy_status sy_checkpoint_save(sy_queue_t q, const char* path, const sy_stencil_params* p, const void* u_prev,
+                             const void* u_cur, int64_t step);
+sy_status sy_checkpoint_load(sy_queue_t q, const char* path, const sy_stencil_params* p, void* u_prev, void* u_cur,
+                             int64_t* step);
+
 /* Allocation-free form of sy_wave_energy.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at the
  * moment they need the energy -- code issuing work while a stream is being

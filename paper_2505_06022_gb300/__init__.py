@@ -179,6 +179,8 @@ _SIGS = {
     "sy_stencil3d_variant_count": [C.c_int, C.c_int, _p],
     "sy_wave3d_energy": [_p, _p, _p, _p, _p, _p, _p],
     "sy_chunk_stats_read": [_p, _p, _p, _p, C.c_int, _p],
+    "sy_checkpoint_save": [_p, C.c_char_p, _p, _p, _p, _i64],
+    "sy_checkpoint_load": [_p, C.c_char_p, _p, _p, _p, _p],
     "sy_stencil3d_step_planes": [_p, _p, _p, _p, _p, _i64, _i64, C.c_int, C.c_int, _p],
     "sy_tune_stencil3d": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p],
     "sy_tune_exhaustive": [_p, C.c_int, _p, _i64, _p, _p, _p, _p, C.c_int, C.c_int, _p, C.c_int, _p, _p],
@@ -902,3 +904,13 @@ def sy_chunk_stats_read(q: int, p: StencilParams, chunks, events) -> list[dict]:
     out = (ChunkStats * max(1, k))()
     _call("sy_chunk_stats_read", q, C.byref(p), arr, evs, k, out)
     return [{"ms": s.ms, "bytes": s.bytes, "joules": s.joules, "updates": s.updates} for s in out[:k]]
+
+
+def sy_checkpoint_save(q: int, path: str, p: StencilParams, u_prev, u_cur, step: int) -> None:
+    _call("sy_checkpoint_save", q, path.encode(), C.byref(p), _ptr(u_prev), _ptr(u_cur), int(step))
+
+
+def sy_checkpoint_load(q: int, path: str, p: StencilParams, u_prev, u_cur) -> int:
+    step = C.c_int64(0)
+    _call("sy_checkpoint_load", q, path.encode(), C.byref(p), _ptr(u_prev), _ptr(u_cur), C.byref(step))
+    return step.value
