@@ -225,7 +225,7 @@ extern "C" {
 
 sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n_grids, int dtype, int tile_rows,
                                 sy_batch_plan_t* out) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!out) return fail(SY_ERR_NULL_POINTER, "out is NULL");
     *out = nullptr;

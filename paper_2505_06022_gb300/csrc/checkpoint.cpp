@@ -44,7 +44,7 @@ extern "C" {
 sy_status sy_checkpoint_save(sy_queue_t qh, const char* path, const sy_stencil_params* p, const void* u_prev,
                              const void* u_cur, int64_t step) {
     clear_error();
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     if (!path || !u_prev || !u_cur) return fail(SY_ERR_NULL_POINTER, "path or field pointer is NULL");
@@ -73,7 +73,7 @@ sy_status sy_checkpoint_save(sy_queue_t qh, const char* path, const sy_stencil_p
 sy_status sy_checkpoint_load(sy_queue_t qh, const char* path, const sy_stencil_params* p, void* u_prev, void* u_cur,
                              int64_t* step) {
     clear_error();
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     if (!path || !u_prev || !u_cur || !step) return fail(SY_ERR_NULL_POINTER, "NULL argument");

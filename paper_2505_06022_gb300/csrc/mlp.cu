@@ -398,7 +398,7 @@ using namespace sy;
 extern "C" {
 
 sy_status sy_mlp_create(sy_queue_t qh, int in_features, int hidden, int out_features, uint64_t seed, sy_mlp_t* out) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!out) return fail(SY_ERR_NULL_POINTER, "out is NULL");
     *out = nullptr;

@@ -181,7 +181,7 @@ using namespace sy;
 extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, const void* u0, void* u_a, void* u_b,
                                  int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius,
                                  sy_event* events, const void** prev_out, const void** cur_out) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     const size_t bytes = static_cast<size_t>(p->ny) * static_cast<size_t>(p->pitch) * dtype_size(p->dtype);
@@ -198,7 +198,7 @@ extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, cons
 extern "C" sy_status sy_wave3d_run(sy_queue_t qh, const sy_stencil3d_params* p, const void* u0, void* u_a,
                                    void* u_b, int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius,
                                    sy_event* events, const void** prev_out, const void** cur_out) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil3d_param_checks(p));
     const size_t bytes = static_cast<size_t>(p->nz) * static_cast<size_t>(p->plane) * dtype_size(p->dtype);

@@ -412,7 +412,7 @@ sy_status sy_queue_destroy(sy_queue_t qh) {
 }
 
 sy_status sy_queue_sync(sy_queue_t qh) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(use_device(q));
     SY_CUDA(cudaStreamSynchronize(q->stream));
@@ -426,7 +426,7 @@ sy_status sy_queue_sync(sy_queue_t qh) {
 }
 
 sy_status sy_queue_stream(sy_queue_t qh, void** stream) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!stream) return fail(SY_ERR_NULL_POINTER, "stream out is NULL");
     *stream = q->stream;
@@ -434,7 +434,7 @@ sy_status sy_queue_stream(sy_queue_t qh, void** stream) {
 }
 
 sy_status sy_queue_launch_count(sy_queue_t qh, uint64_t* launches) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!launches) return fail(SY_ERR_NULL_POINTER, "launches out is NULL");
     *launches = q->launches;
@@ -443,7 +443,7 @@ sy_status sy_queue_launch_count(sy_queue_t qh, uint64_t* launches) {
 
 // ---- events and energy ------------------------------------------------------------
 sy_status sy_event_elapsed(sy_queue_t qh, sy_event ev, double* ms) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!ms) return fail(SY_ERR_NULL_POINTER, "ms out is NULL");
     EventRecord* r;
@@ -455,7 +455,7 @@ sy_status sy_event_elapsed(sy_queue_t qh, sy_event ev, double* ms) {
 }
 
 sy_status sy_events_elapsed(sy_queue_t qh, const sy_event* evs, int n, double* ms) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (n < 0) return fail(SY_ERR_INVALID_ARGUMENT, "n = %d < 0", n);
     if (n == 0) return SY_OK;
@@ -470,7 +470,7 @@ sy_status sy_events_elapsed(sy_queue_t qh, const sy_event* evs, int n, double* m
 }
 
 sy_status sy_energy_read(sy_queue_t qh, uint64_t* mj) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!mj) return fail(SY_ERR_NULL_POINTER, "millijoules out is NULL");
     if (!q->nvml_device || !nvml::energy_mj(q->nvml_device, mj))
@@ -479,7 +479,7 @@ sy_status sy_energy_read(sy_queue_t qh, uint64_t* mj) {
 }
 
 sy_status sy_device_energy(sy_queue_t qh, double* joules) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!joules) return fail(SY_ERR_NULL_POINTER, "joules out is NULL");
     uint64_t now = 0;
@@ -490,7 +490,7 @@ sy_status sy_device_energy(sy_queue_t qh, double* joules) {
 }
 
 sy_status sy_meter_begin(sy_queue_t qh) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(use_device(q));
     if (q->open_window >= 0) return fail(SY_ERR_INVALID_ARGUMENT, "a metering window is already open");
@@ -507,7 +507,7 @@ sy_status sy_meter_begin(sy_queue_t qh) {
 }
 
 sy_status sy_meter_end(sy_queue_t qh, double* joules, double* seconds) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(use_device(q));
     if (q->open_window < 0) return fail(SY_ERR_INVALID_ARGUMENT, "no metering window is open");
@@ -529,7 +529,7 @@ sy_status sy_meter_end(sy_queue_t qh, double* joules, double* seconds) {
 }
 
 sy_status sy_kernel_energy(sy_queue_t qh, sy_event ev, double* joules) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!joules) return fail(SY_ERR_NULL_POINTER, "joules out is NULL");
     EventRecord* r;
@@ -548,7 +548,7 @@ sy_status sy_kernel_energy(sy_queue_t qh, sy_event ev, double* joules) {
 
 sy_status sy_chunk_stats_read(sy_queue_t qh, const sy_stencil_params* p, const sy_chunk* chunks,
                               const sy_event* events, int n, sy_chunk_stats* out) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     if (n < 0) return fail(SY_ERR_INVALID_ARGUMENT, "n = %d < 0", n);
@@ -615,7 +615,7 @@ static sy_status saxpy_checks(int64_t n, const float* x, const float* y, float* 
 }
 
 sy_status sy_saxpy(sy_queue_t qh, int64_t n, float alpha, const float* x, const float* y, float* z, sy_event* ev) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(saxpy_checks(n, x, y, z));
     SY_TRY(use_device(q));
@@ -627,7 +627,7 @@ sy_status sy_saxpy(sy_queue_t qh, int64_t n, float alpha, const float* x, const 
 
 sy_status sy_saxpy_split(sy_queue_t qh, int64_t n, float alpha, const float* x, const float* y, float* z,
                          const sy_chunk* chunks, int n_chunks, sy_event* events) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(saxpy_checks(n, x, y, z));
     if (n == 0 && n_chunks == 0) return SY_OK;
@@ -647,14 +647,14 @@ sy_status sy_saxpy_split(sy_queue_t qh, int64_t n, float alpha, const float* x, 
 sy_status sy_stencil_step(sy_queue_t qh, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
                           void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
                           sy_event* chunk_events) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     return stencil_common(q, p, u_prev, u_cur, u_next, chunks, n_chunks, halo_radius, chunk_events, false);
 }
 
 sy_status sy_stencil_start(sy_queue_t qh, const sy_stencil_params* p, const void* u0, void* u_m1,
                            const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* chunk_events) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     return stencil_common(q, p, nullptr, u0, u_m1, chunks, n_chunks, halo_radius, chunk_events, true);
 }
@@ -662,7 +662,7 @@ sy_status sy_stencil_start(sy_queue_t qh, const sy_stencil_params* p, const void
 sy_status sy_stencil_multistep(sy_queue_t qh, const sy_stencil_params* p, int T, const void* u_prev,
                                const void* u_cur, void* out_prev, void* out_cur, const sy_chunk* chunks, int n_chunks,
                                int halo_radius, sy_event* chunk_events) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     if (T != 2 && T != 4) return fail(SY_ERR_INVALID_ARGUMENT, "T = %d not in {2, 4}", T);
@@ -732,7 +732,7 @@ sy_status sy_stencil_variant_info(int radius, int dtype, int variant, int* tile_
 
 sy_status sy_wave_energy(sy_queue_t qh, const sy_stencil_params* p, const void* u_new, const void* u_old,
                          double* energy, double* kinetic, double* potential) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     if (!energy) return fail(SY_ERR_NULL_POINTER, "energy out is NULL");

@@ -165,7 +165,7 @@ extern "C" {
 sy_status sy_stencil_step_split(sy_queue_t qh, const sy_stencil_params* p, void* const* local_prev,
                                 void* const* local_cur, void* const* local_next, const sy_chunk* chunks,
                                 int n_chunks, int halo_radius, sy_event* chunk_events) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     return split_common(q, p, local_prev, local_cur, local_next, chunks, n_chunks, halo_radius, chunk_events,
                         false);
@@ -174,7 +174,7 @@ sy_status sy_stencil_step_split(sy_queue_t qh, const sy_stencil_params* p, void*
 sy_status sy_stencil_start_split(sy_queue_t qh, const sy_stencil_params* p, void* const* local_u0,
                                  void* const* local_um1, const sy_chunk* chunks, int n_chunks, int halo_radius,
                                  sy_event* chunk_events) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     return split_common(q, p, nullptr, local_u0, local_um1, chunks, n_chunks, halo_radius, chunk_events, true);
 }
@@ -182,7 +182,7 @@ sy_status sy_stencil_start_split(sy_queue_t qh, const sy_stencil_params* p, void
 sy_status sy_stencil_step_rows(sy_queue_t qh, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
                                void* u_next, int64_t row_begin, int64_t row_end, int halo_radius, int start,
                                sy_event* ev) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     if (row_begin < 0 || row_end < row_begin || row_end > p->ny)

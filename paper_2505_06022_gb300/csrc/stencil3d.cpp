@@ -69,7 +69,7 @@ sy_status sy_stencil3d_step(sy_queue_t qh, const sy_stencil3d_params* p, const v
                             void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
                             sy_event* chunk_events) {
     clear_error();
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     return stencil3d_common(q, p, u_prev, u_cur, u_next, chunks, n_chunks, halo_radius, chunk_events, false);
 }
@@ -77,7 +77,7 @@ sy_status sy_stencil3d_step(sy_queue_t qh, const sy_stencil3d_params* p, const v
 sy_status sy_stencil3d_start(sy_queue_t qh, const sy_stencil3d_params* p, const void* u0, void* u_m1,
                              const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* chunk_events) {
     clear_error();
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     return stencil3d_common(q, p, nullptr, u0, u_m1, chunks, n_chunks, halo_radius, chunk_events, true);
 }
@@ -86,7 +86,7 @@ sy_status sy_stencil3d_step_planes(sy_queue_t qh, const sy_stencil3d_params* p, 
                                    const void* u_cur, void* u_next, int64_t plane_begin, int64_t plane_end,
                                    int halo_radius, int start, sy_event* ev) {
     clear_error();
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil3d_param_checks(p));
     if (plane_begin < 0 || plane_end < plane_begin || plane_end > p->nz)
@@ -126,7 +126,7 @@ sy_status sy_stencil3d_step_planes(sy_queue_t qh, const sy_stencil3d_params* p, 
 sy_status sy_wave3d_energy(sy_queue_t qh, const sy_stencil3d_params* p, const void* u_new, const void* u_old,
                            double* energy, double* kinetic, double* potential) {
     clear_error();
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil3d_param_checks(p));
     if (!energy) return fail(SY_ERR_NULL_POINTER, "energy out is NULL");

@@ -68,7 +68,7 @@ sy_status sy_saxpy_variant_info(int variant, int* threads, int* waves) {
 
 sy_status sy_saxpy_config(sy_queue_t qh, int64_t n, float alpha, const float* x, const float* y, float* z,
                           int variant, const sy_chunk* chunks, int n_chunks, sy_event* events) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (n < 0) return fail(SY_ERR_INVALID_ARGUMENT, "n = %lld < 0", (long long)n);
     if (!saxpy_variant_info(variant, nullptr, nullptr))
@@ -93,7 +93,7 @@ sy_status sy_saxpy_config(sy_queue_t qh, int64_t n, float alpha, const float* x,
 sy_status sy_tune_stencil(sy_queue_t qh, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
                           void* u_next, const int* chunk_counts, int n_counts, int reps, sy_tune_record* out,
                           int max_out, int* n_out) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     if (!out || !n_out) return fail(SY_ERR_NULL_POINTER, "out or n_out is NULL");
@@ -132,7 +132,7 @@ sy_status sy_tune_stencil(sy_queue_t qh, const sy_stencil_params* p, const void*
 
 sy_status sy_tune_saxpy(sy_queue_t qh, int64_t n, const float* x, const float* y, float* z, const int* chunk_counts,
                         int n_counts, int reps, sy_tune_record* out, int max_out, int* n_out) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!out || !n_out) return fail(SY_ERR_NULL_POINTER, "out or n_out is NULL");
     if (reps < 1 || n < 1) return fail(SY_ERR_INVALID_ARGUMENT, "reps < 1 or n < 1");
@@ -172,7 +172,7 @@ sy_status sy_tune_saxpy(sy_queue_t qh, int64_t n, const float* x, const float* y
 sy_status sy_tune_stencil3d(sy_queue_t qh, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
                             void* u_next, const int* chunk_counts, int n_counts, int reps, sy_tune_record* out,
                             int max_out, int* n_out) {
-    Queue* q;
+    Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil3d_param_checks(p));
     if (!out || !n_out) return fail(SY_ERR_NULL_POINTER, "out or n_out is NULL");
