@@ -297,7 +297,7 @@ sy_status sy::stencil_common(Queue* q, const sy_stencil_params* p, const void* u
         return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
     SY_TRY(use_device(q));
     for (int c = 0; c < n_chunks; ++c) {
-        EventRecord* rec;
+        EventRecord* rec = nullptr;
         SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
         WaveLaunch w;
         w.ny = p->ny;
@@ -446,7 +446,7 @@ sy_status sy_event_elapsed(sy_queue_t qh, sy_event ev, double* ms) {
     Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!ms) return fail(SY_ERR_NULL_POINTER, "ms out is NULL");
-    EventRecord* r;
+    EventRecord* r = nullptr;
     SY_TRY(find_event(q, ev, &r));
     SY_TRY(use_device(q));
     std::vector<unsigned long long> st;
@@ -532,7 +532,7 @@ sy_status sy_kernel_energy(sy_queue_t qh, sy_event ev, double* joules) {
     Queue* q = nullptr;
     SY_TRY(check_queue(qh, &q));
     if (!joules) return fail(SY_ERR_NULL_POINTER, "joules out is NULL");
-    EventRecord* r;
+    EventRecord* r = nullptr;
     SY_TRY(find_event(q, ev, &r));
     if (r->window < 0 || r->window >= static_cast<int64_t>(q->windows.size()) || !q->windows[r->window].closed)
         return fail(SY_ERR_NOT_READY, "event %llu was not issued inside a closed metering window",
@@ -619,7 +619,7 @@ sy_status sy_saxpy(sy_queue_t qh, int64_t n, float alpha, const float* x, const 
     SY_TRY(check_queue(qh, &q));
     SY_TRY(saxpy_checks(n, x, y, z));
     SY_TRY(use_device(q));
-    EventRecord* rec;
+    EventRecord* rec = nullptr;
     SY_TRY(begin_event(q, ev, &rec));
     if (n > 0) SY_TRY(launch_saxpy(q, n, alpha, x, y, z));
     return end_event(q, rec);
@@ -634,7 +634,7 @@ sy_status sy_saxpy_split(sy_queue_t qh, int64_t n, float alpha, const float* x, 
     SY_TRY(validate_chunks(n, chunks, n_chunks));
     SY_TRY(use_device(q));
     for (int c = 0; c < n_chunks; ++c) {
-        EventRecord* rec;
+        EventRecord* rec = nullptr;
         SY_TRY(begin_event(q, events ? &events[c] : nullptr, &rec));
         int64_t a = chunks[c].begin, len = chunks[c].end - a;
         SY_TRY(launch_saxpy(q, len, alpha, x + a, y + a, z + a));  // one_to_one: [a, b) -> [a, b)
@@ -691,7 +691,7 @@ sy_status sy_stencil_multistep(sy_queue_t qh, const sy_stencil_params* p, int T,
     SY_TRY(use_device(q));
     const int fault = fault_enabled("tb_timeout") ? 1 : 0;
     for (int c = 0; c < n_chunks; ++c) {
-        EventRecord* rec;
+        EventRecord* rec = nullptr;
         SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
         TBLaunch w;
         w.ny = p->ny;

@@ -135,7 +135,7 @@ sy_status split_common(Queue* q, const sy_stencil_params* p, void* const* local_
     }
     // 2. each chunk steps its own rows of a local grid of halo_lo + len + halo_hi rows
     for (int c = 0; c < n_chunks; ++c) {
-        EventRecord* rec;
+        EventRecord* rec = nullptr;
         SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
         WaveLaunch w;
         w.ny = lay[c].rows;
@@ -196,7 +196,7 @@ sy_status sy_stencil_step_rows(sy_queue_t qh, const sy_stencil_params* p, const 
     if (!start && u_next != u_prev && ranges_overlap(u_next, bytes, u_prev, bytes))
         return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
     SY_TRY(use_device(q));
-    EventRecord* rec;
+    EventRecord* rec = nullptr;
     SY_TRY(begin_event(q, ev, &rec));
     WaveLaunch w;
     w.ny = p->ny;

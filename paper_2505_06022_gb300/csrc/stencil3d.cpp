@@ -34,7 +34,7 @@ sy_status stencil3d_common(Queue* q, const sy_stencil3d_params* p, const void* u
         return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
     SY_TRY(use_device(q));
     for (int c = 0; c < n_chunks; ++c) {
-        EventRecord* rec;
+        EventRecord* rec = nullptr;
         SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
         WaveLaunch3 w;
         w.nz = p->nz;
@@ -100,7 +100,7 @@ sy_status sy_stencil3d_step_planes(sy_queue_t qh, const sy_stencil3d_params* p, 
     if (!start && u_next != u_prev && ranges_overlap(u_next, bytes, u_prev, bytes))
         return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
     SY_TRY(use_device(q));
-    EventRecord* rec;
+    EventRecord* rec = nullptr;
     SY_TRY(begin_event(q, ev, &rec));
     WaveLaunch3 w;
     w.nz = p->nz;

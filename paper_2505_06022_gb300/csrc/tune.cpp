@@ -81,7 +81,7 @@ sy_status sy_saxpy_config(sy_queue_t qh, int64_t n, float alpha, const float* x,
     SY_TRY(validate_chunks(n, chunks, n_chunks));
     SY_TRY(use_device(q));
     for (int c = 0; c < n_chunks; ++c) {
-        EventRecord* rec;
+        EventRecord* rec = nullptr;
         SY_TRY(begin_event(q, events ? &events[c] : nullptr, &rec));
         const int64_t a = chunks[c].begin, len = chunks[c].end - a;
         SY_TRY(launch_saxpy_variant(q, len, alpha, x + a, y + a, z + a, variant));
