@@ -811,6 +811,10 @@ def run_gpu(args) -> None:
             torch.cuda.synchronize()
             times_pipe.append(e0.elapsed_time(e1))
         ms_e2e = statistics.median(times_pipe)
+        if dist:  # the job takes as long as its slowest replica
+            t = torch.tensor([ms_e2e, ms_seq], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e, ms_seq = float(t[0].item()), float(t[1].item())
         assert torch.equal(h_out, want_out), "pipelined end-to-end result differs from the sequential one"
         e2e = {"value": world * k_e2e * updates_per_step / (ms_e2e * 1e-3), "unit": "updates/s",
                "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
@@ -831,7 +835,8 @@ def run_gpu(args) -> None:
         accuracy = dict(error_vs_f64(final), tolerance_max_rel=1e-5)
 
     forms = None
-    if rank == 0 and args.forms and args.dtype == "f32" and RADIUS == 1:
+    if rank == 0 and world == 1 and args.forms and args.dtype == "f32" and RADIUS == 1:
+        # the other forms are single-GPU comparisons; with replicas they would hold every GPU idle
         forms = {"plain_f32": {"updates_per_s": value, "gb_per_s": value * BYTES_PER_UPDATE / 1e9,
                                "j_per_update": None if not energy else energy["j_per_update"]}}
         for dt in ("bf16", "f16"):
