@@ -208,11 +208,13 @@ sy_status launch_wave3d_energy(Queue* q, const sy_stencil3d_params* p, const voi
 
 namespace {
 // The default variant per storage class and radius: the fastest of a sweep at 512^3 on
-// GB300 (FP32 radius 1 / 2 / 4: 5.1e11 / 4.1e11 / 2.1e11 updates/s; BF16 radius 1 / 2:
-// 8.9e11 / 6.0e11).  Warp columns of one row except FP32 radius 2 (two rows): the
-// register queue, (2r+1) x rows vectors per lane, sets how many warps stay resident;
-// the slab and TMA variants measured slower (see their kernels).
-constexpr int kDefaultVariant3[2][4] = {{1, 2, 1, 1}, {1, 4, 1, 1}};
+// GB300 (FP32 radius 1 / 2 / 4: 5.3e11 / 4.2e11 / 2.2e11 updates/s; BF16 radius 1 / 2 / 4:
+// 9.4e11 / 6.0e11 / 2.5e11).  Warp columns of one row except FP32 radius 2 (two rows):
+// the register queue, (2r+1) x rows vectors per lane, sets how many warps stay resident;
+// 16-bit radius 2 and 4 run them in blocks of 256 threads.  The slab and TMA variants
+// measured slower (see their kernels), except 16-bit radius 4, where TMA strips of 32
+// rows tie with the default (2.53e11).
+constexpr int kDefaultVariant3[2][4] = {{1, 2, 1, 1}, {1, 4, 1, 4}};
 
 enum class Form3 { column, slab, tma };
 
@@ -236,6 +238,8 @@ bool variant3(int radius, int dtype, int variant, int* rows, int* threads, Form3
     return true;
 }
 }  // namespace
+
+static_assert(kWave3dVariants == wave3::kVariants3, "the ABI's 3D variant count is the kernel table's");
 
 bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads) {
     if (radius < 1 || radius > 4 || dtype_size(dtype) == 0 || variant < 0 || variant > wave3::kVariants3)
