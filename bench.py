@@ -140,6 +140,16 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def kernel_label(dtype: str) -> str:
+    """The dominant kernel of the timed step: the default tile of the 2D step for this storage
+    type (16-bit radius-1 4-row tiles run the 96-register form)."""
+    import paper_2505_06022_gb300 as sy
+
+    rows, _, threads = sy.sy_stencil_variant_info(RADIUS, sy.DTYPE_CODES[dtype], 0)
+    name = "wave_vec_kernel_r96" if dtype != "f32" and RADIUS == 1 and rows == 4 else "wave_vec_kernel"
+    return f"{name}<{dtype},{RADIUS},{rows},false> x {threads} threads, one 2048x8192 chunk per launch"
+
+
 def ncu_traffic() -> float | None:
     """Per-launch DRAM bytes of the wave kernel from the committed ncu summary, if
     it was captured from the current kernel source."""
@@ -694,8 +704,7 @@ def run_gpu(args) -> None:
                 "traffic": ncu_traffic() if (args.dtype == "f32" and RADIUS == 1) else None,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "wave_vec_kernel<{},{},{},false> x {} threads, one 2048x8192 chunk per launch".format(
-                    args.dtype, RADIUS, *sy.sy_stencil_variant_info(RADIUS, sy.DTYPE_CODES[args.dtype], 0)[::2]),
+                "kernel": kernel_label(args.dtype),
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "frac_of_nominal_8000": achieved / 8000.0,
                 "stamp_avg_chunk_ms": statistics.mean(stamp_ms),

@@ -281,25 +281,48 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
                 prev[k] = __ldcs(reinterpret_cast<const uint4*>(prev_base + k * pb));
         }
     }
-    // warp edges: lane 0 fetches the vector left of the warp, lane 31 the one right of it
-    uint4 edge[RY];
-    const int64_t xe = lane == 0 ? x0 - V : x0 + V;
-    const bool edge_lane = (lane == 0 && xe >= 0) || (lane == 31 && xe < a.nx);
-    const int edge_valid = lane == 0 ? V : static_cast<int>(a.nx - xe < V ? a.nx - xe : V);
-    const char* edge_base = a.u_cur + y0 * pb + xe * ES;
+    // warp edges: lane 0 fetches the columns left of the warp, lane 31 those right of
+    // it: the whole neighbouring vector per row, or, for 16-bit storage at radius 1, the
+    // one column as a scalar (one value per row instead of a vector that every lane
+    // holds registers for; the 8-point vectors' unpacked arithmetic needs them more).
+    // Measured at 8192^2 with 4-row tiles: BF16 +1 %, FP16 +5 %; at radius 3-4 the R
+    // scalar loads per row cost more than they save (10-26 % slower with 8-row tiles).
+    constexpr bool kScalarEdge = sizeof(S) == 2 && R == 1;
+    uint4 edge[kScalarEdge ? 1 : RY];
+    float edge1[kScalarEdge ? RY : 1][R];  // edge1[k][d-1]: column x0 - d (lane 0) or x0 + V - 1 + d (lane 31)
+    if constexpr (kScalarEdge) {
+        const bool edge_lane = lane == 0 || lane == 31;
+        const int64_t col0 = lane == 0 ? x0 - 1 : x0 + V;
+        const int64_t step = lane == 0 ? -1 : 1;
+        const char* erow = a.u_cur + y0 * pb;
 #pragma unroll
-    for (int k = 0; k < RY; ++k) {
-        edge[k] = make_uint4(0u, 0u, 0u, 0u);
-        if (edge_lane && (!CHECK || y0 + k < a.row_end))
-            edge[k] = __ldg(reinterpret_cast<const uint4*>(edge_base + k * pb));
+        for (int k = 0; k < RY; ++k)
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                const int64_t col = col0 + (d - 1) * step;
+                edge1[k][d - 1] = 0.0f;
+                if (edge_lane && (!CHECK || y0 + k < a.row_end) && col >= 0 && col < a.nx)
+                    edge1[k][d - 1] = T::load1(erow + k * pb + col * ES);
+            }
+    } else {
+        const int64_t xe = lane == 0 ? x0 - V : x0 + V;
+        const bool edge_lane = (lane == 0 && xe >= 0) || (lane == 31 && xe < a.nx);
+        const int edge_valid = lane == 0 ? V : static_cast<int>(a.nx - xe < V ? a.nx - xe : V);
+        const char* edge_base = a.u_cur + y0 * pb + xe * ES;
+#pragma unroll
+        for (int k = 0; k < RY; ++k) {
+            edge[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (edge_lane && (!CHECK || y0 + k < a.row_end))
+                edge[k] = __ldg(reinterpret_cast<const uint4*>(edge_base + k * pb));
+        }
+        if (lane == 31 && edge_valid < V) {
+#pragma unroll
+            for (int k = 0; k < RY; ++k) T::mask(edge[k], edge_valid);
+        }
     }
     if (CHECK && nvalid < V) {  // only the vector straddling nx (or past it) needs masking
 #pragma unroll
         for (int k = 0; k < RY + 2 * R; ++k) T::mask(cur[k], nvalid);
-    }
-    if (lane == 31 && edge_valid < V) {
-#pragma unroll
-        for (int k = 0; k < RY; ++k) T::mask(edge[k], edge_valid);
     }
 
     // ---- arithmetic and stores, row by row ----
@@ -314,8 +337,13 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
         for (int d = 1; d <= R; ++d) {
             float from_left = __shfl_up_sync(kFull, ext[R + V - d], 1);
             float from_right = __shfl_down_sync(kFull, ext[R + d - 1], 1);
-            ext[R - d] = lane == 0 ? T::elem(edge[k], V - d) : from_left;
-            ext[R + V - 1 + d] = lane == 31 ? T::elem(edge[k], d - 1) : from_right;
+            if constexpr (kScalarEdge) {
+                ext[R - d] = lane == 0 ? edge1[k][d - 1] : from_left;
+                ext[R + V - 1 + d] = lane == 31 ? edge1[k][d - 1] : from_right;
+            } else {
+                ext[R - d] = lane == 0 ? T::elem(edge[k], V - d) : from_left;
+                ext[R + V - 1 + d] = lane == 31 ? T::elem(edge[k], d - 1) : from_right;
+            }
         }
         float out[V];
         if constexpr (sizeof(S) == 2) {  // 16-bit storage: twice the arithmetic per byte; pair the additions
@@ -375,7 +403,7 @@ __device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty,
 }
 
 template <typename S, int R, int RY, bool START>
-__global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
+__device__ __forceinline__ void wave_vec_body(const Args& a) {
     if (a.pdl == 1) griddep_wait();
     if (a.pdl) griddep_launch_dependents();
     stamp_begin(a.stamp);
@@ -398,6 +426,19 @@ __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
     }
     stamp_end(a.stamp);
     if (a.pdl && threadIdx.x == 0) griddep_wait();
+}
+
+template <typename S, int R, int RY, bool START>
+__global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
+    wave_vec_body<S, R, RY, START>(a);
+}
+
+// The same kernel held to 96 registers (5 blocks of 128 threads an SM instead of 4, for
+// a 20-byte spill): 16-bit storage, radius 1, 4-row tiles, the default there.  Measured
+// at 8192^2: BF16 6.38 -> 6.55 TB/s, FP16 6.38 -> 6.50 TB/s.
+template <typename S, int R, int RY, bool START>
+__global__ void __maxnreg__(96) wave_vec_kernel_r96(Args a) {
+    wave_vec_body<S, R, RY, START>(a);
 }
 
 // One point per thread; any element-aligned layout.
@@ -444,7 +485,9 @@ template <typename S, int R, bool START>
 KernelFn pick_vec(int tile_rows) {
     switch (tile_rows) {
         case 2: return wave_vec_kernel<S, R, 2, START>;
-        case 4: return wave_vec_kernel<S, R, 4, START>;
+        case 4:
+            if constexpr (sizeof(S) == 2 && R == 1) return wave_vec_kernel_r96<S, R, 4, START>;
+            else return wave_vec_kernel<S, R, 4, START>;
         case 8: return wave_vec_kernel<S, R, 8, START>;
         default: return wave_vec_kernel<S, R, 16, START>;
     }

@@ -198,6 +198,32 @@ def test_3d_full_size_sampled_light_cone(q):
         assert np.float32(got).view(np.uint32) == want.view(np.uint32), pt
 
 
+@pytest.mark.parametrize("dtype,r,steps", [("bf16", 1, 100), ("f32", 2, 30)])
+def test_3d_full_size_other_forms_sampled(q, dtype, r, steps):
+    """512^3 in 4 chunks of planes through sy_wave3d_run with the default variant -- the
+    benchmark's BF16 radius-1 and FP32 radius-2 forms (radius 2 over 30 of its 100 steps, so
+    that the light cones stay small; the launches are the same): sampled points equal the
+    oracle's precision mirror on the box of their light cone, bit for bit."""
+    torch = torch_cuda()
+    n = 512
+    u0 = inputs.to_storage(inputs.gaussian_pulse_3d(n, n, n, 16.0), dtype)
+    d0 = torch.from_numpy(u0 if dtype == "f32" else u0.view(np.int16)).cuda().reshape(-1)
+    a, b = torch.empty_like(d0), torch.empty_like(d0)
+    p = sy.stencil3d_params(n, n, n, r, C2, dtype)
+    _, cv, _ = sy.sy_wave3d_run(q, p, d0, a, b, steps, sy.sy_split_rows(n, 4), r)
+    torch.cuda.synchronize()
+    cur = {d0.data_ptr(): d0, a.data_ptr(): a, b.data_ptr(): b}[cv].reshape(n, n, n).cpu().numpy()
+    if dtype != "f32":
+        cur = cur.view(np.uint16)
+    h = (steps + 1) * r + 1
+    for pt in [(256, 256, 256), (0, 0, 0), (511, 200, 5), (128, 383, 511), (300, 256, 160)]:
+        lo = [max(0, pt[d] - h) for d in range(3)]
+        hi = [min(n, pt[d] + h + 1) for d in range(3)]
+        sub0 = np.ascontiguousarray(u0[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]])
+        _, sub = oracle.wave3d_run_mirror(DT[dtype], sub0, steps, r, C2)
+        assert bits(cur)[pt] == bits(sub)[pt[0] - lo[0], pt[1] - lo[1], pt[2] - lo[2]], pt
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_3d_256_sampled_light_cone(q, dtype):
     """256^3 (fields larger than L2), radius 1, 20 steps, 4 chunks of planes through sy_wave3d_run;

@@ -274,6 +274,30 @@ def test_config1_full_size_sampled(q):
     assert worst <= 1e-5
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_full_size_sampled_through_wave_run(q, dtype):
+    """8192^2, radius 1, 200 steps in 4 chunks with FP32, BF16 or FP16 storage, through
+    sy_wave_run -- the CUDA graph of chained, overlapped chunk launches the benchmark times:
+    sampled points equal the oracle's precision mirror on the box of their light cone, bit
+    for bit."""
+    torch = torch_cuda()
+    ny = nx = 8192
+    steps, r = 200, 1
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 64.0), dtype)
+    d0 = to_device(u0)
+    ua, ub = torch.empty_like(d0), torch.empty_like(d0)
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype)
+    _, cv, _ = sy.sy_wave_run(q, p, d0, ua, ub, steps, sy.sy_split_rows(ny, 4), r)
+    torch.cuda.synchronize()
+    st = np.float32 if dtype == "f32" else np.uint16
+    gc = to_host({d0.data_ptr(): d0, ua.data_ptr(): ua, ub.data_ptr(): ub}[cv], None, st)
+    assert np.any(bits(gc) != 0)
+    for pt in FULL_SAMPLES:
+        y0, y1, x0, x1 = light_cone_box(pt, (ny, nx), steps, r)
+        _, m = oracle.wave_run_mirror(DT[dtype], np.ascontiguousarray(u0[y0:y1, x0:x1]), steps, r, 0.25)
+        assert bits(gc)[pt] == bits(m)[pt[0] - y0, pt[1] - x0], pt
+
+
 @pytest.mark.parametrize("mx,my", [(1, 1), (16, 32), (1000, 3000)])
 def test_config1_mode_closed_form_full_size(q, mx, my):
     # single sin(kx x) sin(ky y) mode on the full grid: u^n = cos(n Omega) u^0 everywhere; the
