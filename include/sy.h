@@ -251,8 +251,12 @@ sy_status sy_stencil_start(sy_queue_t q, const sy_stencil_params* p, const void*
  * (device) are work fields that receive the results: on return *prev_out and
  * *cur_out (nullable) name the buffers (u0, u_a or u_b) holding u^{steps-1} and
  * u^{steps}.  u0, u_a, u_b must not overlap.  events (nullable) receives
- * (steps + 1) * n_chunks ids -- the start's chunks, then each step's -- valid until
- * the next sy_wave_run on this queue (at most 16384 per run; pass NULL beyond). */
+ * (steps + 1) * n_chunks ids -- the start's chunks, then each step's, in chunk
+ * order -- valid until the next sy_wave_run on this queue (at most 16384 per run;
+ * pass NULL beyond).  The chunks of a step are independent, so the run orders
+ * them for cache reuse: odd steps launch the chunks last to first and sweep each
+ * chunk's rows bottom to top, so that a step starts on the rows the previous step
+ * touched last (results are identical to any other order). */
 sy_status sy_wave_run(sy_queue_t q, const sy_stencil_params* p, const void* u0, void* u_a, void* u_b, int64_t steps,
                       const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* events, const void** prev_out,
                       const void** cur_out);
@@ -641,7 +645,9 @@ sy_status sy_stencil3d_start(sy_queue_t q, const sy_stencil3d_params* p, const v
 sy_status sy_stencil3d_step_planes(sy_queue_t q, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
                                    void* u_next, int64_t plane_begin, int64_t plane_end, int halo_radius, int start,
                                    sy_event* ev);
-/* Start + `steps` steps as one cached CUDA graph, as sy_wave_run. */
+/* Start + `steps` steps as one cached CUDA graph, as sy_wave_run (odd steps
+ * launch the chunks of planes last to first; each chunk's tiles in their usual
+ * order). */
 sy_status sy_wave3d_run(sy_queue_t q, const sy_stencil3d_params* p, const void* u0, void* u_a, void* u_b,
                         int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* events,
                         const void** prev_out, const void** cur_out);

@@ -4,6 +4,15 @@
 // forms) issue; capturing them removes the host's per-launch cost and the gaps
 // between stream launches, and the per-chunk timestamps keep working inside the
 // graph (their slots are zeroed by the graph's first node on every replay).
+//
+// The chunks of one step are independent (each writes only its own rows and reads
+// the previous two levels), so their launch order is free; the run alternates it
+// (start and even steps first to last, odd steps last to first), and a reversed 2D
+// step also sweeps each chunk's tiles bottom to top.  A step then starts on the rows
+// the previous step touched last, while they are still in L2 (8192^2: FP32 +4 %,
+// BF16 +8 %; 3D chunks of planes gain nothing, so only their order alternates).
+// Results are unchanged; event ids are returned in chunk order.
+#include <algorithm>
 #include <cstring>
 
 #include "sy_internal.h"
@@ -123,44 +132,51 @@ std::vector<unsigned char> run_key(const RunArgs<P>& a) {
 }
 
 sy_status step2(Queue* q, const sy_stencil_params* p, const void* up, const void* uc, void* un, const sy_chunk* ch,
-                int n, int halo, sy_event* ev, bool start) {
-    return stencil_common(q, p, up, uc, un, ch, n, halo, ev, start);
+                int n, int halo, sy_event* ev, bool start, bool reverse) {
+    return stencil_common(q, p, up, uc, un, ch, n, halo, ev, start, reverse);
 }
 sy_status step3(Queue* q, const sy_stencil3d_params* p, const void* up, const void* uc, void* un, const sy_chunk* ch,
-                int n, int halo, sy_event* ev, bool start) {
-    return stencil3d_common(q, p, up, uc, un, ch, n, halo, ev, start);
+                int n, int halo, sy_event* ev, bool start, bool reverse) {
+    return stencil3d_common(q, p, up, uc, un, ch, n, halo, ev, start, reverse);
 }
 
 // Start into u_a, step 1 in place over it, step 2 into u_b (u0 is never written),
-// then in place, alternating u_a / u_b.
+// then in place, alternating u_a / u_b; step s launches its chunks in reverse
+// order when s is odd (the start counts as step 0).
 template <class P, sy_status (*STEP)(Queue*, const P*, const void*, const void*, void*, const sy_chunk*, int, int,
-                                     sy_event*, bool)>
+                                     sy_event*, bool, bool)>
 sy_status issue_run(Queue* q, const void* ctx, const void** prev, const void** cur) {
     const RunArgs<P>& a = *static_cast<const RunArgs<P>*>(ctx);
     std::vector<sy_event> ev(a.events ? a.n_chunks : 0);
     sy_event* evp = a.events ? ev.data() : nullptr;
-    SY_TRY(STEP(q, a.p, nullptr, a.u0, a.ua, a.chunks, a.n_chunks, a.halo, evp, true));
+    SY_TRY(STEP(q, a.p, nullptr, a.u0, a.ua, a.chunks, a.n_chunks, a.halo, evp, true, false));
     const void* pv = a.ua;  // u^{-1}
     const void* cv = a.u0;  // u^0
     if (a.steps >= 1) {
-        SY_TRY(STEP(q, a.p, a.ua, a.u0, a.ua, a.chunks, a.n_chunks, a.halo, evp, false));
+        SY_TRY(STEP(q, a.p, a.ua, a.u0, a.ua, a.chunks, a.n_chunks, a.halo, evp, false, true));
         pv = a.u0;
         cv = a.ua;
     }
     if (a.steps >= 2) {
-        SY_TRY(STEP(q, a.p, a.u0, a.ua, a.ub, a.chunks, a.n_chunks, a.halo, evp, false));
+        SY_TRY(STEP(q, a.p, a.u0, a.ua, a.ub, a.chunks, a.n_chunks, a.halo, evp, false, false));
         pv = a.ua;
         cv = a.ub;
     }
-    for (int64_t s = 2; s < a.steps; ++s) {
+    for (int64_t s = 2; s < a.steps; ++s) {  // this is step s + 1
         void* nv = const_cast<void*>(pv);
-        SY_TRY(STEP(q, a.p, pv, cv, nv, a.chunks, a.n_chunks, a.halo, evp, false));
+        SY_TRY(STEP(q, a.p, pv, cv, nv, a.chunks, a.n_chunks, a.halo, evp, false, (s + 1) % 2 == 1));
         pv = cv;
         cv = nv;
     }
     *prev = pv;
     *cur = cv;
     return SY_OK;
+}
+
+// graph_run returns the event ids in launch order; put each odd step's back in chunk order.
+void chunk_order(sy_event* events, int64_t steps, int n_chunks) {
+    if (!events) return;
+    for (int64_t s = 1; s <= steps; s += 2) std::reverse(events + s * n_chunks, events + (s + 1) * n_chunks);
 }
 
 sy_status run_checks(int64_t steps, const void* u0, const void* ua, const void* ub, size_t bytes, bool empty) {
@@ -191,8 +207,10 @@ extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, cons
         return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
     RunArgs<sy_stencil_params> a{p, u0, u_a, u_b, steps, chunks, n_chunks, halo_radius, events != nullptr};
     const uint64_t timed = static_cast<uint64_t>(steps + 1) * static_cast<uint64_t>(n_chunks);
-    return graph_run(q, q->run, run_key(a), timed, events != nullptr, issue_run<sy_stencil_params, step2>, &a,
-                     events, prev_out, cur_out);
+    SY_TRY(graph_run(q, q->run, run_key(a), timed, events != nullptr, issue_run<sy_stencil_params, step2>, &a,
+                     events, prev_out, cur_out));
+    chunk_order(events, steps, n_chunks);
+    return SY_OK;
 }
 
 extern "C" sy_status sy_wave3d_run(sy_queue_t qh, const sy_stencil3d_params* p, const void* u0, void* u_a,
@@ -208,6 +226,8 @@ extern "C" sy_status sy_wave3d_run(sy_queue_t qh, const sy_stencil3d_params* p, 
         return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
     RunArgs<sy_stencil3d_params> a{p, u0, u_a, u_b, steps, chunks, n_chunks, halo_radius, events != nullptr};
     const uint64_t timed = static_cast<uint64_t>(steps + 1) * static_cast<uint64_t>(n_chunks);
-    return graph_run(q, q->run3, run_key(a), timed, events != nullptr, issue_run<sy_stencil3d_params, step3>, &a,
-                     events, prev_out, cur_out);
+    SY_TRY(graph_run(q, q->run3, run_key(a), timed, events != nullptr, issue_run<sy_stencil3d_params, step3>, &a,
+                     events, prev_out, cur_out));
+    chunk_order(events, steps, n_chunks);
+    return SY_OK;
 }

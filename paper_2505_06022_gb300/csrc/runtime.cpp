@@ -282,7 +282,7 @@ sy_status sy::stencil_param_checks(const sy_stencil_params* p) {
 
 sy_status sy::stencil_common(Queue* q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
                                 void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
-                                sy_event* chunk_events, bool start) {
+                                sy_event* chunk_events, bool start, bool reverse) {
     SY_TRY(stencil_param_checks(p));
     if (p->ny == 0 || p->nx == 0) {
         if (n_chunks == 0) return SY_OK;
@@ -296,7 +296,8 @@ sy_status sy::stencil_common(Queue* q, const sy_stencil_params* p, const void* u
     if (!start && u_next != u_prev && ranges_overlap(u_next, bytes, u_prev, bytes))
         return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
     SY_TRY(use_device(q));
-    for (int c = 0; c < n_chunks; ++c) {
+    for (int i = 0; i < n_chunks; ++i) {
+        const int c = reverse ? n_chunks - 1 - i : i;
         EventRecord* rec = nullptr;
         SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
         WaveLaunch w;
@@ -313,7 +314,8 @@ sy_status sy::stencil_common(Queue* q, const sy_stencil_params* p, const void* u
         w.u_next = u_next;
         w.row_begin = chunks[c].begin;
         w.row_end = chunks[c].end;
-        w.pdl = c == 0 ? 1 : 2;
+        w.pdl = i == 0 ? 1 : 2;  // the first launch waits for the previous step; the rest overlap it
+        w.reverse = reverse;     // a reversed step also sweeps each chunk bottom to top
         SY_TRY(launch_wave(q, w));
         SY_TRY(end_event(q, rec));
     }

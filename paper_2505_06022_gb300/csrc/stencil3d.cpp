@@ -21,7 +21,7 @@ sy_status stencil3d_param_checks(const sy_stencil3d_params* p) {
 
 sy_status stencil3d_common(Queue* q, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
                            void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
-                           sy_event* chunk_events, bool start) {
+                           sy_event* chunk_events, bool start, bool reverse) {
     SY_TRY(stencil3d_param_checks(p));
     if ((p->nz == 0 || p->ny == 0 || p->nx == 0) && n_chunks == 0) return SY_OK;
     SY_TRY(validate_chunks(p->nz, chunks, n_chunks));
@@ -33,7 +33,8 @@ sy_status stencil3d_common(Queue* q, const sy_stencil3d_params* p, const void* u
     if (!start && u_next != u_prev && ranges_overlap(u_next, bytes, u_prev, bytes))
         return fail(SY_ERR_ALIAS, "u_next partially overlaps u_prev");
     SY_TRY(use_device(q));
-    for (int c = 0; c < n_chunks; ++c) {
+    for (int i = 0; i < n_chunks; ++i) {
+        const int c = reverse ? n_chunks - 1 - i : i;
         EventRecord* rec = nullptr;
         SY_TRY(begin_event(q, chunk_events ? &chunk_events[c] : nullptr, &rec));
         WaveLaunch3 w;
@@ -52,7 +53,7 @@ sy_status stencil3d_common(Queue* q, const sy_stencil3d_params* p, const void* u
         w.u_next = u_next;
         w.z_begin = chunks[c].begin;
         w.z_end = chunks[c].end;
-        w.pdl = c == 0 ? 1 : 2;
+        w.pdl = i == 0 ? 1 : 2;  // the first launch waits for the previous step; the rest overlap it
         SY_TRY(launch_wave3d(q, w));
         SY_TRY(end_event(q, rec));
     }

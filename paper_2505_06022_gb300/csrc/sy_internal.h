@@ -153,6 +153,7 @@ struct WaveLaunch {
     const void* u_cur;
     void* u_next;
     int64_t row_begin, row_end;
+    bool reverse = false;  // visit the chunk's tiles last to first (same results)
 };
 sy_status launch_wave(Queue* q, const WaveLaunch& w);
 namespace wave {
@@ -180,9 +181,10 @@ sy_status launch_wave3d(Queue* q, const WaveLaunch3& w);
 bool wave3d_variant_info(int radius, int dtype, int variant, int* tile_rows, int* threads);
 constexpr int kWave3dVariants = 10;
 sy_status stencil3d_param_checks(const sy_stencil3d_params* p);
+// reverse: launch the chunks last to first (chunk_events[c] still belongs to chunk c).
 sy_status stencil3d_common(Queue* q, const sy_stencil3d_params* p, const void* u_prev, const void* u_cur,
                            void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
-                           sy_event* chunk_events, bool start);
+                           sy_event* chunk_events, bool start, bool reverse = false);
 
 // Replays (capturing on first use) the graph of a whole run.  `key` identifies
 // the call; `issue` enqueues its launches on q->launch and reports the buffers
@@ -190,10 +192,11 @@ sy_status stencil3d_common(Queue* q, const sy_stencil3d_params* p, const void* u
 sy_status graph_run(Queue* q, RunGraph& g, const std::vector<unsigned char>& key, uint64_t timed, bool want,
                     sy_status (*issue)(Queue*, const void*, const void**, const void**), const void* ctx,
                     sy_event* events, const void** prev_out, const void** cur_out);
-// Argument checks and one launch per chunk, shared by sy_stencil_step/start/run.
+// Argument checks and one launch per chunk, shared by sy_stencil_step/start/run;
+// reverse: launch the chunks last to first (chunk_events[c] still belongs to chunk c).
 sy_status stencil_common(Queue* q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
                          void* u_next, const sy_chunk* chunks, int n_chunks, int halo_radius,
-                         sy_event* chunk_events, bool start);
+                         sy_event* chunk_events, bool start, bool reverse = false);
 sy_status stencil_param_checks(const sy_stencil_params* p);
 int wave_variant_count(int radius, int dtype);
 bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* tile_cols, int* threads);

@@ -195,6 +195,9 @@ struct Args {
     // With 1 or 2 the block's first thread also waits at exit, so that a launch's
     // completion implies its predecessor's and the chain is transitive.
     int pdl;
+    // Vector kernel: 1 = visit the tiles in reverse order (tile t as tiles - 1 - t), so
+    // the sweep over the chunk runs bottom to top; the results are the same.
+    int reverse;
 };
 
 // One output point from its neighbourhood, in the canonical operation order.
@@ -415,8 +418,9 @@ __device__ __forceinline__ void wave_vec_body(const Args& a) {
     // warp, then the coordinates advance by (dy, dx) per trip.
     int64_t ty = w / a.tiles_x, tx = w - ty * a.tiles_x;
     const int64_t dy = nwarps / a.tiles_x, dx = nwarps - dy * a.tiles_x;
+    const int64_t tiles_y = a.tiles / a.tiles_x;
     for (int64_t t = w; t < a.tiles; t += nwarps) {
-        wave_tile<S, R, RY, START>(a, tx, ty, lane);
+        wave_tile<S, R, RY, START>(a, a.reverse ? a.tiles_x - 1 - tx : tx, a.reverse ? tiles_y - 1 - ty : ty, lane);
         tx += dx;
         ty += dy;
         if (tx >= a.tiles_x) {

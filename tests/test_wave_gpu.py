@@ -359,6 +359,24 @@ def test_wave_run_matches_oracle(q, steps, dtype, r, nch):
         assert all(m > 0 for m in ms) and ms[0] == sy.sy_event_elapsed(q, evs[0])
 
 
+def test_wave_run_events_in_chunk_order(q):
+    """The run launches alternate steps' chunks in reverse order; the ids it returns stay in chunk
+    order: with a thin and a thick chunk, every step's first id times the thin one."""
+    torch = torch_cuda()
+    ny, nx, steps = 4096, 4096, 5
+    d0 = to_device(inputs.to_storage(inputs.gaussian_pulse(ny, nx, 50.0), "f32"))
+    ua, ub = torch.empty_like(d0), torch.empty_like(d0)
+    p = sy.stencil_params(ny, nx, 1, 0.25, "f32")
+    chunks = [(0, 8), (8, ny)]
+    for _ in range(2):
+        _, _, evs = sy.sy_wave_run(q, p, d0, ua, ub, steps, chunks, 1, want_events=True)
+        torch.cuda.synchronize()
+        ms = sy.sy_events_elapsed(q, evs)
+        assert len(ms) == 2 * (steps + 1)
+        for s in range(steps + 1):
+            assert ms[2 * s + 1] > 2 * ms[2 * s], (s, ms)  # about 2-3 us against 20 us
+
+
 def test_wave_run_errors(q):
     torch = torch_cuda()
     a = torch.zeros(8, 64, device="cuda")
