@@ -24,6 +24,10 @@
  *     host before anything is launched; a rejected call launches nothing.
  *   - All kernels are hand-written CUDA for sm_103a; there is no CPU fallback.
  *     SY_ERR_CUDA reports a CUDA runtime error (message in sy_last_error()).
+ *   - A queue is not safe for concurrent calls: calls taking the same queue (or a
+ *     plan or model made on it) must not overlap in time -- issue them from one
+ *     host thread or serialise them.  Different queues may be driven from
+ *     different threads at once; the library's shared tables are locked.
  */
 #ifndef SY_H
 #define SY_H
