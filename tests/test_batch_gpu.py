@@ -149,6 +149,41 @@ def test_config2_full_batch_sampled(q, tile_rows):
         sy.sy_stencil_batch_destroy(plan)
 
 
+@pytest.mark.parametrize("tile_rows", [0, 4])
+def test_max_grids_per_plan(q, tile_rows):
+    """4096 grids in one plan (the most a plan takes; a work-list entry holds the grid index in
+    12 bits), sides from 1 to 300, every radius: two steps bit-exact against the oracle; a
+    4097th grid is refused."""
+    torch = torch_cuda()
+    z = inputs.splitmix64(31, 3 * 4096)
+    shapes = [(1 + int(z[3 * g] % np.uint64(40)), 1 + int(z[3 * g + 1] % np.uint64(300)),
+               1 + int(z[3 * g + 2] % np.uint64(4))) for g in range(4096)]
+    host, dev = [], []
+    for g, (ny, nx, r) in enumerate(shapes):
+        u0 = inputs.random_field(5000 + g, ny, nx)
+        pitch = pitch_for(nx, "f32")
+        ub = torch.zeros((ny, pitch), dtype=torch.float32, device="cuda")
+        ub[:, :nx] = torch.from_numpy(u0).cuda()
+        host.append(u0)
+        dev.append((torch.zeros_like(ub), ub, pitch))
+    plan = plan_for(q, shapes, dev, "f32", tile_rows)
+    try:
+        sy.sy_stencil_batch_start(plan)
+        sy.sy_stencil_batch_step(plan, 0)
+        sy.sy_stencil_batch_step(plan, 1)
+        torch.cuda.synchronize()
+    finally:
+        sy.sy_stencil_batch_destroy(plan)
+    for (ny, nx, r), (ua, ub, pitch), u0 in zip(shapes, dev, host):
+        _, want = oracle.wave_run_mirror(oracle.F32, u0, 2, r, 0.25)
+        assert np.array_equal(bits(host_of(ub, nx, "f32")), bits(want)), (ny, nx, r)
+    extra = torch.zeros((1, 4), device="cuda"), torch.zeros((1, 4), device="cuda")
+    with pytest.raises(sy.SyError) as e:
+        sy.sy_stencil_batch_plan(q, [(ny, nx, pitch, r, 0.25, ua, ub) for (ny, nx, r), (ua, ub, pitch)
+                                     in zip(shapes, dev)] + [(1, 1, 4, 1, 0.25, extra[0], extra[1])], "f32", tile_rows)
+    assert e.value.name == "SY_ERR_INVALID_ARGUMENT"
+
+
 def test_batch_errors(q):
     torch = torch_cuda()
     a = torch.zeros(16, 64, device="cuda")
