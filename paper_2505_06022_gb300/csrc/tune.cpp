@@ -6,7 +6,7 @@
 // records between launches), and reports the median of `reps` timed runs after
 // one warm-up run.  A run's time is the span from the first chunk's first block
 // to the last chunk's last block.  It is both the fallback of the learned cost
-// model and the judge of its regret.
+// model and the baseline its regret is measured against.
 #include <algorithm>
 #include <cmath>
 #include <vector>
