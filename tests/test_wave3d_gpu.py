@@ -127,6 +127,25 @@ def test_3d_slab_variants_16bit_ragged(q, variant, dtype):
     assert np.array_equal(bits(c), bits(oc)) and np.array_equal(bits(p), bits(op))
 
 
+@pytest.mark.parametrize("c2", [0.0, 0.07, 0.33])
+@pytest.mark.parametrize("dtype,r", [("f32", 1), ("bf16", 2)])
+def test_3d_any_c2_bit_exact(q, c2, dtype, r):
+    shape = (11, 23, 150)
+    u0 = field(shape, dtype, seed=14)
+    nz = shape[0]
+    p = sy.stencil3d_params(*shape, r, c2, dtype)
+    torch = torch_cuda()
+    d0 = torch.from_numpy(u0 if dtype == "f32" else u0.view(np.int16)).cuda().reshape(-1)
+    a, b = torch.empty_like(d0), torch.empty_like(d0)
+    pv, cv, _ = sy.sy_wave3d_run(q, p, d0, a, b, 4, sy.sy_split_rows(nz, 3), r)
+    torch.cuda.synchronize()
+    byptr = {d0.data_ptr(): d0, a.data_ptr(): a, b.data_ptr(): b}
+    st = np.float32 if dtype == "f32" else np.uint16
+    op, oc = oracle.wave3d_run_mirror(DT[dtype], u0, 4, r, c2)
+    assert np.array_equal(bits(byptr[cv].cpu().numpy().view(st).reshape(shape)), bits(oc))
+    assert np.array_equal(bits(byptr[pv].cpu().numpy().view(st).reshape(shape)), bits(op))
+
+
 def test_3d_degenerate_shapes(q):
     for shape, chunks in [((1, 1, 1), [(0, 1)]), ((1, 8, 8), [(0, 1)]), ((7, 1, 5), [(0, 7)]),
                           ((5, 6, 1), [(0, 2), (2, 5)])]:

@@ -333,6 +333,18 @@ def test_config1_energy_drift_full_size(q):
     assert E0 > 0 and abs(E1 - E0) / E0 < 1e-3
 
 
+@pytest.mark.parametrize("c2", [0.0, 0.1, 0.3, 0.49, 1.7])
+@pytest.mark.parametrize("dtype,r", [("f32", 1), ("f32", 3), ("bf16", 2), ("f16", 1)])
+def test_any_c2_bit_exact(q, c2, dtype, r):
+    # c2 not a power of two (its FP32 rounding, and c2/2 for the start, enter every update),
+    # c2 = 0 (pure inertia) and an unstable c2 = 1.7 (growing values) all stay bit-exact
+    ny, nx = 41, 300
+    u0 = field(ny, nx, dtype, seed=11)
+    gp, gc = wave_run(q, u0, 5, r, c2, dtype, sy.sy_split_rows(ny, 3))
+    op, oc = oracle.wave_run_mirror(DT[dtype], u0, 5, r, c2)
+    assert np.array_equal(bits(gc), bits(oc)) and np.array_equal(bits(gp), bits(op))
+
+
 # ---- whole-run entry (CUDA graph) and per-chunk timestamps ---------------------------
 
 @pytest.mark.parametrize("steps", [0, 1, 2, 3, 10])
