@@ -230,11 +230,16 @@ def _call(name: str, *args) -> None:
 
 
 def _ptr(t) -> int | None:
-    """Device (or host) address of a tensor / integer address / None."""
+    """Device (or host) address of a tensor / integer address / None.  A tensor must be
+    contiguous: the library reads its own layout (pitch, plane) from the call's
+    parameters, so a strided view would be read as something else."""
     if t is None:
         return None
     if isinstance(t, int):
         return t
+    if hasattr(t, "is_contiguous") and not t.is_contiguous():
+        raise ValueError("tensor arguments must be contiguous (pass the pitch / plane of a padded layout instead "
+                         "of a strided view)")
     return t.data_ptr()
 
 

@@ -83,3 +83,13 @@ def test_no_oracle_in_the_product_library():
     assert "oracle" not in out
     deps = subprocess.run(["ldd", sy.lib_path()], capture_output=True, text=True).stdout
     assert "liboracle" not in deps
+
+
+def test_binding_refuses_strided_views():
+    import torch
+
+    base = torch.zeros(6, 8)
+    assert sy._ptr(base) == base.data_ptr() and sy._ptr(base[2:]) == base[2:].data_ptr()
+    for view in (base.t(), base[:, :5], base[::2]):
+        with pytest.raises(ValueError):
+            sy._ptr(view)
