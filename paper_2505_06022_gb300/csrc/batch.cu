@@ -94,7 +94,6 @@ __device__ __forceinline__ void batch_tile(const BatchGridDev& G, int parity, in
     a.c2 = START ? 0.5f * G.c2 : G.c2;
     a.stamp = nullptr;
     a.pdl = 0;
-    a.reverse = 0;
     wave::wave_tile<S, R, RY, START>(a, tx, ty, lane);
 }
 

@@ -195,9 +195,6 @@ struct Args {
     // With 1 or 2 the block's first thread also waits at exit, so that a launch's
     // completion implies its predecessor's and the chain is transitive.
     int pdl;
-    // Vector kernel: 1 = visit the tiles in reverse order (tile t as tiles - 1 - t), so
-    // the sweep over the chunk runs bottom to top; the results are the same.
-    int reverse;
 };
 
 // One output point from its neighbourhood, in the canonical operation order.
@@ -405,7 +402,9 @@ __device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty,
     else wave_tile_impl<S, R, RY, START, true>(a, tx, ty, lane);
 }
 
-template <typename S, int R, int RY, bool START>
+// REV = true visits the tiles in reverse order (tile t as tiles - 1 - t): the chunk is
+// swept bottom to top, with the same results.
+template <typename S, int R, int RY, bool START, bool REV>
 __device__ __forceinline__ void wave_vec_body(const Args& a) {
     if (a.pdl == 1) griddep_wait();
     if (a.pdl) griddep_launch_dependents();
@@ -414,35 +413,44 @@ __device__ __forceinline__ void wave_vec_body(const Args& a) {
     const int64_t warps_per_block = blockDim.x >> 5;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * warps_per_block;
     const int64_t w = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5);
-    // tile t = w + i * nwarps, as (ty, tx) = divmod(t, tiles_x): two divisions per
-    // warp, then the coordinates advance by (dy, dx) per trip.
-    int64_t ty = w / a.tiles_x, tx = w - ty * a.tiles_x;
+    // tile t = w + i * nwarps (REV: tiles - 1 - t), as (ty, tx) = divmod(tile, tiles_x):
+    // two divisions per warp, then the coordinates move by (dy, dx) per trip.
+    const int64_t first = REV ? a.tiles - 1 - w : w;
+    int64_t ty = first / a.tiles_x, tx = first - ty * a.tiles_x;
     const int64_t dy = nwarps / a.tiles_x, dx = nwarps - dy * a.tiles_x;
-    const int64_t tiles_y = a.tiles / a.tiles_x;
     for (int64_t t = w; t < a.tiles; t += nwarps) {
-        wave_tile<S, R, RY, START>(a, a.reverse ? a.tiles_x - 1 - tx : tx, a.reverse ? tiles_y - 1 - ty : ty, lane);
-        tx += dx;
-        ty += dy;
-        if (tx >= a.tiles_x) {
-            tx -= a.tiles_x;
-            ++ty;
+        wave_tile<S, R, RY, START>(a, tx, ty, lane);
+        if constexpr (REV) {
+            tx -= dx;
+            ty -= dy;
+            if (tx < 0) {
+                tx += a.tiles_x;
+                --ty;
+            }
+        } else {
+            tx += dx;
+            ty += dy;
+            if (tx >= a.tiles_x) {
+                tx -= a.tiles_x;
+                ++ty;
+            }
         }
     }
     stamp_end(a.stamp);
     if (a.pdl && threadIdx.x == 0) griddep_wait();
 }
 
-template <typename S, int R, int RY, bool START>
+template <typename S, int R, int RY, bool START, bool REV>
 __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
-    wave_vec_body<S, R, RY, START>(a);
+    wave_vec_body<S, R, RY, START, REV>(a);
 }
 
 // The same kernel held to 96 registers (5 blocks of 128 threads an SM instead of 4, for
 // a 20-byte spill): 16-bit storage, radius 1, 4-row tiles, the default there.  Measured
 // at 8192^2: BF16 6.38 -> 6.55 TB/s, FP16 6.38 -> 6.50 TB/s.
-template <typename S, int R, int RY, bool START>
+template <typename S, int R, int RY, bool START, bool REV>
 __global__ void __maxnreg__(96) wave_vec_kernel_r96(Args a) {
-    wave_vec_body<S, R, RY, START>(a);
+    wave_vec_body<S, R, RY, START, REV>(a);
 }
 
 // One point per thread; any element-aligned layout.
@@ -485,21 +493,24 @@ using KernelFn = void (*)(Args);
 sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn scalar_fn, int tile_rows,
                        int threads, int V, size_t esize);
 
-template <typename S, int R, bool START>
+template <typename S, int R, bool START, bool REV>
 KernelFn pick_vec(int tile_rows) {
     switch (tile_rows) {
-        case 2: return wave_vec_kernel<S, R, 2, START>;
+        case 2: return wave_vec_kernel<S, R, 2, START, REV>;
         case 4:
-            if constexpr (sizeof(S) == 2 && R == 1) return wave_vec_kernel_r96<S, R, 4, START>;
-            else return wave_vec_kernel<S, R, 4, START>;
-        case 8: return wave_vec_kernel<S, R, 8, START>;
-        default: return wave_vec_kernel<S, R, 16, START>;
+            if constexpr (sizeof(S) == 2 && R == 1) return wave_vec_kernel_r96<S, R, 4, START, REV>;
+            else return wave_vec_kernel<S, R, 4, START, REV>;
+        case 8: return wave_vec_kernel<S, R, 8, START, REV>;
+        default: return wave_vec_kernel<S, R, 16, START, REV>;
     }
 }
 
+// The start always sweeps forward (a run's reversed steps are its odd leapfrog steps).
 template <typename S, int R>
 sy_status launch_r(Queue* q, const WaveLaunch& w, int tile_rows, int threads) {
-    KernelFn vec = w.start ? pick_vec<S, R, true>(tile_rows) : pick_vec<S, R, false>(tile_rows);
+    KernelFn vec = w.start     ? pick_vec<S, R, true, false>(tile_rows)
+                   : w.reverse ? pick_vec<S, R, false, true>(tile_rows)
+                               : pick_vec<S, R, false, false>(tile_rows);
     KernelFn sca = w.start ? wave_scalar_kernel<S, R, true> : wave_scalar_kernel<S, R, false>;
     return launch_typed(q, w, vec, sca, tile_rows, threads, Traits<S>::V, sizeof(S));
 }
