@@ -52,6 +52,40 @@ def test_bit_exact_vs_mirror(q, dtype, r, shape):
     assert np.array_equal(bits(gc), bits(oc)) and np.array_equal(bits(gp), bits(op))
 
 
+# Central second-difference weights of order 2r (Fornberg 1988), (w_0, w_1, ..., w_r).
+FORNBERG = {1: (-2.0, 1.0), 2: (-5 / 2, 4 / 3, -1 / 12), 3: (-49 / 18, 3 / 2, -3 / 20, 1 / 90),
+            4: (-205 / 72, 8 / 5, -1 / 5, 8 / 315, -1 / 560)}
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_8x8_two_chunks_vs_dense_operator(q, r):
+    """8 x 8 grid stepped in the chunks [0, 3) and [3, 8) (a chunk thinner than 2r, and halos
+    reaching across several rows of the other chunk): bit-exact against the oracle's mirror, and
+    within FP32 rounding of an FP64 iteration with the dense 64 x 64 operator built here point by
+    point from the weights."""
+    n, steps, c2 = 8, 7, 0.25
+    w = FORNBERG[r]
+    L = np.zeros((n * n, n * n))
+    for i in range(n):
+        for j in range(n):
+            row = i * n + j
+            L[row, row] += 2 * w[0]
+            for k in range(1, r + 1):
+                for ii, jj in ((i - k, j), (i + k, j), (i, j - k), (i, j + k)):
+                    if 0 <= ii < n and 0 <= jj < n:
+                        L[row, ii * n + jj] += w[k]
+    u0 = field(n, n, "f32", seed=40 + r)
+    gp, gc = wave_run(q, u0, steps, r, c2, "f32", [(0, 3), (3, 8)])
+    _, oc = oracle.wave_run_mirror(oracle.F32, u0, steps, r, c2)
+    assert np.array_equal(bits(gc), bits(oc))
+    x0 = u0.astype(np.float64).reshape(-1)
+    prev, cur = x0 + 0.5 * c2 * (L @ x0), x0
+    for _ in range(steps):
+        prev, cur = cur, 2 * cur - prev + c2 * (L @ cur)
+    tol = (1e-5 if r == 1 else 1e-4) * np.max(np.abs(cur))
+    assert np.max(np.abs(gc.reshape(-1).astype(np.float64) - cur)) <= tol
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 @pytest.mark.parametrize("r", [1, 2, 4])
 def test_start_bit_exact(q, dtype, r):
