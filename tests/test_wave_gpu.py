@@ -52,9 +52,20 @@ def test_bit_exact_vs_mirror(q, dtype, r, shape):
     assert np.array_equal(bits(gc), bits(oc)) and np.array_equal(bits(gp), bits(op))
 
 
-# Central second-difference weights of order 2r (Fornberg 1988), (w_0, w_1, ..., w_r).
-FORNBERG = {1: (-2.0, 1.0), 2: (-5 / 2, 4 / 3, -1 / 12), 3: (-49 / 18, 3 / 2, -3 / 20, 1 / 90),
-            4: (-205 / 72, 8 / 5, -1 / 5, 8 / 315, -1 / 560)}
+def fornberg_weights() -> dict:
+    """(w_0, ..., w_r) per radius from the cited fixture tests/golden/fornberg_d2_weights.txt."""
+    from fractions import Fraction
+    import os
+
+    out = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "fornberg_d2_weights.txt")):
+        if line.strip() and not line.startswith("#"):
+            r, *w = line.split()
+            out[int(r)] = tuple(float(Fraction(x)) for x in w)
+    return out
+
+
+FORNBERG = fornberg_weights()
 
 
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
