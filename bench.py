@@ -879,7 +879,9 @@ def run_gpu(args) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "updates_per_step": updates_per_step,
                        "launches_per_step": launches // max(1, args.steps),
-                       "l2": "inputs larger than L2 (three 256 MiB fields per step, 161 GB moved per step)",
+                       "l2": ("inputs larger than L2 (three 256 MiB fields, 161 GB of algorithmic traffic per "
+                              "step); no flush between steps: the run alternates its sweep direction, so each "
+                              "time step starts on rows the previous one left in L2"),
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "gb_per_s": value * BYTES_PER_UPDATE / 1e9,
             "frac_hbm_measured": value * BYTES_PER_UPDATE / 1e9 / peaks["hbm_gbs"],
