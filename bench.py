@@ -880,8 +880,9 @@ def run_gpu(args) -> None:
             "config": {"workload": WORKLOAD, "updates_per_step": updates_per_step,
                        "launches_per_step": launches // max(1, args.steps),
                        "l2": ("inputs larger than L2 (three 256 MiB fields, 161 GB of algorithmic traffic per "
-                              "step); no flush between steps: the run alternates its sweep direction, so each "
-                              "time step starts on rows the previous one left in L2"),
+                              "simulation), so simulations need no L2 flush between them; inside a simulation "
+                              "the sweep direction alternates, so each time step starts on rows the previous "
+                              "one left in L2"),
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "gb_per_s": value * BYTES_PER_UPDATE / 1e9,
             "frac_hbm_measured": value * BYTES_PER_UPDATE / 1e9 / peaks["hbm_gbs"],
