@@ -64,7 +64,12 @@ class RankChunk:
 
 
 class GpuRankChunk(RankChunk):
-    """RankChunk stepping with the library's CUDA kernel on this rank's GPU."""
+    """RankChunk stepping with the library's CUDA kernel on this rank's GPU.
+
+    The queue must issue on torch's current stream (what sy.Queue borrows by default):
+    the exchange's NCCL sends are ordered after the work already on that stream, and
+    waiting on its receives orders that stream after them, so the step's kernel reads
+    the new halo rows and the next exchange sends finished ones."""
 
     def __init__(self, queue, c2: float, dtype: str = "f32", **kw):
         super().__init__(**kw)
@@ -80,7 +85,8 @@ class GpuRankChunk(RankChunk):
 class GpuRankChunk3d(RankChunk):
     """The 3D grid split into chunks of planes, one per rank: the same exchange along
     dimension 0 (whole planes), stepping with the library's 3D kernel on this rank's
-    planes.  Local buffers are (planes, ny, pitch) tensors."""
+    planes.  Local buffers are (planes, ny, pitch) tensors.  The queue issues on torch's
+    current stream, as for GpuRankChunk."""
 
     def __init__(self, queue, nz: int, ny: int, nx: int, radius: int, halo: int, rank: int, world: int, c2: float,
                  dtype: str = "f32", pitch: int | None = None):
