@@ -87,7 +87,7 @@ const char* sy_last_error(void);
 int sy_abi_version(void);
 
 /* ------------------------------------------------------------------------- */
-/* Queue (paper §2, Listing 1: `queue q(gpu_selector)`)                       */
+/* Queue (paper §2, Listing 1: a queue bound to one GPU device)               */
 /* ------------------------------------------------------------------------- */
 
 /* Borrow the legacy default stream (the runtime's cudaStreamLegacy handle); the
@@ -128,7 +128,7 @@ sy_status sy_events_elapsed(sy_queue_t q, const sy_event* events, int n, double*
 sy_status sy_energy_read(sy_queue_t q, uint64_t* millijoules);
 
 /* Device energy in joules since the queue was created (paper §4, Listing 3:
- * `q.device_energy_consumption()`).  Includes every process's work on the GPU. */
+ * the queue's whole-device energy query).  Includes every process's work on the GPU. */
 sy_status sy_device_energy(sy_queue_t q, double* joules);
 
 /* Metering window.  sy_meter_begin synchronises the queue and samples the energy
@@ -140,7 +140,7 @@ sy_status sy_device_energy(sy_queue_t q, double* joules);
 sy_status sy_meter_begin(sy_queue_t q);
 sy_status sy_meter_end(sy_queue_t q, double* joules, double* seconds);
 
-/* Energy of one kernel (paper §4, Listing 3: `q.kernel_energy_consumption(e)`):
+/* Energy of one kernel (paper §4, Listing 3: the energy query on a kernel's event):
  * the average device power of the closed metering window the kernel ran in,
  * times the kernel's device time.  SY_ERR_NOT_READY if the kernel was not
  * issued inside a window that has since been closed. */
