@@ -18,3 +18,57 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["unit"] == "updates/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["higher_is_better"] is True
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    return bench
+
+
+def test_clock_record_from_nvidia_smi_lines():
+    import threading
+
+    bench = _bench()
+
+    class Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.proc, s._t = Proc(), threading.Thread(target=lambda: None)
+    s._t.start()
+    s.lines = ["0, 2070, 2070, 650.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 700.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line", "0, [N/A], 2070, 1.0, 0x0, a, b, c, d"]
+    rec = s.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"] and rec["power_w_median"] == 700.0
+    s2 = bench.ClockSampler(0)
+    s2.proc, s2._t = Proc(), threading.Thread(target=lambda: None)
+    s2._t.start()
+    s2.lines = ["0, 900, 2070, 300, 0x8, Not Active, Active, Not Active, Not Active"]
+    assert s2.stop()["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_clock_record_without_nvidia_smi():
+    bench = _bench()
+    s = bench.ClockSampler(0)
+    s.proc = None
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_measured_peak_and_kernel_hash():
+    bench = _bench()
+    peaks = bench.measured_peaks()
+    assert peaks["hbm_gbs"] > 0 and peaks["source"] in ("measured", "fallback")
+    sha = bench.kernel_source_sha()
+    assert len(sha) == 16 and sha == bench.kernel_source_sha()
+    assert bench.ncu_traffic() in (None, float(json.load(open(os.path.join(ROOT, "profiles",
+                                                                            "wave_f32_8192_traffic.json")))
+                                                 ["dram_bytes_per_launch"]))
