@@ -71,6 +71,27 @@ def test_3d_stencil_matches_dense_kronecker_operator(r, shape):
     assert np.max(np.abs(prev.reshape(-1) - a)) <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("dt", [oracle.F32, oracle.BF16, oracle.F16])
+@pytest.mark.parametrize("r", [1, 3])
+def test_3d_start_mirror_is_the_rounded_taylor_start(dt, r):
+    # u^{-1} = u^0 + (c2/2) L u^0 with the dense Kronecker operator in FP64: the mirror's start agrees
+    # within one rounding of the storage type (relative to the field's size), equals the run's
+    # u^{-1} bit for bit, and with c2 = 0 returns u^0 unchanged
+    shape = (4, 5, 7)
+    name = {oracle.F32: "f32", oracle.BF16: "bf16", oracle.F16: "f16"}[dt]
+    u0 = inputs.to_storage(inputs.random_field_3d(61 + r, *shape).astype(np.float64), name)
+    x0 = (oracle.storage_to_f64(u0, dt) if dt != oracle.F32 else u0.astype(np.float64)).reshape(-1)
+    want = x0 + 0.5 * C2 * (kron3(*shape, r) @ x0)
+    um1 = oracle.wave3d_start_mirror(dt, u0, r, C2)
+    got = (oracle.storage_to_f64(um1, dt) if dt != oracle.F32 else um1.astype(np.float64)).reshape(-1)
+    ulp = {oracle.F32: 2.0 ** -23, oracle.BF16: 2.0 ** -7, oracle.F16: 2.0 ** -10}[dt]
+    assert np.max(np.abs(got - want)) <= 4 * ulp * max(1.0, np.max(np.abs(want)))
+    prev0, cur0 = oracle.wave3d_run_mirror(dt, u0, 0, r, C2)
+    assert np.array_equal(um1.view(np.uint8), prev0.view(np.uint8))
+    assert np.array_equal(cur0.view(np.uint8), u0.view(np.uint8))
+    assert np.array_equal(oracle.wave3d_start_mirror(dt, u0, r, 0.0).view(np.uint8), u0.view(np.uint8))
+
+
 @pytest.mark.parametrize("r", [1, 2])
 def test_3d_stencil_exact_on_polynomials(r):
     # L applied to z^a y^b x^c (a+b+c <= 2r+1) is the exact Laplacian at points r away from the
