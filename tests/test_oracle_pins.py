@@ -410,3 +410,22 @@ def test_adam_constant_gradient_closed_form():
     for t in range(1, 6):
         oracle.adam_step(p, g, m, v, t, lr, 0.9, 0.999, eps)
         np.testing.assert_allclose(p, -t * lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-18)
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    # every output point is computed independently, so 1 thread and all threads give the same bits
+    u0 = inputs.to_storage(inputs.gaussian_pulse(96, 130, 9.0) + 0.05 * inputs.random_field(71, 96, 130), "f32")
+    u3 = inputs.to_storage(inputs.random_field_3d(72, 9, 20, 33).astype(np.float64), "bf16")
+    x, y = inputs.saxpy_inputs(10007, seed=73)
+    n0 = oracle.threads()
+    try:
+        runs = []
+        for n in (1, max(2, n0)):
+            oracle.set_threads(n)
+            runs.append((oracle.wave_run_mirror(oracle.F32, u0, 9, 2, 0.25), oracle.wave_run_f64(u0.astype(np.float64), 9, 2, 0.25),
+                         oracle.wave3d_run_mirror(oracle.BF16, u3, 4, 1, 0.125), oracle.saxpy_f32(2.5, x, y)))
+    finally:
+        oracle.set_threads(n0)
+    (m1, f1, t1, s1), (m2, f2, t2, s2) = runs
+    for a, b in [(m1[0], m2[0]), (m1[1], m2[1]), (f1[1], f2[1]), (t1[1], t2[1]), (s1, s2)]:
+        assert np.array_equal(np.asarray(a).view(np.uint8), np.asarray(b).view(np.uint8))
