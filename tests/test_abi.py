@@ -85,6 +85,25 @@ def test_no_oracle_in_the_product_library():
     assert "liboracle" not in deps
 
 
+def test_product_package_never_imports_the_oracle():
+    import ast
+    import os
+
+    pkg = os.path.dirname(sy.__file__)
+    for name in os.listdir(pkg):
+        if not name.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, name)).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert all(not a.name.startswith("oracle") for a in node.names), name
+            elif isinstance(node, ast.ImportFrom):
+                assert not (node.module or "").startswith("oracle"), name
+    csrc = os.path.join(pkg, "csrc")
+    for name in os.listdir(csrc):
+        assert "oracle" not in open(os.path.join(csrc, name), errors="ignore").read().lower(), name
+
+
 def test_binding_refuses_strided_views():
     import torch
 
