@@ -102,6 +102,18 @@ def test_product_package_never_imports_the_oracle():
     csrc = os.path.join(pkg, "csrc")
     for name in os.listdir(csrc):
         assert "oracle" not in open(os.path.join(csrc, name), errors="ignore").read().lower(), name
+    # and the oracle uses nothing of the product: no package import, no repository header
+    odir = os.path.join(os.path.dirname(pkg), "oracle")
+    for name in os.listdir(odir):
+        path = os.path.join(odir, name)
+        if name.endswith(".py"):
+            for node in ast.walk(ast.parse(open(path).read())):
+                if isinstance(node, (ast.Import, ast.ImportFrom)):
+                    mods = [a.name for a in node.names] if isinstance(node, ast.Import) else [node.module or ""]
+                    assert all("paper_2505_06022_gb300" not in m for m in mods), name
+        elif name.endswith(".c"):
+            includes = [l for l in open(path) if l.startswith("#include")]
+            assert all("<" in l for l in includes), (name, includes)
 
 
 def test_binding_refuses_strided_views():
