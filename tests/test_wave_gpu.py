@@ -434,6 +434,29 @@ def test_wave_run_events_in_chunk_order(q):
             assert ms[2 * s + 1] > 2 * ms[2 * s], (s, ms)  # about 2-3 us against 20 us
 
 
+def test_wave_run_graph_cache_follows_every_argument(q):
+    """One cached graph per queue: any change of grid parameters, c2, step count, chunks, halo,
+    variant or buffers must re-capture; returning to earlier arguments must not replay a stale graph."""
+    torch = torch_cuda()
+    ny, nx = 40, 264
+    u0 = field(ny, nx, "f32", seed=21)
+    u1 = field(ny, nx, "f32", seed=22)
+    d0, d1 = to_device(u0), to_device(u1)
+    ua, ub, uc = (torch.empty_like(d0) for _ in range(3))
+    base = dict(r=1, c2=0.25, steps=4, chunks=[(0, 20), (20, 40)], halo=1, variant=0, src=(d0, u0), bufs=(ua, ub))
+    cases = [base, dict(base, c2=0.3), dict(base, steps=5), dict(base, chunks=[(0, 7), (7, 40)]), dict(base, halo=2),
+             dict(base, variant=3), dict(base, r=2, halo=2), dict(base, src=(d1, u1)), dict(base, bufs=(ub, uc)), base]
+    for c in cases:
+        dsrc, hsrc = c["src"]
+        p = sy.stencil_params(ny, nx, c["r"], c["c2"], "f32", variant=c["variant"])
+        pv, cv, _ = sy.sy_wave_run(q, p, dsrc, c["bufs"][0], c["bufs"][1], c["steps"], c["chunks"], c["halo"])
+        torch.cuda.synchronize()
+        byptr = {t.data_ptr(): t for t in (d0, d1, ua, ub, uc)}
+        op, oc = oracle.wave_run_mirror(oracle.F32, hsrc, c["steps"], c["r"], c["c2"])
+        assert np.array_equal(bits(to_host(byptr[cv], None, np.float32)), bits(oc)), c
+        assert np.array_equal(bits(to_host(byptr[pv], None, np.float32)), bits(op)), c
+
+
 def test_wave_run_errors(q):
     torch = torch_cuda()
     a = torch.zeros(8, 64, device="cuda")
