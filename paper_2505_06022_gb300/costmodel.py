@@ -213,10 +213,37 @@ def train(q: Queue, corpus, train_ids, epochs: int = 300, batch: int = 256, lr: 
     return model
 
 
+def tile_sweep(q: Queue, n: int = 8192, reps: int = 5) -> list[dict]:
+    """Every tile variant of the 2D step on one n x n chunk, per storage type and radius, with the
+    library's exhaustive tuner (device timestamps, median of `reps`): GB/s of algorithmic bytes
+    (3 x element size per point) for each variant and the fastest."""
+    import torch
+
+    out = []
+    for dtype in ("f32", "bf16", "f16"):
+        tdt = torch.float32 if dtype == "f32" else torch.int16
+        a, b, c = (torch.zeros(n, n, dtype=tdt, device="cuda") for _ in range(3))
+        b.copy_(torch.from_numpy(inputs.to_storage(inputs.gaussian_pulse(n, n, 64.0), dtype)
+                                 .view(np.float32 if dtype == "f32" else np.int16)).cuda())
+        es = 4 if dtype == "f32" else 2
+        for r in (1, 2, 3, 4):
+            p = stencil_params(n, n, r, 0.25, dtype)
+            recs = sy_tune_stencil(q.handle, p, a, b, c, chunk_counts=(1,), reps=reps)
+            gbs = {rec["variant"]: 3 * es * n * n / (rec["ms"] * 1e-3) / 1e9 for rec in recs}
+            best = max(recs, key=lambda rec: gbs[rec["variant"]])
+            out.append({"dtype": dtype, "radius": r, "gb_per_s": gbs, "best_variant": best["variant"],
+                        "best_tile": [best["tile_rows"], best["threads"]], "best_gb_per_s": gbs[best["variant"]],
+                        "default_tile": list(sy_stencil_variant_info(r, DTYPE_CODES[dtype], 0)[::2])})
+        del a, b, c
+    return out
+
+
 def main() -> None:
     import torch
 
     ap = argparse.ArgumentParser()
+    ap.add_argument("--tile-sweep", type=int, default=0, metavar="N",
+                    help="only sweep the 2D tile variants on an N x N chunk and print one JSON line per case")
     ap.add_argument("--stencil", type=int, default=560)
     ap.add_argument("--saxpy", type=int, default=40)
     ap.add_argument("--reps", type=int, default=3)
@@ -226,6 +253,10 @@ def main() -> None:
     args = ap.parse_args()
     torch.cuda.set_device(0)
     q = Queue(0)
+    if args.tile_sweep:
+        for rec in tile_sweep(q, args.tile_sweep):
+            print(json.dumps(rec), flush=True)
+        return
     shapes = inputs.cost_corpus_shapes(n_stencil=args.stencil, n_saxpy=args.saxpy)
     t0 = time.time()
     corpus = measure(q, shapes, reps=args.reps, log=lambda m: print(m, flush=True))
