@@ -140,13 +140,16 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_label(dtype: str) -> str:
-    """The dominant kernel of the timed step: the default tile of the 2D step for this storage
-    type (16-bit radius-1 4-row tiles run the 96-register form)."""
+def kernel_label(dtype: str, variant: int = 0) -> str:
+    """The dominant kernel of the timed step: the 2D step's variant for this storage type
+    (the default unless one is asked for; 16-bit radius-1 4-row tiles run the 96-register form)."""
     import paper_2505_06022_gb300 as sy
 
-    rows, _, threads = sy.sy_stencil_variant_info(RADIUS, sy.DTYPE_CODES[dtype], 0)
-    name = "wave_vec_kernel_r96" if dtype != "f32" and RADIUS == 1 and rows == 4 else "wave_vec_kernel"
+    code = sy.DTYPE_CODES[dtype]
+    v = variant or sy.sy_stencil_default_variant(RADIUS, code)
+    rows, _, threads = sy.sy_stencil_variant_info(RADIUS, code, v)
+    name = "wave_hln_kernel" if v >= 13 else "wave_hl_kernel" if v >= 9 else \
+        ("wave_vec_kernel_r96" if dtype != "f32" and RADIUS == 1 and rows == 4 else "wave_vec_kernel")
     return f"{name}<{dtype},{RADIUS},{rows},false> x {threads} threads, one 2048x8192 chunk per launch"
 
 
@@ -325,9 +328,22 @@ def measure_precision_form(q, stream, dtype: str) -> dict:
     err = error_vs_f64(got)
     esize = 4 if dtype == "f32" else 2
     upd = STEPS * NY * NX
+    drift = (E1 - E0) / E0
     return {"dtype": dtype, "updates_per_s": upd / (ms * 1e-3), "gb_per_s": 3 * esize * upd / (ms * 1e-3) / 1e9,
             "ms_per_sim": ms, "j_per_update": None if not joules else joules / (reps * upd),
-            "error_vs_f64": err, "energy_drift_rel": (E1 - E0) / E0}
+            "error_vs_f64": err, "energy_drift_rel": drift, **stated_accuracy(dtype, dict(err, energy_drift=drift))}
+
+
+def stated_accuracy(dtype: str, errors: dict) -> dict:
+    """tolerance_<measure> keys (the stored bounds of the accuracy module), whether every
+    measured error is within them, and whether the storage type is usable on this workload."""
+    from paper_2505_06022_gb300 import accuracy
+
+    res = accuracy.check(dtype, errors)
+    out = {f"tolerance_{k}": bound for k, (_, bound, _) in res.items()}
+    out["within_tolerance"] = all(ok for (_, _, ok) in res.values())
+    out["usable"] = accuracy.USABLE[dtype]
+    return out
 
 
 def measure_batched(q, stream) -> dict:
@@ -372,6 +388,15 @@ def measure_batched(q, stream) -> dict:
     reps, ms, joules = _metered(q, stream, lambda: sy.sy_stencil_batch_run(plan))
     sy.sy_stencil_batch_destroy(plan)
 
+    # the cross-step form: the whole run as one cooperative launch, a grid barrier per step
+    plan = sy.sy_stencil_batch_plan(q.handle, [(ny, nx, pitch, r, C2, ua, ub) for ny, nx, pitch, r, ua, ub
+                                               in fields], "f32", 0)
+    sy.sy_stencil_batch_capture_persistent(plan, steps)
+    sy.sy_stencil_batch_run(plan)
+    reps_p, ms_p, joules_p = _metered(q, stream, lambda: sy.sy_stencil_batch_run(plan))
+    sy.sy_queue_sync(q.handle)  # a barrier that gave up would show here
+    sy.sy_stencil_batch_destroy(plan)
+
     # baseline: one launch per grid per step
     params = [(sy.stencil_params(ny, nx, r, C2, "f32", pitch=pitch), ua, ub, [(0, ny)], r)
               for ny, nx, pitch, r, ua, ub in fields]
@@ -400,7 +425,32 @@ def measure_batched(q, stream) -> dict:
     qg = qg_saved
     qs.close()
     del g
+
+    # Energy per update by radius class: each class's grids alone in a plan of their own
+    # (>= 1 s metering window each), and the plain 8192^2 single field at the same radius
+    # (4 chunks, 20 steps): the batch's J/update is the classes' update-weighted mix.
+    per_class = {}
+    for r in sorted({f[3] for f in fields}):
+        sub = [f for f in fields if f[3] == r]
+        cplan = sy.sy_stencil_batch_plan(q.handle, [(ny, nx, pitch, rr, C2, ua, ub)
+                                                    for ny, nx, pitch, rr, ua, ub in sub], "f32", 0)
+        sy.sy_stencil_batch_capture(cplan, steps)
+        sy.sy_stencil_batch_run(cplan)
+        reps_c, ms_c, j_c = _metered(q, stream, lambda: sy.sy_stencil_batch_run(cplan))
+        sy.sy_stencil_batch_destroy(cplan)
+        pts = sum(ny * nx for ny, nx, *_ in sub)
+        per_class[f"r{r}"] = {"grids": len(sub), "points": pts, "updates_per_s": steps * pts / (ms_c * 1e-3),
+                              "ms_per_run": ms_c,
+                              "j_per_update": None if not j_c else j_c / (reps_c * steps * pts),
+                              "avg_power_w": None if not j_c else j_c / (reps_c * ms_c * 1e-3),
+                              "zero_fraction_u0": float(np.mean([float((inputs.batch_initial(ny, nx, "f32") == 0)
+                                                                        .mean()) for ny, nx, *_ in sub])),
+                              "plain_8192": plain_radius_energy(q, stream, r),
+                              "plain_8192_dense": plain_radius_energy(q, stream, r, sigma=NX / 16)}
     return {"grids": len(fields), "points": points, "steps": steps, "tile_rows": tile_rows,
+            "per_class": per_class,
+            "cross_step_updates_per_s": upd / (ms_p * 1e-3), "cross_step_ms_per_run": ms_p,
+            "cross_step_j_per_update": None if not joules_p else joules_p / (reps_p * upd),
             "batched_updates_per_s": upd / (ms * 1e-3), "batched_gb_per_s": 12 * upd / (ms * 1e-3) / 1e9,
             "batched_ms_per_run": ms, "batched_j_per_update": None if not joules else joules / (reps * upd),
             "per_grid_graph_updates_per_s": upd / (ms_g * 1e-3), "per_grid_graph_ms_per_run": ms_g,
@@ -408,6 +458,31 @@ def measure_batched(q, stream) -> dict:
             "per_grid_stream_updates_per_s": upd / (ms_s * 1e-3), "per_grid_stream_ms_per_run": ms_s,
             "launches_per_run": {"batched": batched_launches, "per_grid": steps * len(fields)},
             "mode": "one launch per radius class per step" if tile_rows == 0 else "one launch per step"}
+
+
+def plain_radius_energy(q, stream, r: int, steps: int = 20, sigma: float = SIGMA) -> dict:
+    """The 8192^2 FP32 single field at radius r (4 chunks, halo r, `steps` steps, whole runs
+    graph-replayed) from a Gaussian of width `sigma`: updates/s, J/update and average power
+    over a >= 1 s window.  With the headline's sigma = 64 most of the field is exactly zero;
+    sigma = 512 (the batched grids' recipe, side / 16) leaves almost no point zero."""
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import inputs
+
+    host = inputs.to_storage(inputs.gaussian_pulse(NY, NX, sigma), "f32")
+    u0 = torch.from_numpy(host).cuda()
+    A, B = torch.empty_like(u0), torch.empty_like(u0)
+    p = sy.stencil_params(NY, NX, r, C2, "f32")
+    chunks = sy.sy_split_rows(NY, CHUNKS)
+    run = lambda: sy.sy_wave_run(q.handle, p, u0, A, B, steps, chunks, r)  # noqa: E731
+    run()
+    reps, ms, joules = _metered(q, stream, run)
+    upd = steps * NY * NX
+    return {"steps": steps, "sigma": sigma, "zero_fraction_u0": float((host == 0).mean()),
+            "updates_per_s": upd / (ms * 1e-3),
+            "j_per_update": None if not joules else joules / (reps * upd),
+            "avg_power_w": None if not joules else joules / (reps * ms * 1e-3)}
 
 
 def measure_saxpy(q, stream) -> dict:
@@ -466,10 +541,11 @@ def measure_saxpy(q, stream) -> dict:
     return out
 
 
-def measure_temporal(q, stream, T: int, dtype: str = "f32") -> dict:
+def measure_temporal(q, stream, T: int, dtype: str = "f32", radius: int = 1) -> dict:
     """The headline simulation (8192^2, 200 steps, 4 row chunks) with temporal blocking: the
-    Taylor start, then 200/T passes of T steps each (halo T*r), from the resident initial field.
-    Not the headline configuration (its halo is 1); reported beside it."""
+    Taylor start, then 200/T passes of T steps each (halo T*r), from the resident initial field;
+    optionally with another storage type or stencil radius.  Not the headline configuration (its
+    halo is 1); reported beside it, with the single-step run of the same storage and radius."""
     import numpy as np
     import torch
 
@@ -480,9 +556,9 @@ def measure_temporal(q, stream, T: int, dtype: str = "f32") -> dict:
     u0 = torch.from_numpy(host if dtype == "f32" else host.view(np.int16)).cuda()
     A, C, D = (torch.empty_like(u0) for _ in range(3))
     Bw = torch.empty_like(u0)
-    p = sy.stencil_params(NY, NX, 1, C2, dtype)
+    p = sy.stencil_params(NY, NX, radius, C2, dtype)
     chunks = sy.sy_split_rows(NY, CHUNKS)
-    halo = T
+    halo = T * radius
 
     def sim():
         sy.sy_stencil_start(q.handle, p, u0, A, chunks, halo)
@@ -499,9 +575,17 @@ def measure_temporal(q, stream, T: int, dtype: str = "f32") -> dict:
     sy.sy_queue_sync(q.handle)
     esize = 4 if dtype == "f32" else 2
     upd = STEPS * NY * NX
-    return {"T": T, "dtype": dtype, "halo": halo, "updates_per_s": upd / (ms * 1e-3), "ms_per_sim": ms,
-            "hbm_bytes_per_update": 4 * esize / T, "j_per_update": None if not joules else joules / (reps * upd),
-            "equivalent_single_step_gb_per_s": 3 * esize * upd / (ms * 1e-3) / 1e9}
+    out = {"T": T, "dtype": dtype, "radius": radius, "halo": halo, "updates_per_s": upd / (ms * 1e-3),
+           "ms_per_sim": ms, "hbm_bytes_per_update": 4 * esize / T,
+           "j_per_update": None if not joules else joules / (reps * upd),
+           "equivalent_single_step_gb_per_s": 3 * esize * upd / (ms * 1e-3) / 1e9}
+    if radius != 1 or dtype != "f32":  # the single-step run it replaces (same storage, radius, halo)
+        run = lambda: sy.sy_wave_run(q.handle, p, u0, A, C, STEPS, chunks, radius)  # noqa: E731
+        run()
+        reps1, ms1, j1 = _metered(q, stream, run)
+        out["single_step_updates_per_s"] = upd / (ms1 * 1e-3)
+        out["single_step_j_per_update"] = None if not j1 else j1 / (reps1 * upd)
+    return out
 
 
 def measure_wave3d(q, stream, dtype: str = "f32", radius: int = 1) -> dict:
@@ -612,7 +696,7 @@ def run_gpu(args) -> None:
     import torch
 
     global RADIUS, HALO, BYTES_PER_UPDATE, WORKLOAD
-    if args.radius != 1 or args.dtype != "f32":  # a non-headline variant of the same workload
+    if args.radius != 1 or args.dtype != "f32" or args.variant:  # a non-headline variant of the workload
         RADIUS = HALO = args.radius
         BYTES_PER_UPDATE = 3 * (4 if args.dtype == "f32" else 2)
         WORKLOAD = WORKLOAD.replace("5-point FP32", f"radius-{RADIUS} star, {args.dtype.upper()} storage") \
@@ -631,7 +715,7 @@ def run_gpu(args) -> None:
 
     stream = torch.cuda.current_stream()
     q = sy.Queue(local, stream)
-    p = sy.stencil_params(NY, NX, RADIUS, C2, args.dtype)
+    p = sy.stencil_params(NY, NX, RADIUS, C2, args.dtype, variant=args.variant)
     chunks = sy.sy_split_rows(NY, CHUNKS)
 
     u0_host = inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), args.dtype)
@@ -704,7 +788,7 @@ def run_gpu(args) -> None:
                 "traffic": ncu_traffic() if (args.dtype == "f32" and RADIUS == 1) else None,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": kernel_label(args.dtype),
+                "kernel": kernel_label(args.dtype, args.variant),
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "frac_of_nominal_8000": achieved / 8000.0,
                 "stamp_avg_chunk_ms": statistics.mean(stamp_ms),
@@ -739,101 +823,60 @@ def run_gpu(args) -> None:
                       "j_per_update_above_idle": (joules - idle_w * seconds) / (sims * updates_per_step),
                       "chunk_kernel_j_mean": statistics.mean(kern_j)}
 
-    # ---- e2e: host (pinned) initial field in, final field out, through the same API ----
-    # Every step copies its input field from pinned host memory and its final field back,
-    # inside the timed region.  The copies run on a second stream, overlapped with the
-    # neighbouring steps' simulations: the next input is staged while this step runs
-    # (then moved into place on the device, so the captured graph keeps its pointers) and
-    # the previous result is read back from a device copy of it.  The sequential form
-    # (copy in, simulate, copy out) is reported beside it.  Each form is timed over k steps
-    # three times and the median reported.
+    # ---- e2e: whole simulations from host memory, through sy_wave_run_host ----
+    # Every step hands the library the pinned host initial field and receives the final
+    # field in pinned host memory; the library makes both copies (one per direction, on
+    # its own copy streams, overlapping the neighbouring steps' simulations).  The timed
+    # region is host wall-clock from a synchronised start to sy_queue_sync after the last
+    # step, so every copy is inside it.  The sequential form (sync after every step, no
+    # overlap) is reported beside it.  Each form is timed three times; the median counts.
     e2e = None
     if True:
         h_in = torch.from_numpy(u0_host if args.dtype == "f32" else u0_host.view(np.int16)).pin_memory()
-        h_out = torch.empty_like(h_in).pin_memory()
-        d_in, d_stage, d_res = torch.empty_like(u0), torch.empty_like(u0), torch.empty_like(u0)
-        byptr = {A.data_ptr(): A, B.data_ptr(): B, d_in.data_ptr(): d_in}
-        side = torch.cuda.Stream()
-        k_e2e = max(1, min(args.steps, 5))
+        h_out = [torch.empty_like(h_in).pin_memory() for _ in range(2)]
+        k_e2e = max(1, min(args.steps, 10))
 
-        def sequential(k):
-            for _ in range(k):
-                d_in.copy_(h_in, non_blocking=True)
-                pv, cv, _ = simulate(d_in, False)
-                h_out.copy_(byptr[cv], non_blocking=True)
-            return pv, cv
-
-        def pipelined(k, start_event):
-            side.wait_event(start_event)
-            with torch.cuda.stream(side):
-                d_stage.copy_(h_in, non_blocking=True)
-            staged = torch.cuda.Event()
-            staged.record(side)
-            read_back = None
+        def host_steps(k, sync_each):
             for i in range(k):
-                stream.wait_event(staged)
-                d_in.copy_(d_stage, non_blocking=True)
-                consumed = torch.cuda.Event()
-                consumed.record(stream)
-                if i + 1 < k:
-                    side.wait_event(consumed)
-                    with torch.cuda.stream(side):
-                        d_stage.copy_(h_in, non_blocking=True)
-                    staged = torch.cuda.Event()
-                    staged.record(side)
-                pv, cv, _ = simulate(d_in, False)
-                if read_back is not None:
-                    stream.wait_event(read_back)
-                d_res.copy_(byptr[cv], non_blocking=True)
-                ready = torch.cuda.Event()
-                ready.record(stream)
-                side.wait_event(ready)
-                with torch.cuda.stream(side):
-                    h_out.copy_(d_res, non_blocking=True)
-                read_back = torch.cuda.Event()
-                read_back.record(side)
-            stream.wait_event(read_back)
-            return pv, cv
+                sy.sy_wave_run_host(q.handle, p, h_in, h_out[i % 2], STEPS, chunks, HALO)
+                if sync_each:
+                    sy.sy_queue_sync(q.handle)
+            sy.sy_queue_sync(q.handle)
 
-        sequential(2)
+        host_steps(2, False)  # first calls allocate the work sets and capture their graphs
+        _, cv_d, _ = simulate(u0, False)
         torch.cuda.synchronize()
-        want_out = h_out.clone()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        times_seq, times_pipe = [], []
-        for _ in range(3):  # each form timed three times; the median is reported
-            e0.record(stream)
-            pv, cv = sequential(k_e2e)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            times_seq.append(e0.elapsed_time(e1))
-        ms_seq = statistics.median(times_seq)
-        h_out.zero_()
-        start = torch.cuda.Event()
-        start.record(stream)
-        pipelined(2, start)
-        torch.cuda.synchronize()
-        for _ in range(3):
-            e0.record(stream)
-            pv, cv = pipelined(k_e2e, e0)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            times_pipe.append(e0.elapsed_time(e1))
-        ms_e2e = statistics.median(times_pipe)
+        want_out = {A.data_ptr(): A, B.data_ptr(): B, u0.data_ptr(): u0}[cv_d].cpu()
+        assert torch.equal(h_out[0], want_out) and torch.equal(h_out[1], want_out), \
+            "sy_wave_run_host result differs from the device-buffer run"
+
+        def timed(sync_each):
+            out = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                if dist:
+                    dist.barrier()
+                t0 = time.perf_counter()
+                host_steps(k_e2e, sync_each)
+                out.append((time.perf_counter() - t0) * 1e3)
+            return statistics.median(out)
+
+        h_out[0].zero_()
+        ms_e2e = timed(False)
+        ms_seq = timed(True)
         if dist:  # the job takes as long as its slowest replica
             t = torch.tensor([ms_e2e, ms_seq], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_e2e, ms_seq = float(t[0].item()), float(t[1].item())
-        assert torch.equal(h_out, want_out), "pipelined end-to-end result differs from the sequential one"
+        assert torch.equal(h_out[0], want_out), "sy_wave_run_host result changed between calls"
         e2e = {"value": world * k_e2e * updates_per_step / (ms_e2e * 1e-3), "unit": "updates/s",
                "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
-               "d2h_bytes_per_step": h_out.numel() * h_out.element_size(),
+               "d2h_bytes_per_step": h_out[0].numel() * h_out[0].element_size(),
                "ms_per_step": ms_e2e / k_e2e, "steps": k_e2e, "repeats": 3,
-               "mode": "host copies on a second stream, overlapped with the neighbouring simulations",
+               "api": "sy_wave_run_host (C ABI, pinned host buffers in and out)",
+               "timing": "host wall clock, synchronised start to sy_queue_sync after the last step",
+               "mode": "the library's copies overlap the neighbouring steps' simulations",
                "sequential_value": world * k_e2e * updates_per_step / (ms_seq * 1e-3)}
-        # the result must be the physics, not garbage: energy of the final state is finite
-        E = sy.sy_wave_energy(q.handle, p, byptr[cv], byptr[pv])[0]
-        assert np.isfinite(E) and E > 0
 
     # accuracy of the headline's final field against the FP64 oracle (tolerance 1e-5 relative)
     accuracy = None
@@ -841,7 +884,8 @@ def run_gpu(args) -> None:
         _, cv_h, _ = simulate(u0, False)
         torch.cuda.synchronize()
         final = {A.data_ptr(): A, B.data_ptr(): B, u0.data_ptr(): u0}[cv_h].cpu().numpy().astype(np.float64)
-        accuracy = dict(error_vs_f64(final), tolerance_max_rel=1e-5)
+        err = error_vs_f64(final)
+        accuracy = dict(err, **stated_accuracy("f32", err))
 
     forms = None
     if rank == 0 and world == 1 and args.forms and args.dtype == "f32" and RADIUS == 1:
@@ -857,6 +901,9 @@ def run_gpu(args) -> None:
         forms["batched"] = measure_batched(q, stream)
         forms["temporal_T2"] = measure_temporal(q, stream, 2)
         forms["temporal_T4"] = measure_temporal(q, stream, 4)
+        forms["temporal_T4_bf16"] = measure_temporal(q, stream, 4, "bf16")
+        forms["temporal_T2_r4"] = measure_temporal(q, stream, 2, "f32", 4)
+        forms["temporal_T4_r4"] = measure_temporal(q, stream, 4, "f32", 4)
         forms["learned"] = measure_learned(q, stream)
     if dist:
         dist.barrier()
@@ -916,6 +963,8 @@ def main() -> None:
                     help="field storage of the wave workload (headline: f32)")
     ap.add_argument("--radius", type=int, default=1, choices=[1, 2, 3, 4],
                     help="stencil and halo radius of the wave workload (headline: 1)")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="2D step variant (0 = the library default; used for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "sy":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -100,7 +100,8 @@ int sy_abi_version(void);
  * creation (for sy_device_energy) when NVML is available. */
 sy_status sy_queue_create(int device, void* cuda_stream, sy_queue_t* out);
 sy_status sy_queue_destroy(sy_queue_t q);
-/* Block until all work submitted to the queue has completed.  Returns
+/* Block until all work submitted to the queue has completed (including the
+ * host copies of sy_wave_run_host).  Returns
  * SY_ERR_TIMEOUT (once) if a kernel's bounded wait gave up since the last sync. */
 sy_status sy_queue_sync(sy_queue_t q);
 /* The cudaStream_t the queue submits to. */
@@ -265,7 +266,35 @@ sy_status sy_wave_run(sy_queue_t q, const sy_stencil_params* p, const void* u0, 
                       const sy_chunk* chunks, int n_chunks, int halo_radius, sy_event* events, const void** prev_out,
                       const void** cur_out);
 
-/* Temporal blocking: T leapfrog steps (T = 2 or 4; radius 1 or 2) in one pass over
+/* sy_wave_run on host memory: the runtime moves the data, as the paper's
+ * buffer/accessor model has it (§2 Listing 1, §3: a kernel names the data it
+ * accesses and the runtime makes it present where the kernel runs).  The call
+ * copies host_u0 (ny x pitch elements of p's storage type, the device layout)
+ * into device memory the queue owns, runs the Taylor start and `steps` chunked
+ * steps exactly as sy_wave_run does (same launches, same cached-graph replay,
+ * same results), and copies u^{steps} into host_out and, when host_prev_out is
+ * not NULL, u^{steps-1} into host_prev_out (each ny x pitch elements).
+ *   - Asynchronous: the call returns once the work is enqueued.  host_u0 must
+ *     stay unchanged, and host_out / host_prev_out must not be read, until
+ *     sy_queue_sync(q) returns.  With pinned host memory (cudaHostAlloc or
+ *     cudaHostRegister) the copies are asynchronous; pageable memory works, but
+ *     its copies synchronise with the host.
+ *   - Consecutive calls overlap: alternate calls use two device work sets of three
+ *     fields each (allocated on the first call and when a larger grid arrives,
+ *     freed by sy_queue_destroy), and the copies run on one stream per direction,
+ *     so a call's input copy overlaps the previous call's simulation and its
+ *     output copy the next call's.  A call whose host_u0 overlaps the previous
+ *     call's outputs waits for those copies first, so feeding a result back in is
+ *     safe.
+ *   - host_out and host_prev_out must not overlap each other (SY_ERR_ALIAS);
+ *     host_u0 may equal host_out (it is read before the result is written).
+ *   - events as in sy_wave_run (valid until the next whole run on this queue);
+ *     other errors as in sy_wave_run. */
+sy_status sy_wave_run_host(sy_queue_t q, const sy_stencil_params* p, const void* host_u0, void* host_out,
+                           void* host_prev_out, int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius,
+                           sy_event* events);
+
+/* Temporal blocking: T leapfrog steps (T = 2 or 4; radius 1 to 4) in one pass over
  * memory.  Each chunk reads u^{n-1} (u_prev) and u^n (u_cur) with a halo of T x r
  * rows (halo_radius >= T * radius) and writes u^{n+T-1} (out_prev) and u^{n+T}
  * (out_cur) for its rows; the intermediate steps are recomputed on the halo in
@@ -281,8 +310,18 @@ sy_status sy_stencil_multistep(sy_queue_t q, const sy_stencil_params* p, int T, 
 
 /* Number of tile variants for a (radius, dtype); variant ids are 1..count
  * (0 always means the default).  tile_rows / tile_cols / threads (nullable)
- * describe variant `variant`. */
+ * describe variant `variant`: a warp tile of tile_rows x tile_cols output points,
+ * `threads` per block.  tile_cols = 32 x (16 / element size) is the register
+ * tile whose outer lanes load the columns beside it; tile_cols = 30 x (16 /
+ * element size) is the halo-lane form, whose two outer lanes hold those columns
+ * instead of producing output (no edge registers, 1/16 of the lanes idle).
+ * Variants 1-8: register tiles of 2/4/8/16 rows x 128/256 threads; 9-12:
+ * halo-lane tiles of 4/8 rows x 128/256 threads; for 16-bit storage also 13-14:
+ * narrow halo-lane tiles (4 elements, 8 bytes, a lane: tile_cols = 120) of 4/8
+ * rows x 128 threads, which hold half the registers per tile row. */
 sy_status sy_stencil_variant_count(int radius, int dtype, int* count);
+/* The variant (1..count) that variant 0 stands for at this radius and storage. */
+sy_status sy_stencil_default_variant(int radius, int dtype, int* variant);
 sy_status sy_stencil_variant_info(int radius, int dtype, int variant, int* tile_rows, int* tile_cols,
                                   int* threads);
 
@@ -386,6 +425,17 @@ sy_status sy_stencil_batch_step(sy_batch_plan_t plan, int parity, int timed);
 /* Capture `steps` consecutive steps, parities 0, 1, 0, ... into a CUDA graph owned
  * by the plan (replacing any earlier capture).  Every launch is timed. */
 sy_status sy_stencil_batch_capture(sy_batch_plan_t plan, int64_t steps);
+/* The same `steps` steps as ONE cooperative launch (the cross-step form): every
+ * block of a co-resident grid walks the classes' tiles of a step, then meets the
+ * others at a grid-wide barrier before the next step.  One kernel carries every
+ * radius (with the per-class tile heights), so its register budget is that of
+ * the radius-4 tiles.  The barrier's wait is bounded (about 1 s): if it gives up,
+ * the next sy_queue_sync returns SY_ERR_TIMEOUT and the fields are invalid.
+ * Needs a per-class plan (tile_rows = 0) and a device with cooperative launch
+ * (SY_ERR_UNSUPPORTED otherwise); replaces any earlier capture, replayed by
+ * sy_stencil_batch_run with the same parity rules; its one launch is timed
+ * (sy_stencil_batch_times index 1). */
+sy_status sy_stencil_batch_capture_persistent(sy_batch_plan_t plan, int64_t steps);
 /* Replay the captured steps on the queue's stream.  Each replay starts at parity
  * 0, so with an even step count consecutive replays continue the simulation; after
  * a replay of an odd count u_a holds the newest field. */
@@ -706,14 +756,19 @@ sy_status sy_checkpoint_load(sy_queue_t q, const char* path, const sy_stencil_pa
  * allocates nothing and synchronises nothing:
  *   - The per-block partial sums live in one fixed module-scope device array of
  *     2 x 1024 doubles (16 KiB), which every GPU that loads the library holds
- *     until the process exits.  The reduction always uses exactly that many; a
- *     call needing more is rejected with SY_ERR_INVALID_ARGUMENT.
+ *     until the process exits.  The reduction has a fixed shape that uses exactly
+ *     that many for any grid size (checked when the library is compiled), so no
+ *     grid is too large for it.
  *   - It runs on the calling thread's current device, on `cuda_stream` (a
  *     cudaStream_t; NULL = the legacy default stream), with no queue.
  *   - out3 (device, 3 doubles, caller-owned) receives energy, kinetic and
  *     potential, as sy_wave_energy computes them (same kernels, same order).
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and keeps it for the life of the process, per device
+ *     ordinal; make that first call before any stream capture.  The address
+ *     belongs to the device's primary context: calling this from another context
+ *     (one created with the driver API), or after cudaDeviceReset, is not
+ *     supported.
  *   - Every call shares the one array and leaves its partial sums there; each
  *     call overwrites all of them before reading, so nothing needs clearing, but
  *     calls that overlap on the GPU (different streams, or a graph replayed

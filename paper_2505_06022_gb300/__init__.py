@@ -168,11 +168,14 @@ _SIGS = {
     "sy_stencil_batch_start": [_p, C.c_int],
     "sy_stencil_batch_step": [_p, C.c_int, C.c_int],
     "sy_stencil_batch_capture": [_p, _i64],
+    "sy_stencil_batch_capture_persistent": [_p, _i64],
     "sy_stencil_batch_run": [_p],
     "sy_stencil_batch_times": [_p, _p, C.c_int],
     "sy_stencil_batch_destroy": [_p],
     "sy_stencil_multistep": [_p, _p, C.c_int, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_wave_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
+    "sy_wave_run_host": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p],
+    "sy_stencil_default_variant": [C.c_int, C.c_int, _p],
     "sy_stencil3d_step": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_stencil3d_start": [_p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_wave3d_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
@@ -424,6 +427,10 @@ def sy_stencil_batch_capture(plan: int, steps: int) -> None:
     _call("sy_stencil_batch_capture", plan, steps)
 
 
+def sy_stencil_batch_capture_persistent(plan: int, steps: int) -> None:
+    _call("sy_stencil_batch_capture_persistent", plan, steps)
+
+
 def sy_stencil_batch_run(plan: int) -> None:
     _call("sy_stencil_batch_run", plan)
 
@@ -648,6 +655,32 @@ def sy_wave_run(q: int, p: StencilParams, u0, u_a, u_b, steps: int, chunks, halo
     return pv.value, cv.value, (list(evs[:n_ev]) if want_events else [])
 
 
+def _host_ptr(a) -> int | None:
+    """Host address of a numpy array / CPU tensor / integer address / None (C-contiguous only)."""
+    if a is None or isinstance(a, int):
+        return a
+    if hasattr(a, "ctypes"):  # numpy
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return a.ctypes.data
+    if getattr(a, "is_cuda", False):
+        raise ValueError("sy_wave_run_host takes host memory; pass device tensors to sy_wave_run")
+    return _ptr(a)
+
+
+def sy_wave_run_host(q: int, p: StencilParams, host_u0, host_out, steps: int, chunks, halo_radius: int,
+                     host_prev_out=None, want_events: bool = False) -> list[int]:
+    """sy_wave_run on host memory (numpy arrays or CPU tensors, pinned for overlap): copies
+    host_u0 in, runs the start and `steps` chunked steps, copies u^{steps} into host_out (and
+    u^{steps-1} into host_prev_out).  Asynchronous: results are valid after sy_queue_sync."""
+    arr, k = _chunks(chunks)
+    n_ev = (steps + 1) * k
+    evs = (C.c_uint64 * max(1, n_ev))() if want_events else None
+    _call("sy_wave_run_host", q, C.byref(p), _host_ptr(host_u0), _host_ptr(host_out), _host_ptr(host_prev_out),
+          steps, arr, k, halo_radius, evs)
+    return list(evs[:n_ev]) if want_events else []
+
+
 def sy_stencil_multistep(q: int, p: StencilParams, T: int, u_prev, u_cur, out_prev, out_cur, chunks,
                          halo_radius: int, want_events: bool = False) -> list[int]:
     arr, k = _chunks(chunks)
@@ -655,6 +688,12 @@ def sy_stencil_multistep(q: int, p: StencilParams, T: int, u_prev, u_cur, out_pr
     _call("sy_stencil_multistep", q, C.byref(p), T, _ptr(u_prev), _ptr(u_cur), _ptr(out_prev), _ptr(out_cur), arr,
           k, halo_radius, evs if want_events else None)
     return list(evs[:k]) if want_events else []
+
+
+def sy_stencil_default_variant(radius: int, dtype: int) -> int:
+    v = C.c_int()
+    _call("sy_stencil_default_variant", radius, dtype, C.byref(v))
+    return v.value
 
 
 def sy_stencil_variant_count(radius: int, dtype: int) -> int:

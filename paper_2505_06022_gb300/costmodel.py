@@ -83,14 +83,28 @@ def measure(q: Queue, shapes: list[dict], reps: int = 3, log=None) -> dict:
             "shape": np.asarray(shape_id, np.int64), "cand": np.asarray(meta, np.int64)}
 
 
+def _fields(dt: str, n: int, seed: int = 5) -> list:
+    """Three n x n device fields of storage `dt` holding uniform values in [-1, 1) (switching
+    power depends on the data: zeros would understate it)."""
+    import torch
+
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    tdt = torch.float32 if dt == "f32" else torch.bfloat16
+    out = []
+    for _ in range(3):
+        t = torch.rand(n * n + 64, generator=g, device="cuda", dtype=torch.float32).mul_(2.0).sub_(1.0)
+        out.append(t.to(tdt))
+    return out
+
+
 def group_power(q: Queue, seconds: float = 1.0) -> dict:
     """Busy device power (W) per (kind, dtype, radius) group from >= `seconds` bursts."""
     import torch
 
     out = {}
     n = 8192
-    fields = {dt: [torch.zeros(n * n * (4 if dt == "f32" else 2) // 4 + 64, dtype=torch.float32, device="cuda")
-                   for _ in range(3)] for dt in ("f32", "bf16")}
+    fields = {dt: _fields(dt, n) for dt in ("f32", "bf16")}
     for dt in ("f32", "bf16"):
         for r in (1, 2, 3, 4):
             p = stencil_params(n, n, r, 0.25, dt)
@@ -126,6 +140,76 @@ def energy_labels(shapes, corpus, power: dict) -> np.ndarray:
         key = (s["kind"], s["dtype"], s.get("radius", 0))
         out[k] = math.log(power[key]) + corpus["logt"][k] - math.log(1e3)
     return out
+
+
+def energy_check(q: Queue, n_cands: int = 96, seconds: float = 1.0, seed: int = 21) -> dict:
+    """Meters a seeded subset of stencil candidates one by one, each repeated in its own
+    >= `seconds` NVML window, and compares the measured joules per step with the label the
+    corpus gives it (group busy power x its own time).  Candidates span both storage types,
+    radius 1..4, every tile variant and chunk counts {1, 4}, on grids of 2048^2 to 8192^2.
+    Returns per-candidate rows and summary statistics (correlation of log J, the spread of
+    measured / label, and within each (storage, radius, grid) group whether the energy
+    order of the candidates is their time order)."""
+    import torch
+
+    from . import sy_stencil_variant_count, sy_split_rows, DTYPE_CODES as CODES
+
+    power = group_power(q, seconds)
+    z = inputs.splitmix64(seed, 4 * n_cands)
+    sides = (2048, 4096, 8192)
+    fields = {dt: _fields(dt, 8192) for dt in ("f32", "bf16")}
+    rows = []
+    for i in range(n_cands):
+        dt = ("f32", "bf16")[int(z[4 * i] % 2)]
+        r = 1 + int(z[4 * i + 1] % 4)
+        side = sides[int(z[4 * i + 2] % 3)]
+        nv = sy_stencil_variant_count(r, CODES[dt])
+        v = 1 + int(z[4 * i + 3] % nv)
+        k = (1, 4)[int((z[4 * i + 3] >> 32) % 2)]
+        p = stencil_params(side, side, r, 0.25, dt, variant=v)
+        chunks = sy_split_rows(side, k)
+        a, b, c = fields[dt]
+        fn = lambda: sy_stencil_step(q.handle, p, a, b, c, chunks, r)  # noqa: E731
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        sy_meter_begin(q.handle)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps, t0 = 0, time.time()
+        e0.record()
+        while reps < 20 or time.time() - t0 < seconds:
+            for _ in range(20):
+                fn()
+            reps += 20
+            torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        joules, _ = sy_meter_end(q.handle)
+        ms = e0.elapsed_time(e1) / reps
+        label = power[(1, dt, r)] * ms * 1e-3
+        rows.append({"dtype": dt, "radius": r, "side": side, "variant": v, "chunks": k, "ms": ms,
+                     "j_measured": joules / reps, "j_label": label})
+    del fields
+    lm = np.log([x["j_measured"] for x in rows])
+    ll = np.log([x["j_label"] for x in rows])
+    ratio = np.exp(lm - ll)
+    agree, groups = 0, 0
+    keyf = lambda x: (x["dtype"], x["radius"], x["side"])  # noqa: E731
+    for key in sorted({keyf(x) for x in rows}):
+        g = [x for x in rows if keyf(x) == key]
+        for a in range(len(g)):
+            for b in range(a + 1, len(g)):
+                dt_ = g[a]["ms"] - g[b]["ms"]
+                de_ = g[a]["j_measured"] - g[b]["j_measured"]
+                if abs(dt_) > 0.02 * max(g[a]["ms"], g[b]["ms"]):  # pairs whose times differ by > 2 %
+                    groups += 1
+                    agree += int((dt_ > 0) == (de_ > 0))
+    return {"candidates": rows, "corr_log_j": float(np.corrcoef(lm, ll)[0, 1]),
+            "ratio_measured_over_label": {"median": float(np.median(ratio)), "p10": float(np.quantile(ratio, 0.1)),
+                                          "p90": float(np.quantile(ratio, 0.9)), "min": float(ratio.min()),
+                                          "max": float(ratio.max())},
+            "pairs_time_order_equals_energy_order": {"pairs": groups, "agree": agree},
+            "group_power_w": {f"{k[1]}/r{k[2]}": v for k, v in power.items() if k[0] == 1}}
 
 
 def split_shapes(n_shapes: int, seed: int = 11, test_fraction: float = 0.2) -> tuple[np.ndarray, np.ndarray]:
@@ -244,6 +328,9 @@ def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--tile-sweep", type=int, default=0, metavar="N",
                     help="only sweep the 2D tile variants on an N x N chunk and print one JSON line per case")
+    ap.add_argument("--energy-check", type=int, default=0, metavar="N",
+                    help="only meter N stencil candidates one by one (>= 1 s NVML window each) and compare "
+                         "their measured energy with the corpus labels (group power x time); one JSON line")
     ap.add_argument("--stencil", type=int, default=560)
     ap.add_argument("--saxpy", type=int, default=40)
     ap.add_argument("--reps", type=int, default=3)
@@ -256,6 +343,9 @@ def main() -> None:
     if args.tile_sweep:
         for rec in tile_sweep(q, args.tile_sweep):
             print(json.dumps(rec), flush=True)
+        return
+    if args.energy_check:
+        print(json.dumps(energy_check(q, args.energy_check)), flush=True)
         return
     shapes = inputs.cost_corpus_shapes(n_stencil=args.stencil, n_saxpy=args.saxpy)
     t0 = time.time()

@@ -19,6 +19,7 @@
 #include <new>
 #include <vector>
 
+#include "tma.cuh"
 #include "wave_kernel.cuh"
 
 namespace sy {
@@ -62,6 +63,8 @@ struct BatchPlan {
     uint64_t graph_launches = 0;
     int blocks = 0;                          // persistent grid size
     int threads = 128;
+    unsigned* d_sync = nullptr;              // cross-step form: [0] barrier arrivals, [1] abort flag
+    int persistent_blocks = 0;               // cross-step form: co-resident grid of its launch
 };
 
 namespace {
@@ -77,7 +80,7 @@ __host__ __device__ __forceinline__ uint64_t pack_tile(int64_t g, int64_t tx, in
            static_cast<uint64_t>(tx);
 }
 
-template <typename S, int R, int RY, bool START>
+template <typename S, int R, int RY, bool START, bool CG = false>
 __device__ __forceinline__ void batch_tile(const BatchGridDev& G, int parity, int64_t tx, int64_t ty, int lane) {
     wave::Args a;
     const bool swap = (parity & 1) != 0;
@@ -94,7 +97,7 @@ __device__ __forceinline__ void batch_tile(const BatchGridDev& G, int parity, in
     a.c2 = START ? 0.5f * G.c2 : G.c2;
     a.stamp = nullptr;
     a.pdl = 0;
-    wave::wave_tile<S, R, RY, START>(a, tx, ty, lane);
+    wave::wave_tile<S, R, RY, START, false, CG>(a, tx, ty, lane);
 }
 
 // Tile height of the per-radius kernels: FP32 4/4/8/4 rows for r = 1..4, 16-bit 4/4/8/8.
@@ -145,6 +148,112 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchGridDev
     }
     stamp_end(stamp);
     if (pdl && threadIdx.x == 0) griddep_wait();
+}
+
+// ---- cross-step form: a whole run in one launch ----------------------------------
+// Every step of every class in one cooperative launch (all blocks co-resident): each
+// step walks the classes' work lists in turn, with the tile heights of the per-class
+// kernels, and a grid-wide barrier separates consecutive steps.  One kernel carries
+// every radius, so its register budget is that of the radius-4 tiles.  Fields are
+// written by one step and read by the next within the launch, so every load goes
+// through L2 (ld.global.cg), made coherent by the barrier's fences.  The barrier's
+// wait is bounded: a block that gives up sets the queue's error flag and an abort
+// flag that releases the others, and every block returns (sy_queue_sync then reports
+// SY_ERR_TIMEOUT and the fields are invalid).
+struct PersistClass {
+    int64_t desc_off, tile_off, tiles;
+    int radius;
+};
+
+struct PersistArgs {
+    const BatchGridDev* grids;
+    const uint64_t* work;
+    PersistClass cls[4];
+    int n_cls;
+    int64_t steps;
+    unsigned* barrier;  // arrivals; zeroed before the launch
+    unsigned* abort;    // set by a block whose wait gave up; zeroed before the launch
+    unsigned* err;      // the queue's error flags (bit 0: a bounded wait gave up)
+    int fault;          // host-injected for tests: 1 = block 0 never arrives at the first barrier
+    unsigned long long* stamp;
+};
+
+template <typename S, int R>
+__device__ __forceinline__ void persist_class(const BatchGridDev* __restrict__ grids, const uint64_t* __restrict__ work,
+                                              int64_t tiles, int parity, int64_t w, int64_t nwarps, int lane) {
+    for (int64_t t = w; t < tiles; t += nwarps) {
+        const uint64_t e = __ldg(work + t);
+        const int g = static_cast<int>(e >> (kTileXBits + kTileYBits));
+        const int64_t ty = static_cast<int64_t>((e >> kTileXBits) & ((1ull << kTileYBits) - 1));
+        const int64_t tx = static_cast<int64_t>(e & ((1ull << kTileXBits) - 1));
+        batch_tile<S, R, ClassRows<S, R>::value, false, true>(grids[g], parity, tx, ty, lane);
+    }
+}
+
+// Grid-wide barrier after step s: true when every block arrived, false if the wait
+// gave up (or another block's did).
+__device__ __forceinline__ bool persist_barrier(const PersistArgs& a, int64_t s) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();  // this block's writes of step s, before its arrival
+        if (!(a.fault == 1 && s == 0 && blockIdx.x == 0)) atomicAdd(a.barrier, 1u);
+        const unsigned target = static_cast<unsigned>(s + 1) * gridDim.x;
+        const long long t0 = clock64();
+        for (;;) {
+            unsigned v, ab;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a.barrier) : "memory");
+            if (v >= target) break;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(ab) : "l"(a.abort) : "memory");
+            if (ab || clock64() - t0 > tma::kWaitCycles) {
+                atomicOr(a.err, 1u);
+                atomicExch(a.abort, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kBatchThreads) batch_persistent_kernel(PersistArgs a) {
+    stamp_begin(a.stamp);
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * wpb;
+    const int64_t w = static_cast<int64_t>(blockIdx.x) * wpb + (threadIdx.x >> 5);
+    for (int64_t s = 0; s < a.steps; ++s) {
+        const int parity = static_cast<int>(s & 1);
+        for (int c = 0; c < a.n_cls; ++c) {
+            const PersistClass& K = a.cls[c];
+            const BatchGridDev* G = a.grids + K.desc_off;
+            const uint64_t* W = a.work + K.tile_off;
+            switch (K.radius) {
+                case 1: persist_class<S, 1>(G, W, K.tiles, parity, w, nwarps, lane); break;
+                case 2: persist_class<S, 2>(G, W, K.tiles, parity, w, nwarps, lane); break;
+                case 3: persist_class<S, 3>(G, W, K.tiles, parity, w, nwarps, lane); break;
+                default: persist_class<S, 4>(G, W, K.tiles, parity, w, nwarps, lane); break;
+            }
+        }
+        if (s + 1 < a.steps && !persist_barrier(a, s)) return;  // block-uniform
+    }
+    stamp_end(a.stamp);
+}
+
+using PersistFn = void (*)(PersistArgs);
+
+PersistFn persist_fn(int dtype) {
+    switch (dtype) {
+        case SY_F32: return batch_persistent_kernel<float>;
+        case SY_BF16: return batch_persistent_kernel<__nv_bfloat16>;
+        default: return batch_persistent_kernel<__half>;
+    }
 }
 
 using BatchFn = void (*)(const BatchGridDev*, const uint64_t*, int64_t, int, unsigned long long*, int);
@@ -465,7 +574,101 @@ sy_status sy_stencil_batch_destroy(sy_batch_plan_t ph) {
     if (P->d_desc) cudaFree(P->d_desc);
     if (P->d_tiles) cudaFree(P->d_tiles);
     if (P->d_stamps) cudaFree(P->d_stamps);
+    if (P->d_sync) cudaFree(P->d_sync);
     delete P;
+    return SY_OK;
+}
+
+sy_status sy_stencil_batch_capture_persistent(sy_batch_plan_t ph, int64_t steps) {
+    if (!ph) return fail(SY_ERR_NULL_POINTER, "plan is NULL");
+    BatchPlan* P = as_plan(ph);
+    if (steps < 1 || steps > (1 << 20)) return fail(SY_ERR_INVALID_ARGUMENT, "steps = %lld", (long long)steps);
+    if (P->tile_rows != 0)
+        return fail(SY_ERR_INVALID_ARGUMENT, "the cross-step form needs a per-class plan (tile_rows = 0)");
+    if (P->classes.size() > 4) return fail(SY_ERR_INVALID_ARGUMENT, "more than 4 radius classes");
+    Queue* q = P->q;
+    SY_TRY(use_device(q));
+    int coop = 0;
+    SY_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, q->device));
+    if (!coop) return fail(SY_ERR_UNSUPPORTED, "the device does not support cooperative launches");
+    PersistFn fn = persist_fn(P->dtype);
+    int occ = 0;
+    SY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void*>(fn), kBatchThreads, 0));
+    if (occ < 1) return fail(SY_ERR_UNSUPPORTED, "the cross-step kernel does not fit on an SM");
+    int64_t blocks = static_cast<int64_t>(occ) * q->sm_count;  // every block co-resident
+    int64_t most_tiles = 0;
+    for (const BatchClass& K : P->classes) most_tiles = K.tiles > most_tiles ? K.tiles : most_tiles;
+    const int64_t want = (most_tiles + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+    if (blocks > want) blocks = want < 1 ? 1 : want;
+    if (static_cast<uint64_t>(steps) * static_cast<uint64_t>(blocks) >= (1ull << 31))
+        return fail(SY_ERR_INVALID_ARGUMENT, "steps x blocks too large for the step barrier's counter");
+    SY_CUDA(cudaStreamSynchronize(q->stream));
+    if (P->exec) {
+        cudaGraphExecDestroy(P->exec);
+        P->exec = nullptr;
+    }
+    if (!P->d_sync) SY_CUDA(cudaMalloc(&P->d_sync, 2 * sizeof(unsigned)));
+    if (P->stamp_slots < 2) {
+        SY_CUDA(cudaFree(P->d_stamps));
+        P->d_stamps = nullptr;
+        SY_CUDA(cudaMalloc(&P->d_stamps, 4 * sizeof(unsigned long long) * 2));
+        P->stamp_slots = 2;
+    }
+    P->expected.assign(2, 0);
+    P->expected[1] = static_cast<uint64_t>(blocks);
+    PersistArgs a = {};
+    a.grids = P->d_desc;
+    a.work = P->d_tiles;
+    a.n_cls = static_cast<int>(P->classes.size());
+    for (int c = 0; c < a.n_cls; ++c) {
+        const BatchClass& K = P->classes[c];
+        a.cls[c] = PersistClass{K.desc_off, K.tile_off, K.tiles, K.radius};
+    }
+    a.steps = steps;
+    a.barrier = P->d_sync;
+    a.abort = P->d_sync + 1;
+    a.err = q->d_flags;
+    a.fault = fault_enabled("batch_barrier_timeout") ? 1 : 0;
+    a.stamp = P->d_stamps + 4;
+    q->launch = q->aux;
+    cudaError_t e = cudaStreamBeginCapture(q->aux, cudaStreamCaptureModeThreadLocal);
+    sy_status st = e == cudaSuccess ? SY_OK : cuda_fail(e, "cudaStreamBeginCapture");
+    if (st == SY_OK) {
+        e = cudaMemsetAsync(P->d_stamps + 4, 0, 4 * sizeof(unsigned long long), q->aux);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->d_sync, 0, 2 * sizeof(unsigned), q->aux);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");
+    }
+    if (st == SY_OK) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+        cfg.blockDim = dim3(kBatchThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = q->aux;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, fn, a);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaLaunchKernelEx(cooperative)");
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(q->aux, &graph);
+    if (st == SY_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
+    q->launch = q->stream;
+    if (st == SY_OK) {
+        e = cudaGraphInstantiate(&P->exec, graph, 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != SY_OK) {
+        if (P->exec) cudaGraphExecDestroy(P->exec);
+        P->exec = nullptr;
+        return st;
+    }
+    P->graph_steps = steps;
+    P->graph_launches = 1;
+    P->persistent_blocks = static_cast<int>(blocks);
     return SY_OK;
 }
 

@@ -12,6 +12,12 @@
 // the previous step touched last, while they are still in L2 (8192^2: FP32 +4 %,
 // BF16 +8 %; 3D chunks of planes gain nothing, so only their order alternates).
 // Results are unchanged; event ids are returned in chunk order.
+//
+// sy_wave_run_host is the same run on host buffers: the runtime, not the caller,
+// moves the data (the buffer/accessor model: a kernel's accessors name the data,
+// the runtime makes it present on the device).  Alternate calls use two device work
+// sets, and the copies run on a stream per direction, so a call's host-to-device copy
+// overlaps the previous call's simulation and its device-to-host copy the next one's.
 #include <algorithm>
 #include <cstring>
 
@@ -190,9 +196,134 @@ sy_status run_checks(int64_t steps, const void* u0, const void* ua, const void* 
 }
 
 }  // namespace
+
+// ---- sy_wave_run_host ---------------------------------------------------------------
+
+sy_status host_run_sync(Queue* q) {
+    HostRun& h = q->host;
+    if (h.h2d) SY_CUDA(cudaStreamSynchronize(h.h2d));
+    if (h.d2h) SY_CUDA(cudaStreamSynchronize(h.d2h));
+    return SY_OK;
+}
+
+void host_run_release(Queue* q) {
+    HostRun& h = q->host;
+    if (h.h2d) cudaStreamSynchronize(h.h2d);
+    if (h.d2h) cudaStreamSynchronize(h.d2h);
+    for (int s = 0; s < 2; ++s) {
+        if (h.graph[s].exec) cudaGraphExecDestroy(h.graph[s].exec);
+        h.graph[s] = RunGraph();
+        for (cudaEvent_t* e : {&h.in_done[s], &h.sim_done[s], &h.out_done[s]})
+            if (*e) {
+                cudaEventDestroy(*e);
+                *e = nullptr;
+            }
+    }
+    if (h.ws) cudaFree(h.ws);
+    h.ws = nullptr;
+    h.ws_bytes = h.field = 0;
+    if (h.h2d) cudaStreamDestroy(h.h2d);
+    if (h.d2h) cudaStreamDestroy(h.d2h);
+    h.h2d = h.d2h = nullptr;
+}
+
+namespace {
+
+// Copy streams and events (first call), and work sets of at least `field` bytes per field.
+sy_status host_run_prepare(Queue* q, size_t field) {
+    HostRun& h = q->host;
+    if (!h.h2d) {
+        SY_CUDA(cudaStreamCreateWithFlags(&h.h2d, cudaStreamNonBlocking));
+        SY_CUDA(cudaStreamCreateWithFlags(&h.d2h, cudaStreamNonBlocking));
+        for (int s = 0; s < 2; ++s)
+            for (cudaEvent_t* e : {&h.in_done[s], &h.sim_done[s], &h.out_done[s]})
+                SY_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    if (h.field < field) {
+        // the old sets may still be read or written: wait for every stream that uses them
+        SY_CUDA(cudaStreamSynchronize(q->stream));
+        SY_TRY(host_run_sync(q));
+        for (int s = 0; s < 2; ++s) {
+            if (h.graph[s].exec) cudaGraphExecDestroy(h.graph[s].exec);
+            h.graph[s] = RunGraph();
+        }
+        if (h.ws) SY_CUDA(cudaFree(h.ws));
+        h.ws = nullptr;
+        h.ws_bytes = h.field = 0;
+        void* ws = nullptr;
+        cudaError_t e = cudaMalloc(&ws, 6 * field);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(host-run work sets)");
+        h.ws = ws;
+        h.ws_bytes = 6 * field;
+        h.field = field;
+    }
+    return SY_OK;
+}
+
+}  // namespace
 }  // namespace sy
 
 using namespace sy;
+
+extern "C" sy_status sy_wave_run_host(sy_queue_t qh, const sy_stencil_params* p, const void* host_u0, void* host_out,
+                                      void* host_prev_out, int64_t steps, const sy_chunk* chunks, int n_chunks,
+                                      int halo_radius, sy_event* events) {
+    Queue* q = nullptr;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil_param_checks(p));
+    if (steps < 0) return fail(SY_ERR_INVALID_ARGUMENT, "steps = %lld < 0", (long long)steps);
+    if (!host_u0 || !host_out) return fail(SY_ERR_NULL_POINTER, "host field pointer is NULL");
+    if (p->ny == 0 || p->nx == 0) return fail(SY_ERR_INVALID_ARGUMENT, "empty grid");
+    const size_t bytes = static_cast<size_t>(p->ny) * static_cast<size_t>(p->pitch) * dtype_size(p->dtype);
+    if (host_prev_out && ranges_overlap(host_out, bytes, host_prev_out, bytes))
+        return fail(SY_ERR_ALIAS, "host_out and host_prev_out must not overlap");
+    SY_TRY(validate_chunks(p->ny, chunks, n_chunks));
+    if (halo_radius < p->radius)
+        return fail(SY_ERR_HALO_TOO_SMALL, "halo radius %d < stencil radius %d", halo_radius, p->radius);
+    const uint64_t timed = static_cast<uint64_t>(steps + 1) * static_cast<uint64_t>(n_chunks);
+    if (events && timed > kGraphStampSlots)
+        return fail(SY_ERR_INVALID_ARGUMENT, "%llu timed launches exceed %u per run (pass events = NULL)",
+                    (unsigned long long)timed, kGraphStampSlots);
+    SY_TRY(use_device(q));
+    const size_t field = (bytes + 255) / 256 * 256;
+    SY_TRY(host_run_prepare(q, field));
+    HostRun& h = q->host;
+    const int s = static_cast<int>(h.calls % 2);
+    char* set = static_cast<char*>(h.ws) + 3 * static_cast<size_t>(s) * field;
+    void* u0 = set;
+    void* ua = set + field;
+    void* ub = set + 2 * field;
+
+    // host -> device: this set's u0 is free once the call two back has finished
+    // simulating and copying out (with steps = 0 its result is u0 itself); if this
+    // input is the previous call's output, wait for that copy too.
+    SY_CUDA(cudaStreamWaitEvent(h.h2d, h.out_done[s], 0));
+    const bool reads_last = (h.last_out[0] && ranges_overlap(host_u0, bytes, h.last_out[0], h.last_out_bytes)) ||
+                            (h.last_out[1] && ranges_overlap(host_u0, bytes, h.last_out[1], h.last_out_bytes));
+    if (reads_last) SY_CUDA(cudaStreamWaitEvent(h.h2d, h.out_done[1 - s], 0));
+    SY_CUDA(cudaMemcpyAsync(u0, host_u0, bytes, cudaMemcpyHostToDevice, h.h2d));
+    SY_CUDA(cudaEventRecord(h.in_done[s], h.h2d));
+
+    // the simulation, on the queue's stream, once the input is in place
+    SY_CUDA(cudaStreamWaitEvent(q->stream, h.in_done[s], 0));
+    RunArgs<sy_stencil_params> a{p, u0, ua, ub, steps, chunks, n_chunks, halo_radius, events != nullptr};
+    const void *pv = nullptr, *cv = nullptr;
+    SY_TRY(graph_run(q, h.graph[s], run_key(a), timed, events != nullptr, issue_run<sy_stencil_params, step2>, &a,
+                     events, &pv, &cv));
+    chunk_order(events, steps, n_chunks);
+    SY_CUDA(cudaEventRecord(h.sim_done[s], q->stream));
+
+    // device -> host
+    SY_CUDA(cudaStreamWaitEvent(h.d2h, h.sim_done[s], 0));
+    SY_CUDA(cudaMemcpyAsync(host_out, cv, bytes, cudaMemcpyDeviceToHost, h.d2h));
+    if (host_prev_out) SY_CUDA(cudaMemcpyAsync(host_prev_out, pv, bytes, cudaMemcpyDeviceToHost, h.d2h));
+    SY_CUDA(cudaEventRecord(h.out_done[s], h.d2h));
+    h.last_out[0] = host_out;
+    h.last_out[1] = host_prev_out;
+    h.last_out_bytes = bytes;
+    ++h.calls;
+    return SY_OK;
+}
 
 extern "C" sy_status sy_wave_run(sy_queue_t qh, const sy_stencil_params* p, const void* u0, void* u_a, void* u_b,
                                  int64_t steps, const sy_chunk* chunks, int n_chunks, int halo_radius,

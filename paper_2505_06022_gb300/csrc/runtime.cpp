@@ -403,7 +403,9 @@ sy_status sy_queue_destroy(sy_queue_t qh) {
     Queue* q = as_queue(qh);
     cudaSetDevice(q->device);
     cudaStreamSynchronize(q->stream);
+    host_run_release(q);
     if (q->run.exec) cudaGraphExecDestroy(q->run.exec);
+    if (q->run3.exec) cudaGraphExecDestroy(q->run3.exec);
     if (q->scratch) cudaFree(q->scratch);
     if (q->d_stamps) cudaFree(q->d_stamps);
     if (q->d_flags) cudaFree(q->d_flags);
@@ -418,6 +420,7 @@ sy_status sy_queue_sync(sy_queue_t qh) {
     SY_TRY(check_queue(qh, &q));
     SY_TRY(use_device(q));
     SY_CUDA(cudaStreamSynchronize(q->stream));
+    SY_TRY(host_run_sync(q));
     unsigned int flags = 0;
     SY_CUDA(cudaMemcpy(&flags, q->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
     if (flags) {
@@ -668,7 +671,6 @@ sy_status sy_stencil_multistep(sy_queue_t qh, const sy_stencil_params* p, int T,
     SY_TRY(check_queue(qh, &q));
     SY_TRY(stencil_param_checks(p));
     if (T != 2 && T != 4) return fail(SY_ERR_INVALID_ARGUMENT, "T = %d not in {2, 4}", T);
-    if (p->radius > 2) return fail(SY_ERR_UNSUPPORTED, "temporal blocking supports radius 1 and 2");
     if (p->ny == 0 || p->nx == 0) {
         if (n_chunks == 0) return SY_OK;
     }
@@ -722,6 +724,14 @@ sy_status sy_stencil_variant_count(int radius, int dtype, int* count) {
     if (radius < 1 || radius > 4 || dtype_size(dtype) == 0)
         return fail(SY_ERR_INVALID_ARGUMENT, "radius %d / dtype %d unsupported", radius, dtype);
     *count = wave_variant_count(radius, dtype);
+    return SY_OK;
+}
+
+sy_status sy_stencil_default_variant(int radius, int dtype, int* variant) {
+    if (!variant) return fail(SY_ERR_NULL_POINTER, "variant is NULL");
+    if (radius < 1 || radius > 4 || dtype_size(dtype) == 0)
+        return fail(SY_ERR_INVALID_ARGUMENT, "bad radius %d or dtype %d", radius, dtype);
+    *variant = wave_default_variant(radius, dtype);
     return SY_OK;
 }
 

@@ -63,7 +63,6 @@ struct Window {
     bool have_energy = false;
 };
 
-// One cached whole-run CUDA graph (sy_wave_run).
 // A cached whole-simulation graph (sy_wave_run, sy_wave3d_run): valid for the
 // exact call it was captured for, identified by the bytes of its arguments.
 struct RunGraph {
@@ -74,6 +73,22 @@ struct RunGraph {
     uint64_t launches = 0;           // kernel launches per replay
     const void* prev_out = nullptr;
     const void* cur_out = nullptr;
+};
+
+struct HostRun {
+    void* ws = nullptr;  // 2 sets x 3 fields of `field` bytes (owned)
+    size_t ws_bytes = 0;
+    size_t field = 0;
+    cudaStream_t h2d = nullptr, d2h = nullptr;  // owned copy streams
+    // per set: host->device copy done, simulation done, device->host copies done
+    cudaEvent_t in_done[2] = {nullptr, nullptr};
+    cudaEvent_t sim_done[2] = {nullptr, nullptr};
+    cudaEvent_t out_done[2] = {nullptr, nullptr};
+    RunGraph graph[2];
+    uint64_t calls = 0;
+    // host ranges the latest call writes (its u^{steps}, u^{steps-1})
+    const void* last_out[2] = {nullptr, nullptr};
+    size_t last_out_bytes = 0;
 };
 
 struct Queue {
@@ -113,7 +128,15 @@ struct Queue {
     size_t scratch_bytes = 0;
     RunGraph run;    // sy_wave_run
     RunGraph run3;   // sy_wave3d_run
+    // sy_wave_run_host: two device work sets (u0, u_a, u_b each) used by alternate
+    // calls, one cached graph per set, and copy streams for each direction, so that
+    // one call's copies overlap the neighbouring calls' simulations.
+    HostRun host;
 };
+
+// Waits for / releases what sy_wave_run_host created on the queue (run.cpp).
+sy_status host_run_sync(Queue* q);
+void host_run_release(Queue* q);
 
 Queue* as_queue(sy_queue_t q);
 sy_status check_queue(sy_queue_t q, Queue** out);
@@ -199,6 +222,8 @@ sy_status stencil_common(Queue* q, const sy_stencil_params* p, const void* u_pre
                          sy_event* chunk_events, bool start, bool reverse = false);
 sy_status stencil_param_checks(const sy_stencil_params* p);
 int wave_variant_count(int radius, int dtype);
+// The variant (1..count) that variant 0 stands for.
+int wave_default_variant(int radius, int dtype);
 bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* tile_cols, int* threads);
 
 // Temporal blocking (tb.cu): T steps per pass for rows [row_begin, row_end).

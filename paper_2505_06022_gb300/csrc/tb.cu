@@ -115,64 +115,76 @@ __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_b
     const int r0 = r_lo + rl * per;
     const int r1 = r0 + per < r_hi ? r0 + per : r_hi;
     if (r0 >= r1) return;  // warp-uniform
-    uint4 win[2 * R + 1];  // rows r - R .. r + R of group g
+    // rolling window of the 2R+1 rows around the current one: row r0 - R + i lives in
+    // win[i % W]; the loop is unrolled by W rows so that every slot index is a
+    // compile-time constant and the window moves without register copies
+    constexpr int W = 2 * R + 1;
+    uint4 win[W];
 #pragma unroll
     for (int d = 0; d < 2 * R; ++d) win[d] = X[(r0 - R + d) * NG + g];
-    for (int r = r0; r < r1; ++r) {
-        win[2 * R] = X[(r + R) * NG + g];
-        const uint4 pv = Y[r * NG + g];
-        float ext[V + 2 * R];                // columns g*V - R .. g*V + V + R - 1
+    const uint4* xrow = X + (r0 + R) * NG + g;  // row r + R of group g
+    const uint4* yrow = Y + r0 * NG + g;
+    uint4* orow = Y + r0 * NG + g;
+    for (int rb = r0; rb < r1; rb += W) {
 #pragma unroll
-        for (int e = 0; e < V; ++e) ext[R + e] = Tr::elem(win[R], e);
+        for (int j = 0; j < W; ++j) {
+            const int r = rb + j;
+            if (r >= r1) break;
+            win[(j + 2 * R) % W] = xrow[(r - r0) * NG];
+            const uint4 pv = yrow[(r - r0) * NG];
+            const uint4& cen = win[(j + R) % W];
+            float ext[V + 2 * R];  // columns g*V - R .. g*V + V + R - 1
 #pragma unroll
-        for (int d = 1; d <= R; ++d) {
-            const float from_left = __shfl_up_sync(wave::kFull, ext[R + V - d], 1);
-            const float from_right = __shfl_down_sync(wave::kFull, ext[R + d - 1], 1);
-            ext[R - d] = g == 0 ? 0.0f : from_left;
-            ext[R + V - 1 + d] = g == 31 ? 0.0f : from_right;
-        }
-        float out[V];
-        if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions (packed FP32 adds)
+            for (int e = 0; e < V; ++e) ext[R + e] = Tr::elem(cen, e);
 #pragma unroll
-            for (int e = 0; e < V; e += 2) {
-                float2 vert[R], horz[R];
+            for (int d = 1; d <= R; ++d) {
+                const float from_left = __shfl_up_sync(wave::kFull, ext[R + V - d], 1);
+                const float from_right = __shfl_down_sync(wave::kFull, ext[R + d - 1], 1);
+                ext[R - d] = g == 0 ? 0.0f : from_left;
+                ext[R + V - 1 + d] = g == 31 ? 0.0f : from_right;
+            }
+            float out[V];
+            if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions (packed FP32 adds)
 #pragma unroll
-                for (int d = 1; d <= R; ++d) {
-                    vert[d - 1] = wave::add2_rn(make_float2(Tr::elem(win[R - d], e), Tr::elem(win[R - d], e + 1)),
-                                                make_float2(Tr::elem(win[R + d], e), Tr::elem(win[R + d], e + 1)));
-                    horz[d - 1] = wave::add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]),
-                                                make_float2(ext[R + e + d], ext[R + e + 1 + d]));
+                for (int e = 0; e < V; e += 2) {
+                    float2 vert[R], horz[R];
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        const uint4& wu = win[(j + R - d) % W];
+                        const uint4& wd = win[(j + R + d) % W];
+                        vert[d - 1] = wave::add2_rn(make_float2(Tr::elem(wu, e), Tr::elem(wu, e + 1)),
+                                                    make_float2(Tr::elem(wd, e), Tr::elem(wd, e + 1)));
+                        horz[d - 1] = wave::horz2<R>(ext, e, d);
+                    }
+                    const float2 o = wave::update2<R, false>(make_float2(ext[R + e], ext[R + e + 1]),
+                                                             make_float2(Tr::elem(pv, e), Tr::elem(pv, e + 1)), vert,
+                                                             horz, c2);
+                    out[e] = o.x;
+                    out[e + 1] = o.y;
                 }
-                const float2 o = wave::update2<R, false>(make_float2(ext[R + e], ext[R + e + 1]),
-                                                         make_float2(Tr::elem(pv, e), Tr::elem(pv, e + 1)), vert,
-                                                         horz, c2);
-                out[e] = o.x;
-                out[e + 1] = o.y;
-            }
-        } else {
+            } else {
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-                float vert[R], horz[R];
+                for (int e = 0; e < V; ++e) {
+                    float vert[R], horz[R];
 #pragma unroll
-                for (int d = 1; d <= R; ++d) {
-                    vert[d - 1] = __fadd_rn(Tr::elem(win[R - d], e), Tr::elem(win[R + d], e));
-                    horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                    for (int d = 1; d <= R; ++d) {
+                        vert[d - 1] = __fadd_rn(Tr::elem(win[(j + R - d) % W], e), Tr::elem(win[(j + R + d) % W], e));
+                        horz[d - 1] = __fadd_rn(ext[R + e - d], ext[R + e + d]);
+                    }
+                    out[e] = wave::update<R, false>(ext[R + e], Tr::elem(pv, e), vert, horz, c2);
                 }
-                out[e] = wave::update<R, false>(ext[R + e], Tr::elem(pv, e), vert, horz, c2);
             }
-        }
-        if (!interior) {  // ghosts outside the grid stay zero
-            const int64_t gy = static_cast<int64_t>(y_buf0) + r;
-            const bool row_in = gy >= 0 && gy < ny;
+            if (!interior) {  // ghosts outside the grid stay zero
+                const int64_t gy = static_cast<int64_t>(y_buf0) + r;
+                const bool row_in = gy >= 0 && gy < ny;
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const int64_t gx = static_cast<int64_t>(x_buf0) + g * V + e;
-                if (!row_in || gx < 0 || gx >= nx) out[e] = 0.0f;
+                for (int e = 0; e < V; ++e) {
+                    const int64_t gx = static_cast<int64_t>(x_buf0) + g * V + e;
+                    if (!row_in || gx < 0 || gx >= nx) out[e] = 0.0f;
+                }
             }
+            orow[(r - r0) * NG] = Tr::pack(out);
         }
-        Y[r * NG + g] = Tr::pack(out);
-#pragma unroll
-        for (int d = 0; d < 2 * R; ++d) win[d] = win[d + 1];
     }
 }
 
@@ -356,7 +368,9 @@ sy_status launch_r(Queue* q, const TBLaunch& w) {
     switch (w.radius) {
         case 1: return launch_tb<S, 1, T>(q, w);
         case 2: return launch_tb<S, 2, T>(q, w);
-        default: return fail(SY_ERR_UNSUPPORTED, "temporal blocking supports radius 1 and 2 (asked %d)", w.radius);
+        case 3: return launch_tb<S, 3, T>(q, w);
+        case 4: return launch_tb<S, 4, T>(q, w);
+        default: return fail(SY_ERR_UNSUPPORTED, "temporal blocking supports radius 1 to 4 (asked %d)", w.radius);
     }
 }
 

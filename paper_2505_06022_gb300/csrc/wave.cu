@@ -51,7 +51,7 @@ int kernel_occupancy(const void* fn, int threads) { return occupancy(fn, threads
 bool launch_overlap_enabled() { return pdl_enabled(); }
 
 sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn scalar_fn, int tile_rows,
-                       int threads, int V, size_t esize) {
+                       int threads, int span, size_t esize, Form form) {
     const int64_t rows = w.row_end - w.row_begin;
     if (rows <= 0 || w.nx == 0) return SY_OK;
     Args a;
@@ -71,9 +71,9 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
     const bool vec_ok = aligned(w.u_cur, 16) && aligned(w.u_next, 16) && (w.start || aligned(w.u_prev, 16)) &&
                         (a.pitch_bytes % 16) == 0;
     if (vec_ok) {
-        const int64_t span = 32 * static_cast<int64_t>(V);
         a.tiles_x = (w.nx + span - 1) / span;
         a.tiles = a.tiles_x * ((rows + tile_rows - 1) / tile_rows);
+        (void)form;
         const int64_t wpb = threads / 32;
         int64_t blocks = (a.tiles + wpb - 1) / wpb;
         const int64_t cap = static_cast<int64_t>(occupancy(reinterpret_cast<const void*>(vec_fn), threads)) * q->sm_count;
@@ -112,26 +112,39 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
 
 }  // namespace wave
 
-int wave_variant_count(int, int) { return wave::kVariants; }
+int wave_variant_count(int, int dtype) { return dtype == SY_F32 ? wave::kVariants32 : wave::kVariants16; }
+
+// Default per storage type and radius: the fastest variant of an exhaustive sweep at
+// 8192 x 8192 on GB300 (128-thread blocks; rows per tile grow with the radius, where
+// the halo re-read factor (rows + 2r) / rows matters).
+int wave_default_variant(int radius, int dtype) {
+    static const int kDefault[2][4] = {{1, 2, 3, 2}, {2, 2, 3, 3}};
+    return kDefault[dtype == SY_F32 ? 0 : 1][radius - 1];
+}
 
 bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* tile_cols, int* threads) {
-    if (radius < 1 || radius > 4 || dtype_size(dtype) == 0 || variant < 0 || variant > wave::kVariants)
+    if (radius < 1 || radius > 4 || dtype_size(dtype) == 0 || variant < 0 ||
+        variant > wave_variant_count(radius, dtype))
         return false;
-    int rows, thr;
-    if (variant == 0) {
-        // Default per storage type and radius: the fastest tile of an exhaustive
-        // sweep at 8192 x 8192 on GB300 (128-thread blocks; rows per tile grow
-        // with the radius, where the halo re-read factor (rows + 2r) / rows matters).
-        static const int kDefaultRows[2][4] = {{2, 4, 8, 4}, {4, 4, 8, 8}};
-        rows = kDefaultRows[dtype == SY_F32 ? 0 : 1][radius - 1];
-        thr = 128;
-    } else {
+    if (variant == 0) variant = wave_default_variant(radius, dtype);
+    const int V = static_cast<int>(16 / dtype_size(dtype));
+    int rows, thr, cols;
+    if (variant <= 8) {
         rows = wave::kTileRows[(variant - 1) % 4];
         thr = wave::kBlockThreads[(variant - 1) / 4];
+        cols = 32 * V;
+    } else if (variant <= 12) {  // halo lanes: 30 of a warp's 32 vectors are output
+        rows = wave::kHlRows[(variant - 9) % 2];
+        thr = wave::kBlockThreads[(variant - 9) / 2];
+        cols = 30 * V;
+    } else {  // narrow halo lanes (16-bit): 30 vectors of 4 elements
+        rows = wave::kHlRows[variant - 13];
+        thr = 128;
+        cols = 30 * 4;
     }
     if (tile_rows) *tile_rows = rows;
     if (threads) *threads = thr;
-    if (tile_cols) *tile_cols = 32 * static_cast<int>(16 / dtype_size(dtype));
+    if (tile_cols) *tile_cols = cols;
     return true;
 }
 
@@ -139,10 +152,12 @@ sy_status launch_wave(Queue* q, const WaveLaunch& w) {
     int tile_rows = 0, threads = 0;
     if (!wave_variant_info(w.radius, w.dtype, w.variant, &tile_rows, nullptr, &threads))
         return fail(SY_ERR_INVALID_ARGUMENT, "bad stencil variant %d", w.variant);
+    const int v = w.variant == 0 ? wave_default_variant(w.radius, w.dtype) : w.variant;
+    const wave::Form form = v >= 13 ? wave::Form::Narrow : v >= 9 ? wave::Form::Halo : wave::Form::Tile;
     switch (w.dtype) {
-        case SY_F32: return wave::launch_f32(q, w, tile_rows, threads);
-        case SY_BF16: return wave::launch_bf16(q, w, tile_rows, threads);
-        case SY_F16: return wave::launch_f16(q, w, tile_rows, threads);
+        case SY_F32: return wave::launch_f32(q, w, tile_rows, threads, form);
+        case SY_BF16: return wave::launch_bf16(q, w, tile_rows, threads, form);
+        case SY_F16: return wave::launch_f16(q, w, tile_rows, threads, form);
     }
     return fail(SY_ERR_INVALID_ARGUMENT, "unknown dtype %d", w.dtype);
 }
@@ -183,8 +198,16 @@ __global__ void __launch_bounds__(kThreads) energy_partials_kernel(EArgs a, doub
     double kin = 0.0, pot = 0.0;
     const int64_t total = a.ny * a.nx;
     const int64_t stride = static_cast<int64_t>(kEnergyBlocks) * kThreads;
-    for (int64_t p = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; p < total; p += stride) {
-        const int64_t i = p / a.nx, j = p - (p / a.nx) * a.nx;
+    // point p = i * nx + j; the thread's points advance by `stride`, so (i, j) moves by
+    // (di, dj) per trip: one division per thread instead of two per point
+    const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    const int64_t di = stride / a.nx, dj = stride - di * a.nx;
+    int64_t i = p0 / a.nx, j = p0 - i * a.nx;
+    for (int64_t p = p0; p < total; p += stride, i += di, j += dj) {
+        if (j >= a.nx) {
+            j -= a.nx;
+            ++i;
+        }
         const double un = at(a.u_new, i, j), uo = at(a.u_old, i, j);
         double lap = __dmul_rn(c0x2_64<R>(), uo);
 #pragma unroll
@@ -296,6 +319,9 @@ sy_status launch_energy_final(cudaStream_t stream, const double* partials, doubl
 // cudaGetSymbolAddress returns for the current device, looked up once per device.
 constexpr int kStaticEnergyDoubles = 2 * kEnergyBlocks;
 static __device__ __align__(256) double g_energy_partials_static[kStaticEnergyDoubles];
+// The reduction's shape is fixed: it always writes 2 x kEnergyBlocks partial sums,
+// whatever the grid size, so the array's size is checked once, here.
+static_assert(2 * kEnergyBlocks <= kStaticEnergyDoubles, "static energy scratch too small for the reduction");
 
 namespace {
 constexpr int kMaxDevices = 64;
@@ -337,11 +363,6 @@ extern "C" sy_status sy_wave_energy_static(void* cuda_stream, const sy_stencil_p
     if (!out3) return fail(SY_ERR_NULL_POINTER, "out3 is NULL");
     if (reinterpret_cast<uintptr_t>(out3) % alignof(double))
         return fail(SY_ERR_INVALID_ARGUMENT, "out3 must be 8-byte aligned");
-    // The reduction always writes 2 * kEnergyBlocks partial sums (its fixed shape).
-    const int64_t need = 2 * static_cast<int64_t>(kEnergyBlocks);
-    if (need > kStaticEnergyDoubles)
-        return fail(SY_ERR_INVALID_ARGUMENT, "the reduction needs %lld partial sums, the static scratch holds %d",
-                    static_cast<long long>(need), kStaticEnergyDoubles);
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     if (p->ny == 0 || p->nx == 0) {
         SY_CUDA(cudaMemsetAsync(out3, 0, 3 * sizeof(double), stream));

@@ -84,8 +84,7 @@ __device__ __forceinline__ float2 update3_2(float2 u, float2 up, const float2 (&
     for (int d = 1; d <= R; ++d)
         acc = add2_rn(acc, mul2_scalar(wk<R>(d), add2_rn(add2_rn(vert[d - 1], horz[d - 1]), depth[d - 1])));
     if (START) return add2_rn(u, mul2_scalar(c2, acc));
-    const float2 inertia = add2_rn(mul2_scalar(2.0f, u), make_float2(-up.x, -up.y));
-    return add2_rn(inertia, mul2_scalar(c2, acc));
+    return add2_rn(wave::inertia2(u, up), mul2_scalar(c2, acc));
 }
 
 // One row of a lane's V points: c is the row itself, up[d-1] / dn[d-1] the rows d
@@ -117,8 +116,7 @@ __device__ __forceinline__ void row_update(const uint4& c, const uint4 (&up)[R],
             for (int d = 1; d <= R; ++d) {
                 vert[d - 1] = wave::add2_rn(make_float2(T::elem(up[d - 1], e), T::elem(up[d - 1], e + 1)),
                                             make_float2(T::elem(dn[d - 1], e), T::elem(dn[d - 1], e + 1)));
-                horz[d - 1] = wave::add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]),
-                                            make_float2(ext[R + e + d], ext[R + e + 1 + d]));
+                horz[d - 1] = wave::horz2<R>(ext, e, d);
                 depth[d - 1] = wave::add2_rn(make_float2(T::elem(zm[d - 1], e), T::elem(zm[d - 1], e + 1)),
                                              make_float2(T::elem(zp[d - 1], e), T::elem(zp[d - 1], e + 1)));
             }

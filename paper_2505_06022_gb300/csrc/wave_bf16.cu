@@ -5,8 +5,8 @@
 namespace sy {
 namespace wave {
 
-sy_status launch_bf16(Queue* q, const WaveLaunch& w, int tile_rows, int threads) {
-    return launch_dtype<__nv_bfloat16>(q, w, tile_rows, threads);
+sy_status launch_bf16(Queue* q, const WaveLaunch& w, int tile_rows, int threads, Form form) {
+    return launch_dtype<__nv_bfloat16>(q, w, tile_rows, threads, form);
 }
 
 }  // namespace wave

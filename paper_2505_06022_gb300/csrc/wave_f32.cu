@@ -5,8 +5,8 @@
 namespace sy {
 namespace wave {
 
-sy_status launch_f32(Queue* q, const WaveLaunch& w, int tile_rows, int threads) {
-    return launch_dtype<float>(q, w, tile_rows, threads);
+sy_status launch_f32(Queue* q, const WaveLaunch& w, int tile_rows, int threads, Form form) {
+    return launch_dtype<float>(q, w, tile_rows, threads, form);
 }
 
 }  // namespace wave

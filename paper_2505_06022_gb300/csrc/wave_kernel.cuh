@@ -88,10 +88,34 @@ __device__ __forceinline__ void set_word(uint4& r, int i, uint32_t v) {
     else if (i == 2) r.z = v;
     else r.w = v;
 }
+__device__ __forceinline__ uint32_t word(const uint2& r, int i) { return i == 0 ? r.x : r.y; }
+__device__ __forceinline__ void set_word(uint2& r, int i, uint32_t v) {
+    if (i == 0) r.x = v;
+    else r.y = v;
+}
+
+// 16- and 8-byte global accesses of one lane's vector.
+struct Vec16 {
+    using T = uint4;
+    __device__ static __forceinline__ uint4 zero() { return make_uint4(0u, 0u, 0u, 0u); }
+    __device__ static __forceinline__ uint4 ld(const char* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+    __device__ static __forceinline__ uint4 ld_cs(const char* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
+    __device__ static __forceinline__ uint4 ld_cg(const char* p) { return __ldcg(reinterpret_cast<const uint4*>(p)); }
+    __device__ static __forceinline__ void st_cs(char* p, uint4 v) { __stcs(reinterpret_cast<uint4*>(p), v); }
+};
+struct Vec8 {
+    using T = uint2;
+    __device__ static __forceinline__ uint2 zero() { return make_uint2(0u, 0u); }
+    __device__ static __forceinline__ uint2 ld(const char* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
+    __device__ static __forceinline__ uint2 ld_cs(const char* p) { return __ldcs(reinterpret_cast<const uint2*>(p)); }
+    __device__ static __forceinline__ uint2 ld_cg(const char* p) { return __ldcg(reinterpret_cast<const uint2*>(p)); }
+    __device__ static __forceinline__ void st_cs(char* p, uint2 v) { __stcs(reinterpret_cast<uint2*>(p), v); }
+};
 
 template <>
 struct Traits<float> {
     static constexpr int V = 4;
+    using Mem = Vec16;
     __device__ static __forceinline__ float elem(const uint4& r, int e) { return __uint_as_float(word(r, e)); }
     // zero elements e >= nvalid
     __device__ static __forceinline__ void mask(uint4& r, int nvalid) {
@@ -104,6 +128,9 @@ struct Traits<float> {
                           __float_as_uint(v[3]));
     }
     __device__ static __forceinline__ float load1(const char* p) { return __ldg(reinterpret_cast<const float*>(p)); }
+    __device__ static __forceinline__ float load1_cg(const char* p) {
+        return __ldcg(reinterpret_cast<const float*>(p));
+    }
     __device__ static __forceinline__ float load1_cs(const char* p) {
         return __ldcs(reinterpret_cast<const float*>(p));
     }
@@ -113,6 +140,7 @@ struct Traits<float> {
 template <>
 struct Traits<__nv_bfloat16> {
     static constexpr int V = 8;
+    using Mem = Vec16;
     __device__ static __forceinline__ float elem(const uint4& r, int e) {
         uint32_t w = word(r, e >> 1);
         return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
@@ -136,6 +164,9 @@ struct Traits<__nv_bfloat16> {
     __device__ static __forceinline__ float load1(const char* p) {
         return __uint_as_float(static_cast<uint32_t>(__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
     }
+    __device__ static __forceinline__ float load1_cg(const char* p) {
+        return __uint_as_float(static_cast<uint32_t>(__ldcg(reinterpret_cast<const unsigned short*>(p))) << 16);
+    }
     __device__ static __forceinline__ float load1_cs(const char* p) {
         return __uint_as_float(static_cast<uint32_t>(__ldcs(reinterpret_cast<const unsigned short*>(p))) << 16);
     }
@@ -147,6 +178,7 @@ struct Traits<__nv_bfloat16> {
 template <>
 struct Traits<__half> {
     static constexpr int V = 8;
+    using Mem = Vec16;
     __device__ static __forceinline__ float elem(const uint4& r, int e) {
         uint32_t w = word(r, e >> 1);
         unsigned short h = static_cast<unsigned short>((e & 1) ? (w >> 16) : (w & 0xffffu));
@@ -171,12 +203,48 @@ struct Traits<__half> {
     __device__ static __forceinline__ float load1(const char* p) {
         return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
     }
+    __device__ static __forceinline__ float load1_cg(const char* p) {
+        return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+    }
     __device__ static __forceinline__ float load1_cs(const char* p) {
         return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p))));
     }
     __device__ static __forceinline__ void store1(char* p, float v) {
         *reinterpret_cast<unsigned short*>(p) = static_cast<unsigned short>(bits(v));
     }
+};
+
+// 16-bit storage, 4 elements (8 bytes) a lane: the narrow form of the tile kernel.
+// Same element conversions as Traits<S>; half the registers per row of a tile.
+template <typename S>
+struct Narrow {
+    static_assert(sizeof(S) == 2, "the narrow form is for 16-bit storage");
+    static constexpr int V = 4;
+    using Mem = Vec8;
+    __device__ static __forceinline__ float elem(const uint2& r, int e) {
+        // element e is half (e & 1) of word e >> 1: the 16-byte form's conversion of that word
+        return Traits<S>::elem(make_uint4(word(r, e >> 1), 0u, 0u, 0u), e & 1);
+    }
+    __device__ static __forceinline__ void mask(uint2& r, int nvalid) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            if (e >= nvalid) set_word(r, e >> 1, word(r, e >> 1) & ((e & 1) ? 0x0000ffffu : 0xffff0000u));
+    }
+    __device__ static __forceinline__ uint2 pack(const float (&v)[V]) {
+        return make_uint2(Traits<S>::pair(v[0], v[1]), Traits<S>::pair(v[2], v[3]));
+    }
+    __device__ static __forceinline__ float load1(const char* p) { return Traits<S>::load1(p); }
+    __device__ static __forceinline__ float load1_cg(const char* p) { return Traits<S>::load1_cg(p); }
+    __device__ static __forceinline__ void store1(char* p, float v) { Traits<S>::store1(p, v); }
+};
+
+template <typename S, bool NARROW>
+struct TileTraits {
+    using type = Traits<S>;
+};
+template <typename S>
+struct TileTraits<S, true> {
+    using type = Narrow<S>;
 };
 
 struct Args {
@@ -225,9 +293,50 @@ __device__ __forceinline__ float2 add2_rn(float2 a, float2 b) {
     return d;
 }
 
-__device__ __forceinline__ float2 mul2_scalar(float w, float2 x) {
-    return make_float2(__fmul_rn(w, x.x), __fmul_rn(w, x.y));
+// a - b for two points (sub.rn.f32x2: each half one IEEE round-to-nearest
+// subtraction, bit-identical to __fsub_rn).
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
 }
+
+// w * x for two points as one packed fused multiply-add with addend -0:
+// fma.rn(w, x, -0) rounds w x once, and adding -0 changes no value (not even the
+// sign of a zero product), so each half equals __fmul_rn(w, x) bit for bit.  A
+// packed mul.rn.f32x2 feeding a packed add came out fused into one rounding despite
+// the explicit rounding modes (16-bit steps at radius 2-4, whose weights make
+// inexact products, stopped matching the mirror; radius 1, whose products are exact,
+// still matched); an fma has no multiply left to fuse.
+__device__ __forceinline__ float2 mul2_scalar(float w, float2 x) {
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\t"
+        "mov.b64 pa, {%2, %2};\n\tmov.b64 pb, {%3, %4};\n\tmov.b64 pc, {%5, %5};\n\t"
+        "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(w), "f"(x.x), "f"(x.y), "f"(-0.0f));
+    return d;
+}
+
+// Horizontal pair sums (u_{j-d} + u_{j+d}) of the points j = e, e+1 from a row held as
+// ext[m] = column x0 - R + m.  A packed add takes its operands from aligned register
+// pairs; the pair (ext[R+e-d], ext[R+e+1-d]) starts at an even index only when R - d is
+// even, so for odd R - d the two sums are scalar additions (same rounding, no register
+// copies to re-pair the operands).
+template <int R, int N>
+__device__ __forceinline__ float2 horz2(const float (&ext)[N], int e, int d) {
+    if ((R - d) % 2 == 0)
+        return add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]), make_float2(ext[R + e + d], ext[R + e + 1 + d]));
+    return make_float2(__fadd_rn(ext[R + e - d], ext[R + e + d]), __fadd_rn(ext[R + e + 1 - d], ext[R + e + 1 + d]));
+}
+
+// 2u - u_prev for two points: 2u = u + u exactly (a power-of-two scaling), and the
+// subtraction as in update(); bit-identical to (2 * u) - up evaluated per point.
+__device__ __forceinline__ float2 inertia2(float2 u, float2 up) { return sub2_rn(add2_rn(u, u), up); }
 
 template <int R, bool START>
 __device__ __forceinline__ float2 update2(float2 u, float2 up, const float2 (&vert)[R], const float2 (&horz)[R],
@@ -236,8 +345,28 @@ __device__ __forceinline__ float2 update2(float2 u, float2 up, const float2 (&ve
 #pragma unroll
     for (int d = 1; d <= R; ++d) acc = add2_rn(acc, mul2_scalar(wk<R>(d), add2_rn(vert[d - 1], horz[d - 1])));
     if (START) return add2_rn(u, mul2_scalar(c2, acc));
-    const float2 inertia = add2_rn(mul2_scalar(2.0f, u), make_float2(-up.x, -up.y));
-    return add2_rn(inertia, mul2_scalar(c2, acc));
+    return add2_rn(inertia2(u, up), mul2_scalar(c2, acc));
+}
+
+// Loads of a tile's vectors.  Within one launch u^n is never written, so it is read
+// through the non-coherent path and u^{n-1} streamed; a kernel that steps several
+// times in one launch (CG = true) writes what its later steps read, so it loads
+// through L2 only (ld.global.cg), which a grid-wide barrier with fences makes
+// coherent.
+template <typename M, bool CG>
+__device__ __forceinline__ typename M::T load_cur_vec(const char* p) {
+    return CG ? M::ld_cg(p) : M::ld(p);
+}
+template <typename M, bool CG>
+__device__ __forceinline__ typename M::T load_prev_vec(const char* p) {
+    return CG ? M::ld_cg(p) : M::ld_cs(p);
+}
+
+// Columns of output per warp tile: 32 lanes x V, or, with halo lanes, the 30 inner
+// lanes' (lanes 0 and 31 only load the columns beside the tile).
+template <typename S, bool HL, bool NARROW = false>
+__host__ __device__ constexpr int tile_span() {
+    return (HL ? 30 : 32) * TileTraits<S, NARROW>::type::V;
 }
 
 // One warp's tile: columns [(tx*32 + lane)*V, +V) of each lane, rows
@@ -245,40 +374,50 @@ __device__ __forceinline__ float2 update2(float2 u, float2 up, const float2 (&ve
 // out as in `a`.  CHECK = false is the interior form, valid when every row the
 // tile reads or writes lies inside the grid and the chunk's range mapper and
 // every lane's V columns lie inside [0, nx): no per-row predicates then.
-template <typename S, int R, int RY, bool START, bool CHECK>
+// HL (halo lanes): lane l covers columns [(tx*30 + l - 1)*V, +V); the outer lanes 0
+// and 31 hold the columns beside the tile's 30*V and store nothing, so the inner
+// lanes take every horizontal neighbour by a shuffle and no lane keeps edge
+// vectors in registers.  A lane's columns outside [0, nx) read as zero (the
+// Dirichlet ghosts).
+// NARROW: 16-bit storage with 4 elements (8 bytes) a lane instead of 8, a warp
+// covering 128 columns (with halo lanes: 120): half the registers per tile row.
+template <typename S, int R, int RY, bool START, bool CHECK, bool HL = false, bool CG = false, bool NARROW = false>
 __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_t ty, int lane) {
-    using T = Traits<S>;
+    using T = typename TileTraits<S, NARROW>::type;
+    using M = typename T::Mem;
+    using VecT = typename M::T;
     constexpr int V = T::V;
     constexpr int64_t ES = sizeof(S);
     static_assert(R <= V, "radius must not exceed the vector width");
     const int64_t pb = a.pitch_bytes;
-    const int64_t x0 = (tx * 32 + lane) * V;
+    const int64_t x0 = HL ? (tx * 30 + lane - 1) * V : (tx * 32 + lane) * V;
     const int64_t y0 = a.row_begin + ty * RY;
-    const bool col_in = !CHECK || x0 < a.nx;
+    const bool col_in = !CHECK || (x0 < a.nx && (!HL || x0 >= 0));
     const int nvalid = !CHECK ? V : (col_in ? static_cast<int>(a.nx - x0 < V ? a.nx - x0 : V) : 0);
+    const bool stores = !HL || (lane >= 1 && lane <= 30);
     const char* cur_base = a.u_cur + (y0 - R) * pb + x0 * ES;  // row y0 - R
     const char* prev_base = a.u_prev + y0 * pb + x0 * ES;
 
     // ---- loads: everything for the tile is in flight before any arithmetic ----
-    uint4 cur[RY + 2 * R];
+    VecT cur[RY + 2 * R];
 #pragma unroll
     for (int k = 0; k < RY + 2 * R; ++k) {
-        cur[k] = make_uint4(0u, 0u, 0u, 0u);
+        cur[k] = M::zero();
         if (!CHECK) {
-            cur[k] = __ldg(reinterpret_cast<const uint4*>(cur_base + k * pb));
+            cur[k] = load_cur_vec<M, CG>(cur_base + k * pb);
         } else {
             const int64_t row = y0 - R + k;
             if (col_in && row >= 0 && row < a.ny && row < a.row_end + R)
-                cur[k] = __ldg(reinterpret_cast<const uint4*>(cur_base + k * pb));
+                cur[k] = load_cur_vec<M, CG>(cur_base + k * pb);
         }
     }
-    uint4 prev[START ? 1 : RY];
+    VecT prev[START ? 1 : RY];
     if (!START) {
 #pragma unroll
         for (int k = 0; k < RY; ++k) {
-            prev[k] = make_uint4(0u, 0u, 0u, 0u);
+            prev[k] = M::zero();
             if (!CHECK || (col_in && y0 + k < a.row_end))
-                prev[k] = __ldcs(reinterpret_cast<const uint4*>(prev_base + k * pb));
+                prev[k] = load_prev_vec<M, CG>(prev_base + k * pb);
         }
     }
     // warp edges: lane 0 fetches the columns left of the warp, lane 31 those right of
@@ -287,10 +426,12 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
     // holds registers for; the 8-point vectors' unpacked arithmetic needs them more).
     // Measured at 8192^2 with 4-row tiles: BF16 +1 %, FP16 +5 %; at radius 3-4 the R
     // scalar loads per row cost more than they save (10-26 % slower with 8-row tiles).
-    constexpr bool kScalarEdge = sizeof(S) == 2 && R == 1;
-    uint4 edge[kScalarEdge ? 1 : RY];
+    constexpr bool kScalarEdge = !HL && sizeof(S) == 2 && R == 1;
+    VecT edge[(kScalarEdge || HL) ? 1 : RY];
     float edge1[kScalarEdge ? RY : 1][R];  // edge1[k][d-1]: column x0 - d (lane 0) or x0 + V - 1 + d (lane 31)
-    if constexpr (kScalarEdge) {
+    if constexpr (HL) {
+        // no edge loads: lanes 0 and 31 are the edges
+    } else if constexpr (kScalarEdge) {
         const bool edge_lane = lane == 0 || lane == 31;
         const int64_t col0 = lane == 0 ? x0 - 1 : x0 + V;
         const int64_t step = lane == 0 ? -1 : 1;
@@ -302,7 +443,7 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
                 const int64_t col = col0 + (d - 1) * step;
                 edge1[k][d - 1] = 0.0f;
                 if (edge_lane && (!CHECK || y0 + k < a.row_end) && col >= 0 && col < a.nx)
-                    edge1[k][d - 1] = T::load1(erow + k * pb + col * ES);
+                    edge1[k][d - 1] = CG ? T::load1_cg(erow + k * pb + col * ES) : T::load1(erow + k * pb + col * ES);
             }
     } else {
         const int64_t xe = lane == 0 ? x0 - V : x0 + V;
@@ -311,9 +452,9 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
         const char* edge_base = a.u_cur + y0 * pb + xe * ES;
 #pragma unroll
         for (int k = 0; k < RY; ++k) {
-            edge[k] = make_uint4(0u, 0u, 0u, 0u);
+            edge[k] = M::zero();
             if (edge_lane && (!CHECK || y0 + k < a.row_end))
-                edge[k] = __ldg(reinterpret_cast<const uint4*>(edge_base + k * pb));
+                edge[k] = load_cur_vec<M, CG>(edge_base + k * pb);
         }
         if (lane == 31 && edge_valid < V) {
 #pragma unroll
@@ -337,7 +478,10 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
         for (int d = 1; d <= R; ++d) {
             float from_left = __shfl_up_sync(kFull, ext[R + V - d], 1);
             float from_right = __shfl_down_sync(kFull, ext[R + d - 1], 1);
-            if constexpr (kScalarEdge) {
+            if constexpr (HL) {  // lanes 0 and 31 get their own values back: unused, they store nothing
+                ext[R - d] = from_left;
+                ext[R + V - 1 + d] = from_right;
+            } else if constexpr (kScalarEdge) {
                 ext[R - d] = lane == 0 ? edge1[k][d - 1] : from_left;
                 ext[R + V - 1 + d] = lane == 31 ? edge1[k][d - 1] : from_right;
             } else {
@@ -354,8 +498,7 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
                 for (int d = 1; d <= R; ++d) {
                     vert[d - 1] = add2_rn(make_float2(T::elem(cur[k + R - d], e), T::elem(cur[k + R - d], e + 1)),
                                           make_float2(T::elem(cur[k + R + d], e), T::elem(cur[k + R + d], e + 1)));
-                    horz[d - 1] = add2_rn(make_float2(ext[R + e - d], ext[R + e + 1 - d]),
-                                          make_float2(ext[R + e + d], ext[R + e + 1 + d]));
+                    horz[d - 1] = horz2<R>(ext, e, d);
                 }
                 const float2 up = START ? make_float2(0.0f, 0.0f)
                                         : make_float2(T::elem(prev[START ? 0 : k], e), T::elem(prev[START ? 0 : k], e + 1));
@@ -376,10 +519,10 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
                 out[e] = update<R, START>(ext[R + e], up, vert, horz, a.c2);
             }
         }
-        if (!CHECK || (col_in && y0 + k < a.row_end)) {
+        if (stores && (!CHECK || (col_in && y0 + k < a.row_end))) {
             char* dst = next_base + k * pb;
             if (!CHECK || nvalid == V) {
-                __stcs(reinterpret_cast<uint4*>(dst), T::pack(out));
+                M::st_cs(dst, T::pack(out));
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e)
@@ -391,20 +534,20 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
 
 // Interior tiles (all rows in the grid and the range mapper, all lanes' columns
 // in [0, nx)) take the predicate-free form.
-template <typename S, int R, int RY, bool START>
+template <typename S, int R, int RY, bool START, bool HL = false, bool CG = false, bool NARROW = false>
 __device__ __forceinline__ void wave_tile(const Args& a, int64_t tx, int64_t ty, int lane) {
-    constexpr int V = Traits<S>::V;
+    constexpr int V = TileTraits<S, NARROW>::type::V;
     const int64_t y0 = a.row_begin + ty * RY;
     const int64_t row_hi = a.row_end + R < a.ny ? a.row_end + R : a.ny;
-    const bool interior = (y0 - R >= 0) && (y0 + RY + R <= row_hi) && (y0 + RY <= a.row_end) &&
-                          ((tx + 1) * 32 * V <= a.nx);
-    if (interior) wave_tile_impl<S, R, RY, START, false>(a, tx, ty, lane);
-    else wave_tile_impl<S, R, RY, START, true>(a, tx, ty, lane);
+    const bool cols_in = HL ? (tx > 0 && (tx * 30 + 31) * V <= a.nx) : ((tx + 1) * 32 * V <= a.nx);
+    const bool interior = (y0 - R >= 0) && (y0 + RY + R <= row_hi) && (y0 + RY <= a.row_end) && cols_in;
+    if (interior) wave_tile_impl<S, R, RY, START, false, HL, CG, NARROW>(a, tx, ty, lane);
+    else wave_tile_impl<S, R, RY, START, true, HL, CG, NARROW>(a, tx, ty, lane);
 }
 
 // REV = true visits the tiles in reverse order (tile t as tiles - 1 - t): the chunk is
 // swept bottom to top, with the same results.
-template <typename S, int R, int RY, bool START, bool REV>
+template <typename S, int R, int RY, bool START, bool REV, bool HL = false, bool NARROW = false>
 __device__ __forceinline__ void wave_vec_body(const Args& a) {
     if (a.pdl == 1) griddep_wait();
     if (a.pdl) griddep_launch_dependents();
@@ -419,7 +562,7 @@ __device__ __forceinline__ void wave_vec_body(const Args& a) {
     int64_t ty = first / a.tiles_x, tx = first - ty * a.tiles_x;
     const int64_t dy = nwarps / a.tiles_x, dx = nwarps - dy * a.tiles_x;
     for (int64_t t = w; t < a.tiles; t += nwarps) {
-        wave_tile<S, R, RY, START>(a, tx, ty, lane);
+        wave_tile<S, R, RY, START, HL, false, NARROW>(a, tx, ty, lane);
         if constexpr (REV) {
             tx -= dx;
             ty -= dy;
@@ -443,6 +586,18 @@ __device__ __forceinline__ void wave_vec_body(const Args& a) {
 template <typename S, int R, int RY, bool START, bool REV>
 __global__ void __launch_bounds__(256) wave_vec_kernel(Args a) {
     wave_vec_body<S, R, RY, START, REV>(a);
+}
+
+// The halo-lane form (tiles of 30*V columns, no edge vectors).
+template <typename S, int R, int RY, bool START, bool REV>
+__global__ void __launch_bounds__(256) wave_hl_kernel(Args a) {
+    wave_vec_body<S, R, RY, START, REV, true>(a);
+}
+
+// The narrow halo-lane form for 16-bit storage (8-byte vectors, tiles of 120 columns).
+template <typename S, int R, int RY, bool START, bool REV>
+__global__ void __launch_bounds__(128) wave_hln_kernel(Args a) {
+    wave_vec_body<S, R, RY, START, REV, true, true>(a);
 }
 
 // The same kernel held to 96 registers (5 blocks of 128 threads an SM instead of 4, for
@@ -482,19 +637,33 @@ __global__ void __launch_bounds__(256) wave_scalar_kernel(Args a) {
 }
 
 // Row heights of the vector kernel's tiles; variant v (1-based) = (kTileRows[(v-1) % 4],
-// kBlockThreads[(v-1) / 4]).
+// kBlockThreads[(v-1) / 4]) for v <= 8; variants 9-12 are the halo-lane form with
+// (kHlRows[(v-9) % 2], kBlockThreads[(v-9) / 2]); 16-bit storage adds variants 13-14,
+// the narrow halo-lane form with kHlRows[v-13] rows and 128 threads.
 constexpr int kTileRows[4] = {2, 4, 8, 16};
 constexpr int kBlockThreads[2] = {128, 256};
-constexpr int kVariants = 8;
+constexpr int kHlRows[2] = {4, 8};
+constexpr int kVariants32 = 12;  // FP32 storage
+constexpr int kVariants16 = 14;  // 16-bit storage
+
+// How a variant covers a chunk.
+enum class Form { Tile, Halo, Narrow };
 
 using KernelFn = void (*)(Args);
 
-// Launch helper shared by the per-dtype translation units.
+// Launch helper shared by the per-dtype translation units; span = output columns per
+// warp tile (or strip); tile_rows = rows per tile (or segment).
 sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn scalar_fn, int tile_rows,
-                       int threads, int V, size_t esize);
+                       int threads, int span, size_t esize, Form form);
 
 template <typename S, int R, bool START, bool REV>
-KernelFn pick_vec(int tile_rows) {
+KernelFn pick_vec(int tile_rows, Form form) {
+    if constexpr (sizeof(S) == 2) {
+        if (form == Form::Narrow)
+            return tile_rows == 4 ? wave_hln_kernel<S, R, 4, START, REV> : wave_hln_kernel<S, R, 8, START, REV>;
+    }
+    if (form == Form::Halo)
+        return tile_rows == 4 ? wave_hl_kernel<S, R, 4, START, REV> : wave_hl_kernel<S, R, 8, START, REV>;
     switch (tile_rows) {
         case 2: return wave_vec_kernel<S, R, 2, START, REV>;
         case 4:
@@ -507,27 +676,31 @@ KernelFn pick_vec(int tile_rows) {
 
 // The start always sweeps forward (a run's reversed steps are its odd leapfrog steps).
 template <typename S, int R>
-sy_status launch_r(Queue* q, const WaveLaunch& w, int tile_rows, int threads) {
-    KernelFn vec = w.start     ? pick_vec<S, R, true, false>(tile_rows)
-                   : w.reverse ? pick_vec<S, R, false, true>(tile_rows)
-                               : pick_vec<S, R, false, false>(tile_rows);
+sy_status launch_r(Queue* q, const WaveLaunch& w, int tile_rows, int threads, Form form) {
+    KernelFn vec = w.start     ? pick_vec<S, R, true, false>(tile_rows, form)
+                   : w.reverse ? pick_vec<S, R, false, true>(tile_rows, form)
+                               : pick_vec<S, R, false, false>(tile_rows, form);
     KernelFn sca = w.start ? wave_scalar_kernel<S, R, true> : wave_scalar_kernel<S, R, false>;
-    return launch_typed(q, w, vec, sca, tile_rows, threads, Traits<S>::V, sizeof(S));
+    int span = form == Form::Tile ? tile_span<S, false>() : tile_span<S, true>();
+    if constexpr (sizeof(S) == 2) {
+        if (form == Form::Narrow) span = tile_span<S, true, true>();
+    }
+    return launch_typed(q, w, vec, sca, tile_rows, threads, span, sizeof(S), form);
 }
 
 template <typename S>
-sy_status launch_dtype(Queue* q, const WaveLaunch& w, int tile_rows, int threads) {
+sy_status launch_dtype(Queue* q, const WaveLaunch& w, int tile_rows, int threads, Form form) {
     switch (w.radius) {
-        case 1: return launch_r<S, 1>(q, w, tile_rows, threads);
-        case 2: return launch_r<S, 2>(q, w, tile_rows, threads);
-        case 3: return launch_r<S, 3>(q, w, tile_rows, threads);
-        default: return launch_r<S, 4>(q, w, tile_rows, threads);
+        case 1: return launch_r<S, 1>(q, w, tile_rows, threads, form);
+        case 2: return launch_r<S, 2>(q, w, tile_rows, threads, form);
+        case 3: return launch_r<S, 3>(q, w, tile_rows, threads, form);
+        default: return launch_r<S, 4>(q, w, tile_rows, threads, form);
     }
 }
 
-sy_status launch_f32(Queue* q, const WaveLaunch& w, int tile_rows, int threads);
-sy_status launch_bf16(Queue* q, const WaveLaunch& w, int tile_rows, int threads);
-sy_status launch_f16(Queue* q, const WaveLaunch& w, int tile_rows, int threads);
+sy_status launch_f32(Queue* q, const WaveLaunch& w, int tile_rows, int threads, Form form);
+sy_status launch_bf16(Queue* q, const WaveLaunch& w, int tile_rows, int threads, Form form);
+sy_status launch_f16(Queue* q, const WaveLaunch& w, int tile_rows, int threads, Form form);
 
 }  // namespace wave
 }  // namespace sy

@@ -115,6 +115,98 @@ def test_graph_run_equals_per_grid_steps(q):
         sy.sy_stencil_batch_destroy(plan)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("steps", [7, 10])
+def test_cross_step_form_bit_exact_vs_oracle(q, dtype, steps):
+    """The whole run as one cooperative launch with a grid barrier between steps."""
+    torch = torch_cuda()
+    host, dev = make_grids(SMALL, dtype)
+    plan = plan_for(q, SMALL, dev, dtype, 0)
+    try:
+        sy.sy_stencil_batch_start(plan)
+        sy.sy_stencil_batch_capture_persistent(plan, steps)
+        sy.sy_stencil_batch_run(plan)
+        sy.sy_queue_sync(q)
+        assert sy.sy_stencil_batch_times(plan, 2)[1] > 0
+        for (ny, nx, r), u0, (ua, ub, _) in zip(SMALL, host, dev):
+            op, oc = oracle.wave_run_mirror(DT[dtype], u0, steps, r, 0.25)
+            newest, older = (ua, ub) if steps % 2 == 1 else (ub, ua)
+            assert np.array_equal(bits(host_of(newest, nx, dtype)), bits(oc)), (ny, nx, r)
+            assert np.array_equal(bits(host_of(older, nx, dtype)), bits(op)), (ny, nx, r)
+    finally:
+        sy.sy_stencil_batch_destroy(plan)
+    torch.cuda.synchronize()
+
+
+def test_cross_step_form_equals_class_launches_on_config2(q):
+    """64 grids of the batched workload, 100 steps: every point of every grid identical
+    between the per-class launches (one graph) and the one-launch form."""
+    torch = torch_cuda()
+    shapes = inputs.batch_grids()
+    runs = []
+    for persistent in (False, True):
+        dev = []
+        for ny, nx, r in shapes:
+            pitch = pitch_for(nx, "f32")
+            ub = torch.zeros((ny, pitch), dtype=torch.float32, device="cuda")
+            ub[:, :nx] = torch.from_numpy(inputs.batch_initial(ny, nx, "f32")).cuda()
+            dev.append((torch.empty_like(ub), ub, pitch))
+        plan = plan_for(q, shapes, dev, "f32", 0)
+        try:
+            sy.sy_stencil_batch_start(plan)
+            (sy.sy_stencil_batch_capture_persistent if persistent else sy.sy_stencil_batch_capture)(plan, 100)
+            sy.sy_stencil_batch_run(plan)
+            sy.sy_queue_sync(q)
+        finally:
+            sy.sy_stencil_batch_destroy(plan)
+        runs.append(dev)
+    for (ny, nx, _), (a0, b0, _), (a1, b1, _) in zip(shapes, *runs):  # the fields, not their row padding
+        assert torch.equal(a0[:, :nx].contiguous().view(torch.int32), a1[:, :nx].contiguous().view(torch.int32))
+        assert torch.equal(b0[:, :nx].contiguous().view(torch.int32), b1[:, :nx].contiguous().view(torch.int32))
+
+
+def test_cross_step_barrier_wait_is_bounded_and_context_survives(q):
+    """Host-injected fault: block 0 never arrives at the first step barrier.  Every other
+    block's wait gives up after about a second, the run reports SY_ERR_TIMEOUT once, and the
+    next capture on the same queue runs correctly."""
+    import os
+
+    torch = torch_cuda()
+    host, dev = make_grids(SMALL, "f32")
+    old = os.environ.get("SY_FAULT")
+    os.environ["SY_FAULT"] = "batch_barrier_timeout"
+    try:
+        plan = plan_for(q, SMALL, dev, "f32", 0)
+        sy.sy_stencil_batch_start(plan)
+        sy.sy_stencil_batch_capture_persistent(plan, 4)
+    finally:
+        if old is None:
+            del os.environ["SY_FAULT"]
+        else:
+            os.environ["SY_FAULT"] = old
+    try:
+        sy.sy_stencil_batch_run(plan)
+        with pytest.raises(sy.SyError) as e:
+            sy.sy_queue_sync(q)
+        assert e.value.name == "SY_ERR_TIMEOUT"
+        sy.sy_queue_sync(q)  # reported once, then cleared
+    finally:
+        sy.sy_stencil_batch_destroy(plan)
+    host, dev = make_grids(SMALL, "f32")
+    plan = plan_for(q, SMALL, dev, "f32", 0)
+    try:
+        sy.sy_stencil_batch_start(plan)
+        sy.sy_stencil_batch_capture_persistent(plan, 4)
+        sy.sy_stencil_batch_run(plan)
+        sy.sy_queue_sync(q)
+        for (ny, nx, r), u0, (ua, ub, _) in zip(SMALL, host, dev):
+            _, oc = oracle.wave_run_mirror(oracle.F32, u0, 4, r, 0.25)
+            assert np.array_equal(bits(host_of(ub, nx, "f32")), bits(oc))
+    finally:
+        sy.sy_stencil_batch_destroy(plan)
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("tile_rows", [0, 4], ids=["classes", "rows4"])
 def test_config2_full_batch_sampled(q, tile_rows):
     """64 grids, sides log-uniform in [256, 4096] (seed 1), radius from {1, 2, 4}, 100 steps in one

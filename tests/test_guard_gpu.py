@@ -62,7 +62,8 @@ def bits(a):
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 @pytest.mark.parametrize("r", [1, 2, 4])
-def test_2d_step_reads_and_writes_only_the_field(q, dtype, r):
+@pytest.mark.parametrize("variant", [0, 9, 13])  # default tiles, halo-lane tiles, narrow (16-bit; FP32: 0)
+def test_2d_step_reads_and_writes_only_the_field(q, dtype, r, variant):
     torch = torch_cuda()
     ny, nx = 37, 301
     v = 4 if dtype == "f32" else 8
@@ -70,7 +71,8 @@ def test_2d_step_reads_and_writes_only_the_field(q, dtype, r):
     u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 6.0) + 0.05 * inputs.random_field(5, ny, nx), dtype)
     cur = Guarded(ny, nx, pitch, dtype, torch, u0)
     prev = Guarded(ny, nx, pitch, dtype, torch)
-    p = sy.stencil_params(ny, nx, r, 0.25, dtype, pitch=pitch)
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype, pitch=pitch, variant=variant if (dtype != "f32" or variant < 13)
+                          else 0)
     chunks = [(0, 5), (5, 6), (6, 30), (30, 37)]
     sy.sy_stencil_start(q, p, cur.field, prev.field, chunks, r)
     for _ in range(4):

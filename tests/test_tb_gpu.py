@@ -45,7 +45,7 @@ def run_tb(q, u0, T, r, dtype, chunks, passes, pitch=None, torch=None):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
-@pytest.mark.parametrize("T,r", [(2, 1), (4, 1), (2, 2), (4, 2)])
+@pytest.mark.parametrize("T,r", [(2, 1), (4, 1), (2, 2), (4, 2), (2, 3), (4, 3), (2, 4), (4, 4)])
 @pytest.mark.parametrize("ny,nx,chunks", [(70, 300, None), (33, 129, [(0, 1), (1, 5), (5, 33)]), (130, 520, None)])
 def test_tb_bit_exact_vs_oracle(q, dtype, T, r, ny, nx, chunks):
     torch = torch_cuda()
@@ -61,17 +61,17 @@ def test_tb_bit_exact_vs_oracle(q, dtype, T, r, ny, nx, chunks):
     assert np.array_equal(bits(to_host(prev, (ny, nx), st)), bits(op))
 
 
-@pytest.mark.parametrize("T", [2, 4])
-def test_tb_full_size_equals_single_steps(q, T):
+@pytest.mark.parametrize("T,r", [(2, 1), (4, 1), (4, 4)])
+def test_tb_full_size_equals_single_steps(q, T, r):
     torch = torch_cuda()
     n, steps = 8192, 200
     u0 = inputs.to_storage(inputs.gaussian_pulse(n, n, 64.0), "f32")
     chunks = sy.sy_split_rows(n, 4)
-    prev, cur = run_tb(q, u0, T, 1, "f32", chunks, steps // T, torch=torch)
+    prev, cur = run_tb(q, u0, T, r, "f32", chunks, steps // T, torch=torch)
     d0 = torch.from_numpy(u0).cuda()
     a, b = torch.empty_like(d0), torch.empty_like(d0)
-    p = sy.stencil_params(n, n, 1, 0.25, "f32")
-    pv, cv, _ = sy.sy_wave_run(q, p, d0, a, b, steps, chunks, 1)
+    p = sy.stencil_params(n, n, r, 0.25, "f32")
+    pv, cv, _ = sy.sy_wave_run(q, p, d0, a, b, steps, chunks, r)
     torch.cuda.synchronize()
     byptr = {d0.data_ptr(): d0, a.data_ptr(): a, b.data_ptr(): b}
     assert torch.equal(cur.view(torch.int32), byptr[cv].view(torch.int32))
@@ -86,7 +86,7 @@ def test_tb_errors(q):
              ((p, 2, a, b, c, c, [(0, 64)], 2), "SY_ERR_ALIAS"),
              ((p, 2, a, b, c, d, [(0, 64)], 1), "SY_ERR_HALO_TOO_SMALL"),
              ((p, 3, a, b, c, d, [(0, 64)], 3), "SY_ERR_INVALID_ARGUMENT"),
-             ((sy.stencil_params(64, 128, 3, 0.25, "f32"), 2, a, b, c, d, [(0, 64)], 6), "SY_ERR_UNSUPPORTED"),
+             ((sy.stencil_params(64, 128, 3, 0.25, "f32"), 2, a, b, c, d, [(0, 64)], 5), "SY_ERR_HALO_TOO_SMALL"),
              ((sy.stencil_params(64, 127, 1, 0.25, "f32", pitch=127), 2, a, b, c, d, [(0, 64)], 2),
               "SY_ERR_INVALID_ARGUMENT")]
     for args, name in cases:

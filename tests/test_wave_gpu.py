@@ -141,6 +141,27 @@ def test_every_variant_identical(q, dtype, r):
         assert np.array_equal(bits(c), bits(oc)), f"variant {v}"
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(1, 1), (3, 241), (17, 257), (70, 1030), (129, 64), (40, 480), (9, 2000)])
+def test_halo_lane_and_march_forms_bit_exact(q, dtype, r, shape):
+    """The halo-lane tiles (variants 9-12: 30 of 32 lanes store) and, for 16-bit storage,
+    the narrow halo-lane tiles (variants 13-14: 8-byte vectors): tiles narrower than the
+    grid, wider than it, ragged at nx, grids shorter than a tile or than the radius, and
+    chunks of one row."""
+    ny, nx = shape
+    u0 = field(ny, nx, dtype, seed=r + 7)
+    steps = 6
+    _, oc = oracle.wave_run_mirror(DT[dtype], u0, steps, r, 0.25)
+    chunkings = [sy.sy_split_rows(ny, min(3, ny))]
+    if ny >= 5:
+        chunkings.append([(0, 1), (1, 2), (2, ny)])
+    for v in ((9, 12, 13, 14) if dtype != "f32" else (9, 12)):
+        for chunks in chunkings:
+            _, c = wave_run(q, u0, steps, r, 0.25, dtype, chunks, variant=v)
+            assert np.array_equal(bits(c), bits(oc)), f"variant {v} chunks {chunks}"
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("pitch_extra", [4, 8, 3, 1])
 def test_padded_and_unaligned_pitch(q, dtype, pitch_extra):

@@ -29,24 +29,31 @@ def test_static_energy_matches_allocating_entry_point_on_two_calls():
     out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream  # 0 = legacy default stream
     with sy.Queue(0) as q:
-        # two calls in a row with different inputs: the second must not see the first's partial sums
-        for dtype, r, (ny, nx), seed in [("f32", 1, (300, 517), 3), ("bf16", 4, (129, 2050), 8)]:
+        # Two calls in a row: first a grid on which every one of the reduction's 1024 x 256
+        # threads has points, then one of 100k points, on which about 600 blocks have none.
+        # Those blocks must still overwrite their partial sums, or the second call would add
+        # the first call's leftovers.
+        for dtype, r, (ny, nx), seed in [("f32", 1, (700, 1030), 3), ("bf16", 4, (100, 1000), 8)]:
             code = oracle.DTYPES[dtype]
             un, uo = _field(ny, nx, dtype, seed), _field(ny, nx, dtype, seed + 1)
             to_dev = (lambda a: torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).cuda())
             dn, do = to_dev(un), to_dev(uo)
             p = sy.stencil_params(ny, nx, r, 0.25, dtype)
             want = sy.sy_wave_energy(q.handle, p, dn, do)
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
             rc = L.sy_wave_energy_static(C.c_void_p(stream or None), C.byref(p), C.c_void_p(dn.data_ptr()),
                                          C.c_void_p(do.data_ptr()), C.c_void_p(out.data_ptr()))
             assert rc == 0, L.sy_last_error().decode()
             torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] == free_before, "the allocation-free entry point allocated"
             got = out.cpu().tolist()
-            # the energy tests' tolerance: two summation orders of N terms differ by <= 2 N eps sum|terms|
+            # same kernels, same fixed reduction shape and order as the allocating entry point
+            assert got == list(want), (dtype, got, want)
+            # and the FP64 oracle, within two summation orders of N terms: <= 2 N eps sum|terms|
             ref = oracle.wave_energy_f64(oracle.storage_to_f64(un, code), oracle.storage_to_f64(uo, code), r, 0.25)
             tol = 2 * ny * nx * 2.0 ** -53 * ref["abs_sum"]
-            for g, w, scale in zip(got, want, (1, 1, 8)):
-                assert abs(g - w) <= scale * tol, (dtype, got, want)
+            assert abs(got[0] - ref["E"]) <= tol, (dtype, got[0], ref["E"])
 
 
 def test_static_energy_rejects_bad_arguments():
