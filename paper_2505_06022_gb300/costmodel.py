@@ -212,6 +212,79 @@ def energy_check(q: Queue, n_cands: int = 96, seconds: float = 1.0, seed: int = 
             "group_power_w": {f"{k[1]}/r{k[2]}": v for k, v in power.items() if k[0] == 1}}
 
 
+def _power_design(rows: list[dict]) -> np.ndarray:
+    """Design matrix of the power model: a bias, the 13 cost features of each candidate, and a
+    one-hot of its (storage, radius) group."""
+    from . import DTYPE_CODES as CODES, sy_stencil_variant_info
+
+    out = []
+    for x in rows:
+        code = CODES[x["dtype"]]
+        tr, tc, thr = sy_stencil_variant_info(x["radius"], code, x["variant"])
+        f = sy_cost_features(1, code, x["radius"], x["side"], x["side"], tr, tc, thr, x["chunks"])
+        onehot = np.zeros(8)
+        onehot[(0 if x["dtype"] == "f32" else 4) + x["radius"] - 1] = 1.0
+        out.append(np.concatenate([[1.0], f.astype(np.float64), onehot]))
+    return np.asarray(out)
+
+
+def fit_power_model(check: dict, ridge: float = 1e-2) -> dict:
+    """Least-squares (ridge) model of log(measured power / group power) on the candidates an
+    energy_check metered one by one: log P = log P_group + design . beta.  Also reports its
+    leave-one-out error against the group-power labels' own error on the same candidates."""
+    rows = check["candidates"]
+    X = _power_design(rows)
+    y = np.log([x["j_measured"] / x["j_label"] for x in rows])  # = log(P_measured / P_group)
+    A = X.T @ X + ridge * np.eye(X.shape[1])
+    beta = np.linalg.solve(A, X.T @ y)
+    loo_pred = []
+    for i in range(len(rows)):
+        m = np.ones(len(rows), bool)
+        m[i] = False
+        b = np.linalg.solve(X[m].T @ X[m] + ridge * np.eye(X.shape[1]), X[m].T @ y[m])
+        loo_pred.append(float(X[i] @ b))
+    loo_pred = np.asarray(loo_pred)
+    loo = np.abs(loo_pred - y)
+
+    def order_agreement(log_e_pred):
+        """Pairs of one (storage, radius, grid) group whose measured energies differ by > 2 %:
+        how many the predicted energies order the same way."""
+        agree = pairs = 0
+        lm = np.log([x["j_measured"] for x in rows])
+        key = [(x["dtype"], x["radius"], x["side"]) for x in rows]
+        for a in range(len(rows)):
+            for b in range(a + 1, len(rows)):
+                if key[a] != key[b] or abs(lm[a] - lm[b]) < 0.02:
+                    continue
+                pairs += 1
+                agree += int((lm[a] > lm[b]) == (log_e_pred[a] > log_e_pred[b]))
+        return {"pairs": pairs, "agree": agree}
+
+    log_label = np.log([x["j_label"] for x in rows])
+    return {"beta": beta.tolist(), "group_power_w": check["group_power_w"], "candidates": len(rows),
+            "loo_abs_log_error": {"median": float(np.median(loo)), "p90": float(np.quantile(loo, 0.9)),
+                                  "max": float(loo.max())},
+            "group_label_abs_log_error": {"median": float(np.median(np.abs(y))),
+                                          "p90": float(np.quantile(np.abs(y), 0.9)), "max": float(np.abs(y).max())},
+            "energy_order_loo": order_agreement(log_label + loo_pred),
+            "energy_order_group_label": order_agreement(log_label)}
+
+
+def energy_labels_measured(shapes, corpus, power: dict, model: dict) -> np.ndarray:
+    """log J per row = log(P_group * t) + the power model's correction for that candidate (stencils;
+    SAXPY rows keep the group label)."""
+    out = energy_labels(shapes, corpus, power)
+    beta = np.asarray(model["beta"])
+    for k, sid in enumerate(corpus["shape"]):
+        s = shapes[sid]
+        if s["kind"] != 1:
+            continue
+        onehot = np.zeros(8)
+        onehot[(0 if s["dtype"] == "f32" else 4) + s["radius"] - 1] = 1.0
+        out[k] += float(np.concatenate([[1.0], corpus["X"][k].astype(np.float64), onehot]) @ beta)
+    return out
+
+
 def split_shapes(n_shapes: int, seed: int = 11, test_fraction: float = 0.2) -> tuple[np.ndarray, np.ndarray]:
     """Held-out shapes never seen in training: a seeded permutation of the shape ids."""
     order = np.argsort(inputs.splitmix64(seed, n_shapes))
@@ -331,6 +404,9 @@ def main() -> None:
     ap.add_argument("--energy-check", type=int, default=0, metavar="N",
                     help="only meter N stencil candidates one by one (>= 1 s NVML window each) and compare "
                          "their measured energy with the corpus labels (group power x time); one JSON line")
+    ap.add_argument("--energy-measured", type=int, default=0, metavar="N",
+                    help="label energy with a power model fitted on N candidates metered one by one "
+                         "(instead of group power x time alone)")
     ap.add_argument("--stencil", type=int, default=560)
     ap.add_argument("--saxpy", type=int, default=40)
     ap.add_argument("--reps", type=int, default=3)
@@ -353,6 +429,10 @@ def main() -> None:
     t_measure = time.time() - t0
     power = group_power(q)
     loge = energy_labels(shapes, corpus, power)
+    pmodel = None
+    if args.energy_measured:
+        pmodel = fit_power_model(energy_check(q, args.energy_measured))
+        loge = energy_labels_measured(shapes, corpus, power, pmodel)
     train_ids, test_ids = split_shapes(len(shapes))
     t1 = time.time()
     model = train(q, corpus, train_ids, epochs=args.epochs, log_energy=loge)
@@ -361,6 +441,8 @@ def main() -> None:
     res.update({"rows": int(corpus["X"].shape[0]), "shapes": len(shapes), "train_shapes": int(train_ids.size),
                 "test_shapes": int(test_ids.size), "measure_s": t_measure, "train_s": t_train,
                 "group_power_w": {f"{k[0]}/{k[1]}/r{k[2]}": v for k, v in power.items()}})
+    if pmodel is not None:
+        res["power_model"] = {k: v for k, v in pmodel.items() if k != "beta"}
     if args.out:
         np.savez(args.out, loge=loge, **corpus)
     if args.model:

@@ -188,8 +188,17 @@ __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_b
     }
 }
 
+// Blocks an SM the kernel is compiled for (its register budget): a tile's shared
+// memory admits 5 blocks at radius 1 and 3-4 at radius 2, and the unrolled row window
+// would otherwise take a few registers more than 4 (radius 1) or 3 (radius 2) blocks
+// leave, which cost 16-bit radius-1 passes a quarter of their resident warps.
+template <int R>
+struct TbMinBlocks {
+    static constexpr int value = R == 1 ? 4 : (R == 2 ? 3 : 2);
+};
+
 template <typename S, int R, int T>
-__global__ void __launch_bounds__(kThreads) wave_tb_kernel(const __grid_constant__ CUtensorMap map_prev,
+__global__ void __launch_bounds__(kThreads, TbMinBlocks<R>::value) wave_tb_kernel(const __grid_constant__ CUtensorMap map_prev,
                                                            const __grid_constant__ CUtensorMap map_cur, TBArgs a) {
     using G = Geo<S, R, T>;
     using Tr = wave::Traits<S>;

@@ -90,7 +90,11 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            SY_CUDA(cudaLaunchKernelEx(&cfg, vec_fn, a));
+            const cudaError_t e = cudaLaunchKernelEx(&cfg, vec_fn, a);
+            if (e != cudaSuccess)
+                return fail(SY_ERR_CUDA, "cudaLaunchKernelEx(%lld blocks x %d threads, %d-row tiles): %s (%s)",
+                            static_cast<long long>(blocks), threads, tile_rows, cudaGetErrorString(e),
+                            cudaGetErrorName(e));
         } else {
             vec_fn<<<static_cast<unsigned>(blocks), threads, 0, q->launch>>>(a);
         }

@@ -278,11 +278,8 @@ __device__ __forceinline__ float update(float u, float up, const float (&vert)[R
 // The same update for two neighbouring points at once.  The additions use
 // Blackwell's packed FP32 add (add.rn.f32x2, written as PTX: each half one IEEE
 // round-to-nearest addition, bit-identical to __fadd_rn); a - b is evaluated as
-// a + (-b), which IEEE 754 defines to be the same operation.  The multiplications
-// stay scalar __fmul_rn: a packed multiply feeding a packed add was measured to be
-// contracted into a fused multiply-add despite the explicit rounding mode, which
-// would change the results, while scalar multiplies are never contracted in the
-// translation units that use this (built with -fmad=false).
+// a + (-b), which IEEE 754 defines to be the same operation.  Scalar multiplies are
+// never contracted in the translation units that use this (built with -fmad=false).
 __device__ __forceinline__ float2 add2_rn(float2 a, float2 b) {
     float2 d;
     asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
@@ -305,21 +302,13 @@ __device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
     return d;
 }
 
-// w * x for two points as one packed fused multiply-add with addend -0:
-// fma.rn(w, x, -0) rounds w x once, and adding -0 changes no value (not even the
-// sign of a zero product), so each half equals __fmul_rn(w, x) bit for bit.  A
-// packed mul.rn.f32x2 feeding a packed add came out fused into one rounding despite
-// the explicit rounding modes (16-bit steps at radius 2-4, whose weights make
-// inexact products, stopped matching the mirror; radius 1, whose products are exact,
-// still matched); an fma has no multiply left to fuse.
+// The multiplications stay scalar.  Two packed forms were tried and measured to
+// change results at radius 2-4 (whose weights make inexact products; radius 1,
+// whose products are exact, still matched): mul.rn.f32x2 feeding a packed add, and
+// fma.rn.f32x2 with a -0 addend (which rounds the product exactly once): both came
+// out fused with the following addition despite the explicit rounding modes.
 __device__ __forceinline__ float2 mul2_scalar(float w, float2 x) {
-    float2 d;
-    asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\t"
-        "mov.b64 pa, {%2, %2};\n\tmov.b64 pb, {%3, %4};\n\tmov.b64 pc, {%5, %5};\n\t"
-        "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(w), "f"(x.x), "f"(x.y), "f"(-0.0f));
-    return d;
+    return make_float2(__fmul_rn(w, x.x), __fmul_rn(w, x.y));
 }
 
 // Horizontal pair sums (u_{j-d} + u_{j+d}) of the points j = e, e+1 from a row held as
@@ -608,6 +597,13 @@ __global__ void __maxnreg__(96) wave_vec_kernel_r96(Args a) {
     wave_vec_body<S, R, RY, START, REV>(a);
 }
 
+// The same kernel held to 168 registers (3 blocks of 128 threads an SM instead of 2):
+// 16-bit storage, radius 3-4, 8-row tiles, whose unbounded form takes 255 registers.
+template <typename S, int R, int RY, bool START, bool REV>
+__global__ void __launch_bounds__(128, 3) wave_vec_kernel_b3(Args a) {
+    wave_vec_body<S, R, RY, START, REV>(a);
+}
+
 // One point per thread; any element-aligned layout.
 template <typename S, int R, bool START>
 __global__ void __launch_bounds__(256) wave_scalar_kernel(Args a) {
@@ -657,7 +653,7 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
                        int threads, int span, size_t esize, Form form);
 
 template <typename S, int R, bool START, bool REV>
-KernelFn pick_vec(int tile_rows, Form form) {
+KernelFn pick_vec(int tile_rows, Form form, int threads) {
     if constexpr (sizeof(S) == 2) {
         if (form == Form::Narrow)
             return tile_rows == 4 ? wave_hln_kernel<S, R, 4, START, REV> : wave_hln_kernel<S, R, 8, START, REV>;
@@ -669,7 +665,11 @@ KernelFn pick_vec(int tile_rows, Form form) {
         case 4:
             if constexpr (sizeof(S) == 2 && R == 1) return wave_vec_kernel_r96<S, R, 4, START, REV>;
             else return wave_vec_kernel<S, R, 4, START, REV>;
-        case 8: return wave_vec_kernel<S, R, 8, START, REV>;
+        case 8:
+            if constexpr (sizeof(S) == 2 && R >= 3) {
+                if (threads == 128) return wave_vec_kernel_b3<S, R, 8, START, REV>;
+            }
+            return wave_vec_kernel<S, R, 8, START, REV>;
         default: return wave_vec_kernel<S, R, 16, START, REV>;
     }
 }
@@ -677,9 +677,9 @@ KernelFn pick_vec(int tile_rows, Form form) {
 // The start always sweeps forward (a run's reversed steps are its odd leapfrog steps).
 template <typename S, int R>
 sy_status launch_r(Queue* q, const WaveLaunch& w, int tile_rows, int threads, Form form) {
-    KernelFn vec = w.start     ? pick_vec<S, R, true, false>(tile_rows, form)
-                   : w.reverse ? pick_vec<S, R, false, true>(tile_rows, form)
-                               : pick_vec<S, R, false, false>(tile_rows, form);
+    KernelFn vec = w.start     ? pick_vec<S, R, true, false>(tile_rows, form, threads)
+                   : w.reverse ? pick_vec<S, R, false, true>(tile_rows, form, threads)
+                               : pick_vec<S, R, false, false>(tile_rows, form, threads);
     KernelFn sca = w.start ? wave_scalar_kernel<S, R, true> : wave_scalar_kernel<S, R, false>;
     int span = form == Form::Tile ? tile_span<S, false>() : tile_span<S, true>();
     if constexpr (sizeof(S) == 2) {

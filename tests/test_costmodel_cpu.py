@@ -60,3 +60,27 @@ def test_corpus_shapes_ranges_and_determinism():
     # log-uniform sides: about half of them below the geometric mean of the range
     below = sum(s["ny"] < math.sqrt(512 * 16384) for s in sten)
     assert 0.35 * 300 < below < 0.65 * 300
+
+
+def test_power_model_recovers_a_known_power_law_and_beats_the_group_label():
+    """Synthetic metered candidates whose power is the group's times exp(0.3 - 0.1 log2 points):
+    the fitted model (features from the library's host-side feature code) predicts held-out
+    candidates far better than the group label, and orders their energies correctly."""
+    z = inputs.splitmix64(3, 4 * 60)
+    rows = []
+    for i in range(60):
+        dt = ("f32", "bf16")[int(z[4 * i] % 2)]
+        r = 1 + int(z[4 * i + 1] % 4)
+        side = (2048, 4096, 8192)[int(z[4 * i + 2] % 3)]
+        v = 1 + int(z[4 * i + 3] % 12)
+        k = (1, 4)[int((z[4 * i + 3] >> 32) % 2)]
+        ms = 1e-3 * side * side / 6e8 * (1.0 + 0.05 * (v % 3))
+        label = 1000.0 * ms * 1e-3
+        meas = label * math.exp(0.3 - 0.1 * math.log2(side * side))
+        rows.append({"dtype": dt, "radius": r, "side": side, "variant": v, "chunks": k, "ms": ms,
+                     "j_measured": meas, "j_label": label})
+    fit = costmodel.fit_power_model({"candidates": rows, "group_power_w": {}}, ridge=1e-6)
+    assert fit["loo_abs_log_error"]["max"] < 0.02
+    assert fit["group_label_abs_log_error"]["median"] > 1.0
+    o = fit["energy_order_loo"]
+    assert o["pairs"] > 0 and o["agree"] == o["pairs"]
