@@ -821,7 +821,15 @@ def run_gpu(args) -> None:
                       "j_per_update": joules / (sims * updates_per_step), "avg_power_w": joules / seconds,
                       "idle_w": idle_w,
                       "j_per_update_above_idle": (joules - idle_w * seconds) / (sims * updates_per_step),
-                      "chunk_kernel_j_mean": statistics.mean(kern_j)}
+                      "chunk_kernel_j_mean": statistics.mean(kern_j),
+                      "chunk_kernel_j_note": "attributed: window power x kernel time (sy_kernel_energy)"}
+            # the same chunk kernel measured alone: chunk 1 replayed in its own >= 1 s window
+            rep = sy.sy_chunk_energy_replay(q.handle, p, A, u0, B, chunks, 1, HALO, min_seconds=1.0)
+            energy["chunk_replay"] = {"chunk": 1, "j_per_launch": rep["joules"], "ms_per_launch": rep["ms"],
+                                      "launches": rep["reps"],
+                                      "j_per_update": rep["joules"] / ((chunks[1][1] - chunks[1][0]) * NX),
+                                      "note": "measured: the chunk's launch replayed alone in one NVML window "
+                                              "(sy_chunk_energy_replay)"}
 
     # ---- e2e: whole simulations from host memory, through sy_wave_run_host ----
     # Every step hands the library the pinned host initial field and receives the final
@@ -834,7 +842,7 @@ def run_gpu(args) -> None:
     if True:
         h_in = torch.from_numpy(u0_host if args.dtype == "f32" else u0_host.view(np.int16)).pin_memory()
         h_out = [torch.empty_like(h_in).pin_memory() for _ in range(2)]
-        k_e2e = max(1, min(args.steps, 10))
+        k_e2e = max(1, args.steps)  # the same step count as the device-timed region
 
         def host_steps(k, sync_each):
             for i in range(k):

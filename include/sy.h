@@ -241,6 +241,23 @@ typedef struct sy_chunk_stats {
 sy_status sy_chunk_stats_read(sy_queue_t q, const sy_stencil_params* p, const sy_chunk* chunks,
                               const sy_event* events, int n, sy_chunk_stats* out);
 
+/* Measured energy of one chunk's step kernel (the metering mode of the paper's
+ * per-kernel energy query, §4 Listing 3): the launch sy_stencil_step issues for
+ * chunks[c] (same variant, range mapper and halo rules) is replayed back to back
+ * inside one NVML metering window lasting at least min_seconds and min_reps
+ * launches; *joules and *ms are the window's energy and the launches' device time
+ * (CUDA events on the queue's stream) divided by the *reps launches.  The window
+ * holds nothing else, so this measures the chunk, unlike sy_kernel_energy, which
+ * attributes a shared window's average power by time.  Idle power is not
+ * subtracted.  u_next is overwritten each time (from the same inputs unless it
+ * aliases u_prev); the queue is synchronised; no metering window may be open.
+ * NVML's counter ticks every ~100 ms on GB300, so min_seconds >= 0.5 gives a
+ * resolution of a few percent.  SY_ERR_NVML_UNAVAILABLE (with *ms and *reps set,
+ * *joules = -1) when the counter cannot be read. */
+sy_status sy_chunk_energy_replay(sy_queue_t q, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
+                                 void* u_next, const sy_chunk* chunks, int n_chunks, int c, int halo_radius,
+                                 double min_seconds, int min_reps, double* joules, double* ms, int* reps);
+
 /* Taylor start for zero initial velocity: u_m1 = u0 + (c2 / 2) * L u0, evaluated
  * as fl(u0 + fl((c2/2) * L u0)) with L as above (bit-identical to a step with c2
  * halved and u_prev = u_cur = u0).  u_m1 must not overlap u0.  Same chunk rules

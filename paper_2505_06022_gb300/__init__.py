@@ -176,6 +176,8 @@ _SIGS = {
     "sy_wave_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
     "sy_wave_run_host": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p],
     "sy_stencil_default_variant": [C.c_int, C.c_int, _p],
+    "sy_chunk_energy_replay": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _p, _p,
+                               _p],
     "sy_stencil3d_step": [_p, _p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_stencil3d_start": [_p, _p, _p, _p, _p, C.c_int, C.c_int, _p],
     "sy_wave3d_run": [_p, _p, _p, _p, _p, _i64, _p, C.c_int, C.c_int, _p, _p, _p],
@@ -679,6 +681,17 @@ def sy_wave_run_host(q: int, p: StencilParams, host_u0, host_out, steps: int, ch
     _call("sy_wave_run_host", q, C.byref(p), _host_ptr(host_u0), _host_ptr(host_out), _host_ptr(host_prev_out),
           steps, arr, k, halo_radius, evs)
     return list(evs[:n_ev]) if want_events else []
+
+
+def sy_chunk_energy_replay(q: int, p: StencilParams, u_prev, u_cur, u_next, chunks, c: int, halo_radius: int,
+                           min_seconds: float = 1.0, min_reps: int = 20) -> dict:
+    """Chunk c's step launch replayed alone in one metering window: measured J and device ms per
+    launch, and the number of launches."""
+    arr, k = _chunks(chunks)
+    j, ms, n = C.c_double(), C.c_double(), C.c_int()
+    _call("sy_chunk_energy_replay", q, C.byref(p), _ptr(u_prev), _ptr(u_cur), _ptr(u_next), arr, k, c, halo_radius,
+          min_seconds, min_reps, C.byref(j), C.byref(ms), C.byref(n))
+    return {"joules": j.value, "ms": ms.value, "reps": n.value}
 
 
 def sy_stencil_multistep(q: int, p: StencilParams, T: int, u_prev, u_cur, out_prev, out_cur, chunks,

@@ -575,6 +575,66 @@ sy_status sy_chunk_stats_read(sy_queue_t qh, const sy_stencil_params* p, const s
     return SY_OK;
 }
 
+sy_status sy_chunk_energy_replay(sy_queue_t qh, const sy_stencil_params* p, const void* u_prev, const void* u_cur,
+                                 void* u_next, const sy_chunk* chunks, int n_chunks, int c, int halo_radius,
+                                 double min_seconds, int min_reps, double* joules, double* ms, int* reps) {
+    Queue* q = nullptr;
+    SY_TRY(check_queue(qh, &q));
+    SY_TRY(stencil_param_checks(p));
+    if (!joules || !ms || !reps) return fail(SY_ERR_NULL_POINTER, "joules, ms or reps is NULL");
+    SY_TRY(validate_chunks(p->ny, chunks, n_chunks));
+    if (c < 0 || c >= n_chunks) return fail(SY_ERR_INVALID_ARGUMENT, "chunk %d not in 0..%d", c, n_chunks - 1);
+    if (min_reps < 1 || !(min_seconds >= 0.0) || min_seconds > 600.0)
+        return fail(SY_ERR_INVALID_ARGUMENT, "min_reps = %d, min_seconds = %g", min_reps, min_seconds);
+    *joules = -1.0;
+    *ms = 0.0;
+    *reps = 0;
+    if (q->open_window >= 0) return fail(SY_ERR_INVALID_ARGUMENT, "a metering window is already open");
+    const int64_t a = chunks[c].begin, b = chunks[c].end;
+    // argument checks and a warm-up (occupancy lookups, first-touch) outside the window
+    for (int i = 0; i < 2; ++i) SY_TRY(sy_stencil_step_rows(qh, p, u_prev, u_cur, u_next, a, b, halo_radius, 0, nullptr));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SY_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
+    const sy_status meter = sy_meter_begin(qh);
+    sy_status st = SY_OK;
+    int n = 0;
+    const double t0 = host_seconds();
+    ce = cudaEventRecord(e0, q->stream);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "cudaEventRecord");
+    while (st == SY_OK && (n < min_reps || host_seconds() - t0 < min_seconds)) {
+        for (int i = 0; i < 32 && st == SY_OK; ++i, ++n)
+            st = sy_stencil_step_rows(qh, p, u_prev, u_cur, u_next, a, b, halo_radius, 0, nullptr);
+        if (st == SY_OK) {
+            ce = cudaStreamSynchronize(q->stream);
+            if (ce != cudaSuccess) st = cuda_fail(ce, "cudaStreamSynchronize");
+        }
+    }
+    if (st == SY_OK) {
+        ce = cudaEventRecord(e1, q->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float el = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&el, e0, e1);
+        if (ce != cudaSuccess) st = cuda_fail(ce, "cudaEventElapsedTime");
+        *ms = static_cast<double>(el) / n;
+        *reps = n;
+    }
+    double j = -1.0, secs = 0.0;
+    sy_status mend = SY_OK;
+    if (meter == SY_OK) mend = sy_meter_end(qh, &j, &secs);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SY_OK) return st;
+    if (meter != SY_OK) return meter;
+    if (mend != SY_OK) return mend;
+    *joules = j / n;
+    return SY_OK;
+}
+
 // ---- range mappers ---------------------------------------------------------------------
 sy_status sy_split_rows(int64_t n, int k, sy_chunk* out) {
     if (!out) return fail(SY_ERR_NULL_POINTER, "out is NULL");

@@ -535,6 +535,42 @@ def test_stream_events_and_energy_window(q):
     assert all((st["joules"] > 0) if metered else (st["joules"] == -1.0) for st in stats)
 
 
+def test_chunk_energy_replay_measures_one_chunk(q):
+    """sy_chunk_energy_replay: one chunk's launch replayed alone in a metering window.  Its output
+    rows equal a normal step's, its device time per launch is that chunk's, and the power it
+    implies is a physical one (NVML energy is not an oracle quantity: parity unpinned)."""
+    torch = torch_cuda()
+    ny, nx = 2048, 8192
+    u0 = to_device(inputs.to_storage(inputs.gaussian_pulse(ny, nx, 50.0), "f32"))
+    prev, nxt, ref = u0.clone(), torch.zeros_like(u0), torch.zeros_like(u0)
+    p = sy.stencil_params(ny, nx, 1, 0.25, "f32")
+    chunks = sy.sy_split_rows(ny, 4)
+    a, b = chunks[1]
+    ev = sy.sy_stencil_step(q, p, prev, u0, ref, chunks, 1, want_events=True)
+    torch.cuda.synchronize()
+    chunk_ms = sy.sy_events_elapsed(q, ev)[1]
+    cur_before = u0.clone()
+    try:
+        r = sy.sy_chunk_energy_replay(q, p, prev, u0, nxt, chunks, 1, 1, min_seconds=0.6, min_reps=50)
+        metered = True
+    except sy.SyError as e:
+        assert e.name == "SY_ERR_NVML_UNAVAILABLE"
+        metered = False
+    torch.cuda.synchronize()
+    assert torch.equal(u0, cur_before)  # inputs untouched
+    assert torch.equal(nxt[a:b].view(torch.int32), ref[a:b].view(torch.int32))
+    assert not nxt[:a].any() and not nxt[b:].any()  # only the chunk's rows are written
+    if metered:
+        assert r["reps"] >= 50 and r["joules"] > 0
+        assert 0.2 * chunk_ms < r["ms"] < 5 * chunk_ms
+        watts = r["joules"] / (r["ms"] * 1e-3)
+        assert 20 < watts < 2000, watts
+    bad = sy.stencil_params(ny, nx, 1, 0.25, "f32")
+    with pytest.raises(sy.SyError) as e:
+        sy.sy_chunk_energy_replay(q, bad, prev, u0, nxt, chunks, 4, 1)
+    assert e.value.name == "SY_ERR_INVALID_ARGUMENT"
+
+
 def test_energy_counter_ticks(q):
     """The device energy counter is monotone and advances while the GPU works."""
     import time
