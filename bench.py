@@ -367,6 +367,7 @@ def measure_batched(q, stream) -> dict:
     points = sum(ny * nx for ny, nx, *_ in fields)
     upd = steps * points
     best = None
+    modes_ms = {}
     for tile_rows in (0, 2, 4, 8):
         plan = sy.sy_stencil_batch_plan(q.handle, [(ny, nx, pitch, r, C2, ua, ub) for ny, nx, pitch, r, ua, ub
                                                    in fields], "f32", tile_rows)
@@ -374,6 +375,7 @@ def measure_batched(q, stream) -> dict:
         sy.sy_stencil_batch_capture(plan, steps)
         sy.sy_stencil_batch_run(plan)
         reps, ms, joules = _metered(q, stream, lambda: sy.sy_stencil_batch_run(plan), min_seconds=0.2)
+        modes_ms[tile_rows] = ms
         if best is None or ms < best[1]:
             best = (tile_rows, ms, joules, reps)
         sy.sy_stencil_batch_destroy(plan)
@@ -449,6 +451,7 @@ def measure_batched(q, stream) -> dict:
                               "plain_8192_dense": plain_radius_energy(q, stream, r, sigma=NX / 16)}
     return {"grids": len(fields), "points": points, "steps": steps, "tile_rows": tile_rows,
             "per_class": per_class,
+            "modes_ms_per_run": {str(k): v for k, v in modes_ms.items()},
             "cross_step_updates_per_s": upd / (ms_p * 1e-3), "cross_step_ms_per_run": ms_p,
             "cross_step_j_per_update": None if not joules_p else joules_p / (reps_p * upd),
             "batched_updates_per_s": upd / (ms * 1e-3), "batched_gb_per_s": 12 * upd / (ms * 1e-3) / 1e9,
@@ -621,7 +624,33 @@ def measure_wave3d(q, stream, dtype: str = "f32", radius: int = 1) -> dict:
             "j_per_update": None if not joules else joules / (reps * upd)}
 
 
-def measure_learned(q, stream) -> dict:
+def batched_pick(models, modes_ms: dict, steps: int = 100) -> dict:
+    """The cost model's choice of the batched plan's tile heights (config 2): per-class heights
+    (mode 0: 4 rows for FP32 radius 1/2/4) or one height for every grid (2, 4, 8), by the least
+    predicted total time of the 64 grids' steps; with the measured rate of that mode and of the
+    default (mode 0), taken from the batched form's timing of every mode."""
+    import numpy as np
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import costmodel, inputs
+
+    grids = inputs.batch_grids()
+    points = sum(ny * nx for ny, nx, _ in grids)
+    pred = {}
+    for mode in (0, 2, 4, 8):
+        feats = []
+        for ny, nx, r in grids:
+            rows = mode or (8 if r == 3 else 4)
+            feats.append(sy.sy_cost_features(1, sy.SY_F32, r, ny, nx, rows, 128, 128, 1))
+        pred[mode] = float(np.sum(np.exp(costmodel.predict(models, np.stack(feats))[:, 0])))
+    pick = min(pred, key=pred.get)
+    rate = lambda m: steps * points / (modes_ms[m] * 1e-3)  # noqa: E731
+    return {"modes": [0, 2, 4, 8], "predicted_total_ms": {str(k): v for k, v in pred.items()},
+            "pick_tile_rows": pick, "pick_updates_per_s": rate(pick), "default_tile_rows": 0,
+            "default_updates_per_s": rate(0), "best_measured_tile_rows": min(modes_ms, key=modes_ms.get)}
+
+
+def measure_learned(q, stream, batched_modes_ms: dict | None = None) -> dict:
     """The learned cost model, end to end on this GPU: the library tunes a reduced
     corpus exhaustively (220 shapes), trains its MLP on 80% of the shapes with its own
     kernels, and reports regret on the held-out 20% for the model and for the default
@@ -641,16 +670,21 @@ def measure_learned(q, stream) -> dict:
     t_measure = time.perf_counter() - t0
     train_ids, test_ids = costmodel.split_shapes(len(shapes))
     t1 = time.perf_counter()
-    model = costmodel.train(q, corpus, train_ids, epochs=250)
+    models = costmodel.train_ensemble(q, corpus, train_ids, n=3, epochs=250)
     t_train = time.perf_counter() - t1
-    res = costmodel.evaluate(q, model, shapes, corpus, test_ids)
-    # choice for the headline workload among the tile variants (chunking fixed at 4)
+    res = costmodel.evaluate(q, models, shapes, corpus, test_ids)
+    single = costmodel.evaluate(q, models[0], shapes, corpus, test_ids)["model"]
+    # choice for the headline workload among the tile variants (chunking fixed at 4): the argmin of
+    # the ensemble's mean predicted log time
     nv = sy.sy_stencil_variant_count(1, sy.SY_F32)
     infos = [sy.sy_stencil_variant_info(1, sy.SY_F32, v) for v in range(1, nv + 1)]
     feats = np.stack([sy.sy_cost_features(1, sy.SY_F32, 1, NY, NX, r, c, t, CHUNKS) for r, c, t in infos])
-    pick = 1 + sy.sy_cost_model_choose(model, feats, 0)
-    ranked = [1 + int(i) for i in np.argsort(sy.sy_cost_model_predict(model, feats)[:, 0])]
-    sy.sy_mlp_destroy(model)
+    pred = costmodel.predict(models, feats)[:, 0]
+    pick = 1 + int(np.argmin(pred))
+    ranked = [1 + int(i) for i in np.argsort(pred)]
+    batched = batched_pick(models, batched_modes_ms) if batched_modes_ms else None
+    for m in models:
+        sy.sy_mlp_destroy(m)
     u0 = torch.from_numpy(inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), "f32")).cuda()
     A, B = torch.empty_like(u0), torch.empty_like(u0)
     chunks = sy.sy_split_rows(NY, CHUNKS)
@@ -670,21 +704,27 @@ def measure_learned(q, stream) -> dict:
     top3 = ranked[:3]
     verified = min(top3, key=one_sim_ms)
     timing = {}
-    for name, variant in (("default", 0), ("learned", pick), ("learned_top3_verified", verified)):
-        p = sy.stencil_params(NY, NX, 1, C2, "f32", variant=variant)
-        run = lambda: sy.sy_wave_run(q.handle, p, u0, A, B, STEPS, chunks, HALO)
-        run()
-        reps, ms, joules = _metered(q, stream, run)
-        upd = STEPS * NY * NX
-        timing[name] = {"variant": variant, "updates_per_s": upd / (ms * 1e-3),
-                        "j_per_update": None if not joules else joules / (reps * upd)}
+    default_v = sy.sy_stencil_default_variant(1, sy.SY_F32)
+    measured = {}
+    for name, variant in (("default", default_v), ("learned", pick), ("learned_top3_verified", verified)):
+        if variant not in measured:  # a pick that is the default configuration is the same measurement
+            p = sy.stencil_params(NY, NX, 1, C2, "f32", variant=variant)
+            run = lambda: sy.sy_wave_run(q.handle, p, u0, A, B, STEPS, chunks, HALO)  # noqa: E731
+            run()
+            reps, ms, joules = _metered(q, stream, run)
+            upd = STEPS * NY * NX
+            measured[variant] = {"updates_per_s": upd / (ms * 1e-3),
+                                 "j_per_update": None if not joules else joules / (reps * upd)}
+        timing[name] = dict(measured[variant], variant=variant, same_as_default=variant == default_v)
     timing["learned_top3_verified"]["candidates"] = top3
     rows, cols, thr = infos[pick - 1]
     return {"corpus_rows": int(corpus["X"].shape[0]), "corpus_shapes": len(shapes), "measure_s": t_measure,
-            "train_s": t_train, "held_out_shapes": int(test_ids.size), "regret_model": res["model"],
+            "train_s": t_train, "ensemble": 3, "held_out_shapes": int(test_ids.size), "regret_model": res["model"],
+            "regret_single_model": single,
             "regret_default": res["default"], "regret_random_expected": res["random_expected_mean"],
             "held_out_totals": res["held_out_totals"],
-            "headline_pick": {"variant": pick, "tile_rows": rows, "threads": thr}, "headline": timing}
+            "headline_pick": {"variant": pick, "tile_rows": rows, "threads": thr}, "headline": timing,
+            "batched": batched}
 
 
 # ---------------------------------------------------------------------------
@@ -906,13 +946,16 @@ def run_gpu(args) -> None:
         forms["wave3d_f32_r1"] = measure_wave3d(q, stream, "f32", 1)
         forms["wave3d_bf16_r1"] = measure_wave3d(q, stream, "bf16", 1)
         forms["wave3d_f32_r2"] = measure_wave3d(q, stream, "f32", 2)
+        forms["wave3d_f32_r4"] = measure_wave3d(q, stream, "f32", 4)
+        forms["wave3d_bf16_r4"] = measure_wave3d(q, stream, "bf16", 4)
         forms["batched"] = measure_batched(q, stream)
         forms["temporal_T2"] = measure_temporal(q, stream, 2)
         forms["temporal_T4"] = measure_temporal(q, stream, 4)
         forms["temporal_T4_bf16"] = measure_temporal(q, stream, 4, "bf16")
         forms["temporal_T2_r4"] = measure_temporal(q, stream, 2, "f32", 4)
         forms["temporal_T4_r4"] = measure_temporal(q, stream, 4, "f32", 4)
-        forms["learned"] = measure_learned(q, stream)
+        forms["learned"] = measure_learned(q, stream, {int(k): v for k, v in
+                                                      forms["batched"]["modes_ms_per_run"].items()})
     if dist:
         dist.barrier()
     if rank == 0:

@@ -310,10 +310,18 @@ def regret(shapes, corpus, pick) -> dict:
             "mean_saxpy": float(np.mean(by_kind[0])) if by_kind[0] else None}
 
 
-def evaluate(q: Queue, model: int, shapes, corpus, test_ids) -> dict:
+def predict(models, X: np.ndarray) -> np.ndarray:
+    """Predicted (log time, log energy) of candidates X: one model's, or the mean over an
+    ensemble of models trained from different seeds (their ranking is steadier than any one's)."""
+    if isinstance(models, (list, tuple)):
+        return np.mean([sy_cost_model_predict(m, X) for m in models], axis=0)
+    return sy_cost_model_predict(models, X)
+
+
+def evaluate(q: Queue, model, shapes, corpus, test_ids) -> dict:
     mask = np.isin(corpus["shape"], test_ids)
     sub = {k: v[mask] for k, v in corpus.items()}
-    pred = sy_cost_model_predict(model, sub["X"])
+    pred = predict(model, sub["X"])
 
     def model_pick(sid, rows):
         return int(np.argmin(pred[rows, 0]))
@@ -358,6 +366,11 @@ def evaluate(q: Queue, model: int, shapes, corpus, test_ids) -> dict:
     # log-time prediction error on held-out rows
     res["held_out_rmse_log_time"] = float(np.sqrt(np.mean((pred[:, 0] - sub["logt"]) ** 2)))
     return res
+
+
+def train_ensemble(q: Queue, corpus, train_ids, n: int = 3, epochs: int = 300, log_energy=None) -> list:
+    """n models on the same rows from seeds 7, 8, ... (initial weights and minibatch order)."""
+    return [train(q, corpus, train_ids, epochs=epochs, seed=7 + i, log_energy=log_energy) for i in range(n)]
 
 
 def train(q: Queue, corpus, train_ids, epochs: int = 300, batch: int = 256, lr: float = 2e-3, seed: int = 7,
@@ -411,6 +424,7 @@ def main() -> None:
     ap.add_argument("--saxpy", type=int, default=40)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--ensemble", type=int, default=3, help="models averaged (different seeds)")
     ap.add_argument("--out", default=None, help="save the corpus (npz) here")
     ap.add_argument("--model", default=None, help="save the trained model here")
     args = ap.parse_args()
@@ -435,9 +449,11 @@ def main() -> None:
         loge = energy_labels_measured(shapes, corpus, power, pmodel)
     train_ids, test_ids = split_shapes(len(shapes))
     t1 = time.time()
-    model = train(q, corpus, train_ids, epochs=args.epochs, log_energy=loge)
+    models = train_ensemble(q, corpus, train_ids, n=args.ensemble, epochs=args.epochs, log_energy=loge)
     t_train = time.time() - t1
-    res = evaluate(q, model, shapes, corpus, test_ids)
+    res = evaluate(q, models, shapes, corpus, test_ids)
+    res["single_model"] = {k: evaluate(q, models[0], shapes, corpus, test_ids)[k] for k in ("model",)}
+    model = models[0]
     res.update({"rows": int(corpus["X"].shape[0]), "shapes": len(shapes), "train_shapes": int(train_ids.size),
                 "test_shapes": int(test_ids.size), "measure_s": t_measure, "train_s": t_train,
                 "group_power_w": {f"{k[0]}/{k[1]}/r{k[2]}": v for k, v in power.items()}})
@@ -447,7 +463,8 @@ def main() -> None:
         np.savez(args.out, loge=loge, **corpus)
     if args.model:
         sy_mlp_save(model, args.model)
-    sy_mlp_destroy(model)
+    for m in models:
+        sy_mlp_destroy(m)
     print(json.dumps(res), flush=True)
 
 

@@ -256,21 +256,27 @@ __device__ __forceinline__ void column(const Args3& a, int64_t tx, int64_t ty, i
 // Register cap per tile height (blocks of 256 threads that must fit an SM): the
 // kernel is latency-bound when few warps are resident, and its loads of a plane are
 // consumed in the same step, so resident warps are what keeps HBM busy.  Radius 1
-// gets 64 / 85 / 128 registers for 1 / 2 / 4 rows, radius 2 one step less; radius
-// 3-4 are left uncapped.  The 1-row FP32 forms and the 1-row 16-bit radius-1 form
+// gets 64 / 85 / 128 registers for 1 / 2 / 4 rows, radius 2 one step less, 16-bit
+// radius 3-4 128 for one row (the rest uncapped).  The 1-row FP32 forms and the 1-row 16-bit radius-1 form
 // fit without spilling; the FP32 radius-1 forms of 2 and 4 rows and several 16-bit
 // forms spill up to about 150 bytes a thread.  Measured at 512^3, resident warps
 // still win: raising the 16-bit radius-2 one-row cap to 128 registers (no spill,
 // 16 warps an SM instead of 24) ran 5 % slower, and loading the next plane's HBM
 // rows one plane ahead (two planes in flight per warp for 2 x rows more vectors a
-// lane) ran 6-30 % slower for every storage type and radius 1-4.
-template <int R, int RY>
+// lane) ran 6-30 % slower for every storage type and radius 1-4.  16-bit radius 3-4
+// one-row columns are held to 2 blocks of 256 (128 registers; uncapped 180 / 210, one
+// block of 256 an SM): BF16 radius 4 2.5e11 -> 2.7e11 updates/s.  The same cap on FP32
+// radius 4 (168 -> 128 registers, a 28-byte spill) ran 8 % slower, so FP32 radius 3-4
+// stay uncapped.
+template <int R, int RY, int ES>
 struct MinBlocks3 {
-    static constexpr int value = R == 1 ? (RY == 1 ? 4 : RY == 2 ? 3 : 2) : R == 2 ? (RY == 1 ? 3 : RY == 2 ? 2 : 1) : 1;
+    static constexpr int value = R == 1   ? (RY == 1 ? 4 : RY == 2 ? 3 : 2)
+                                 : R == 2 ? (RY == 1 ? 3 : RY == 2 ? 2 : 1)
+                                          : (RY == 1 && ES == 2 ? 2 : 1);
 };
 
 template <typename S, int R, int RY, bool START>
-__global__ void __launch_bounds__(256, MinBlocks3<R, RY>::value) wave3d_vec_kernel(Args3 a) {
+__global__ void __launch_bounds__(256, MinBlocks3<R, RY, sizeof(S)>::value) wave3d_vec_kernel(Args3 a) {
     if (a.pdl == 1) griddep_wait();
     if (a.pdl) griddep_launch_dependents();
     stamp_begin(a.stamp);

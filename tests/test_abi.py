@@ -124,3 +124,30 @@ def test_binding_refuses_strided_views():
     for view in (base.t(), base[:, :5], base[::2]):
         with pytest.raises(ValueError):
             sy._ptr(view)
+
+
+def test_stencil_variant_table_and_default():
+    """Host-side variant table: 12 tile forms for FP32 storage, 14 for 16-bit (the narrow forms);
+    variant 0 stands for a listed variant with the same description; tile widths are 32 vectors
+    (register tiles) or 30 (halo-lane and narrow tiles); out-of-range ids are refused."""
+    for dtype, count in ((sy.SY_F32, 12), (sy.SY_BF16, 14), (sy.SY_F16, 14)):
+        es = 4 if dtype == sy.SY_F32 else 2
+        V = 16 // es
+        for r in (1, 2, 3, 4):
+            assert sy.sy_stencil_variant_count(r, dtype) == count
+            d = sy.sy_stencil_default_variant(r, dtype)
+            assert 1 <= d <= count
+            assert sy.sy_stencil_variant_info(r, dtype, 0) == sy.sy_stencil_variant_info(r, dtype, d)
+            for v in range(1, count + 1):
+                rows, cols, thr = sy.sy_stencil_variant_info(r, dtype, v)
+                assert rows in (2, 4, 8, 16) and thr in (128, 256)
+                if v <= 8:
+                    assert cols == 32 * V
+                elif v <= 12:
+                    assert cols == 30 * V and rows in (4, 8)
+                else:
+                    assert cols == 30 * 4 and thr == 128
+            with pytest.raises(sy.SyError):
+                sy.sy_stencil_variant_info(r, dtype, count + 1)
+    with pytest.raises(sy.SyError):
+        sy.sy_stencil_default_variant(5, sy.SY_F32)

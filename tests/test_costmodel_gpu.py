@@ -58,11 +58,14 @@ def test_learned_model_beats_the_default_on_held_out_shapes(queue):
     shapes = inputs.cost_corpus_shapes(n_stencil=200, n_saxpy=20, side_hi=8192, n_hi=1 << 26)
     corpus = costmodel.measure(queue, shapes, reps=3)
     train_ids, test_ids = costmodel.split_shapes(len(shapes))
-    model = costmodel.train(queue, corpus, train_ids, epochs=250)
+    models = costmodel.train_ensemble(queue, corpus, train_ids, n=3, epochs=250)
     try:
-        res = costmodel.evaluate(queue, model, shapes, corpus, test_ids)
+        res = costmodel.evaluate(queue, models, shapes, corpus, test_ids)
+        one = costmodel.evaluate(queue, models[0], shapes, corpus, test_ids)
     finally:
-        sy.sy_mlp_destroy(model)
+        for m in models:
+            sy.sy_mlp_destroy(m)
+    assert one["model"]["mean"] <= 0.10, one  # each model alone is already a good chooser
     # the model's pick is close to the exhaustive optimum and better than the fixed default
     assert res["model"]["mean"] <= 0.10, res
     assert res["model"]["mean"] < res["default"]["mean"], res

@@ -126,3 +126,31 @@ def test_host_run_rejects_bad_arguments(q):
         assert e.value.name == name
     with pytest.raises(ValueError):
         sy.sy_wave_run_host(q, p, u[:, ::2], out, 3, chunks, 1)
+
+
+def test_host_run_zero_steps_growing_grids_and_events(q):
+    """steps = 0 returns u^0 and u^-1 (the Taylor start); a larger grid after a smaller one
+    reallocates the work sets (waiting for the calls still using them); per-chunk events of a
+    host run time every chunk launch."""
+    torch_cuda()
+    results = []
+    for (ny, nx), steps in (((20, 64), 0), ((90, 520), 4), ((30, 128), 3)):
+        u = field(ny, nx, "f32", seed=ny)
+        out, prv = np.zeros_like(u), np.zeros_like(u)
+        p = sy.stencil_params(ny, nx, 1, 0.25, "f32")
+        chunks = sy.sy_split_rows(ny, 3)
+        ev = sy.sy_wave_run_host(q, p, u, out, steps, chunks, 1, host_prev_out=prv, want_events=True)
+        results.append((u, out, prv, steps, ev))
+    sy.sy_queue_sync(q)
+    for u, out, prv, steps, ev in results:
+        if steps == 0:
+            assert np.array_equal(bits(out), bits(u))
+            want_prev = oracle.wave_start_mirror(oracle.F32, u, 1, 0.25)
+        else:
+            want_prev, want = oracle.wave_run_mirror(oracle.F32, u, steps, 1, 0.25)
+            assert np.array_equal(bits(out), bits(want))
+        assert np.array_equal(bits(prv), bits(want_prev))
+        assert len(ev) == (steps + 1) * 3
+    # the last call's events are still valid: every chunk launch timed
+    ms = sy.sy_events_elapsed(q, results[-1][4])
+    assert all(m > 0 for m in ms)
