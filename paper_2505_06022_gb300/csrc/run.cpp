@@ -233,11 +233,26 @@ namespace {
 sy_status host_run_prepare(Queue* q, size_t field) {
     HostRun& h = q->host;
     if (!h.h2d) {
-        SY_CUDA(cudaStreamCreateWithFlags(&h.h2d, cudaStreamNonBlocking));
-        SY_CUDA(cudaStreamCreateWithFlags(&h.d2h, cudaStreamNonBlocking));
-        for (int s = 0; s < 2; ++s)
-            for (cudaEvent_t* e : {&h.in_done[s], &h.sim_done[s], &h.out_done[s]})
-                SY_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        // all or nothing: a partial failure leaves no half-made stream or event behind
+        cudaStream_t s2[2] = {nullptr, nullptr};
+        cudaEvent_t ev[6] = {};
+        cudaError_t e = cudaStreamCreateWithFlags(&s2[0], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s2[1], cudaStreamNonBlocking);
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            for (cudaStream_t x : s2)
+                if (x) cudaStreamDestroy(x);
+            return cuda_fail(e, "sy_wave_run_host: copy streams and events");
+        }
+        h.h2d = s2[0];
+        h.d2h = s2[1];
+        for (int s = 0; s < 2; ++s) {
+            h.in_done[s] = ev[3 * s];
+            h.sim_done[s] = ev[3 * s + 1];
+            h.out_done[s] = ev[3 * s + 2];
+        }
     }
     if (h.field < field) {
         // the old sets may still be read or written: wait for every stream that uses them
