@@ -364,6 +364,29 @@ def test_full_size_sampled_through_wave_run(q, dtype):
         assert bits(gc)[pt] == bits(m)[pt[0] - y0, pt[1] - x0], pt
 
 
+@pytest.mark.parametrize("dtype,variant", [("bf16", 0), ("bf16", 10), ("f16", 14), ("f32", 9)])
+def test_full_size_radius4_forms_sampled(q, dtype, variant):
+    """8192^2, radius 4, 40 steps in 4 chunks through sy_wave_run, with the 16-bit default
+    (the 8-row tile held to 168 registers), a halo-lane tile, a narrow tile and the FP32
+    halo-lane tile: sampled points (corners, chunk and tile boundaries, the centre) equal the
+    precision mirror on the box of their light cone, bit for bit."""
+    torch = torch_cuda()
+    ny = nx = 8192
+    steps, r = 40, 4
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 64.0) + 0.01 * inputs.random_field(9, ny, nx), dtype)
+    d0 = to_device(u0)
+    ua, ub = torch.empty_like(d0), torch.empty_like(d0)
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype, variant=variant)
+    _, cv, _ = sy.sy_wave_run(q, p, d0, ua, ub, steps, sy.sy_split_rows(ny, 4), r)
+    torch.cuda.synchronize()
+    st = np.float32 if dtype == "f32" else np.uint16
+    gc = to_host({d0.data_ptr(): d0, ua.data_ptr(): ua, ub.data_ptr(): ub}[cv], None, st)
+    for pt in FULL_SAMPLES[:12] + [(4096, 239), (4096, 240), (4096, 119), (4096, 120), (2043, 4000)]:
+        y0, y1, x0, x1 = light_cone_box(pt, (ny, nx), steps, r)
+        _, m = oracle.wave_run_mirror(DT[dtype], np.ascontiguousarray(u0[y0:y1, x0:x1]), steps, r, 0.25)
+        assert bits(gc)[pt] == bits(m)[pt[0] - y0, pt[1] - x0], pt
+
+
 @pytest.mark.parametrize("mx,my", [(1, 1), (16, 32), (1000, 3000)])
 def test_config1_mode_closed_form_full_size(q, mx, my):
     # single sin(kx x) sin(ky y) mode on the full grid: u^n = cos(n Omega) u^0 everywhere; the
