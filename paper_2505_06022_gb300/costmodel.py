@@ -338,6 +338,18 @@ def evaluate(q: Queue, model, shapes, corpus, test_ids) -> dict:
         return None
 
     res = {"model": regret(shapes, sub, model_pick), "default": regret(shapes, sub, default_pick)}
+    # the held-out shapes the model chooses worst for: the shape, its pick and the best candidate
+    # (tile rows, tile cols, threads, chunks) with their measured times
+    worst = []
+    for sid in np.unique(sub["shape"]):
+        rows = np.nonzero(sub["shape"] == sid)[0]
+        t = np.exp(sub["logt"][rows])
+        k, b = model_pick(sid, rows), int(np.argmin(t))
+        worst.append((float(t[k] / t[b] - 1.0), int(sid), [int(x) for x in sub["cand"][rows[k]]], float(t[k]),
+                      [int(x) for x in sub["cand"][rows[b]]], float(t[b])))
+    worst.sort(reverse=True)
+    res["worst_picks"] = [{"regret": w[0], "shape": {k: v for k, v in shapes[w[1]].items()}, "pick": w[2],
+                           "pick_ms": w[3], "best": w[4], "best_ms": w[5]} for w in worst[:6]]
     # the same picks as whole-corpus throughput: work of every held-out shape (grid points of one
     # step, or SAXPY elements) over the summed measured time of the chosen configurations
     totals = {}
