@@ -591,6 +591,58 @@ def measure_temporal(q, stream, T: int, dtype: str = "f32", radius: int = 1) -> 
     return out
 
 
+def measure_split(q, stream) -> dict:
+    """Split-buffer mode on the headline simulation (8192^2 FP32, 200 steps, 4 chunks, halo 1):
+    every chunk in a buffer of its own with its halo rows, the rows the range mappers say each
+    chunk needs moved by device-to-device copies before every step (sy_stencil_step_split), the
+    whole simulation captured in a CUDA graph; against the shared-buffer run's rate."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06022_gb300 as sy
+    from paper_2505_06022_gb300 import inputs
+
+    chunks = sy.sy_split_rows(NY, CHUNKS)
+    u0 = inputs.to_storage(inputs.gaussian_pulse(NY, NX, SIGMA), "f32")
+    cur0, prev, cur = [], [], []
+    for c, (a, b) in enumerate(chunks):
+        lo, _, rows = sy.sy_split_layout(NY, chunks, HALO, c)
+        t = torch.zeros(rows, NX, dtype=torch.float32, device="cuda")
+        t[lo: lo + (b - a)] = torch.from_numpy(np.ascontiguousarray(u0[a:b])).cuda()
+        cur0.append(t)
+        cur.append(torch.empty_like(t))
+        prev.append(torch.empty_like(t))
+    p = sy.stencil_params(NY, NX, RADIUS, C2, "f32")
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    qs = sy.Queue(q.device, side)
+
+    def sim():
+        for c in range(CHUNKS):
+            cur[c].copy_(cur0[c])
+        sy.sy_stencil_start_split(qs.handle, p, cur, prev, chunks, HALO)
+        a_, b_ = prev, cur
+        for _ in range(STEPS):
+            sy.sy_stencil_step_split(qs.handle, p, a_, b_, a_, chunks, HALO)
+            a_, b_ = b_, a_
+
+    with torch.cuda.stream(side):
+        sim()  # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        sim()
+    g.replay()
+    reps, ms, joules = _metered(q, stream, g.replay)
+    torch.cuda.synchronize()
+    qs.close()
+    upd = STEPS * NY * NX
+    n_tr = len(sy.sy_rm_transfers(NY, chunks, HALO))
+    return {"chunks": CHUNKS, "halo": HALO, "transfers_per_step": n_tr, "updates_per_s": upd / (ms * 1e-3),
+            "ms_per_sim": ms, "j_per_update": None if not joules else joules / (reps * upd),
+            "mode": "chunk-local buffers, halo rows copied device to device before each step, CUDA graph"}
+
+
 def measure_wave3d(q, stream, dtype: str = "f32", radius: int = 1) -> dict:
     """Second workload: the leapfrog step on a 512^3 grid (c2 = 1/8, Gaussian sigma = 16 at the
     centre), 100 steps in 4 chunks of planes with halo r, one sy_wave3d_run replay per
@@ -949,6 +1001,7 @@ def run_gpu(args) -> None:
         forms["wave3d_f32_r4"] = measure_wave3d(q, stream, "f32", 4)
         forms["wave3d_bf16_r4"] = measure_wave3d(q, stream, "bf16", 4)
         forms["batched"] = measure_batched(q, stream)
+        forms["split_buffers"] = measure_split(q, stream)
         forms["temporal_T2"] = measure_temporal(q, stream, 2)
         forms["temporal_T4"] = measure_temporal(q, stream, 4)
         forms["temporal_T4_bf16"] = measure_temporal(q, stream, 4, "bf16")
