@@ -594,7 +594,7 @@ def measure_temporal(q, stream, T: int, dtype: str = "f32", radius: int = 1) -> 
 def measure_split(q, stream) -> dict:
     """Split-buffer mode on the headline simulation (8192^2 FP32, 200 steps, 4 chunks, halo 1):
     every chunk in a buffer of its own with its halo rows, the rows the range mappers say each
-    chunk needs moved by device-to-device copies before every step (sy_stencil_step_split), the
+    chunk needs moved by one halo-exchange kernel before every step (sy_stencil_step_split), the
     whole simulation captured in a CUDA graph; against the shared-buffer run's rate."""
     import numpy as np
     import torch
@@ -640,7 +640,7 @@ def measure_split(q, stream) -> dict:
     n_tr = len(sy.sy_rm_transfers(NY, chunks, HALO))
     return {"chunks": CHUNKS, "halo": HALO, "transfers_per_step": n_tr, "updates_per_s": upd / (ms * 1e-3),
             "ms_per_sim": ms, "j_per_update": None if not joules else joules / (reps * upd),
-            "mode": "chunk-local buffers, halo rows copied device to device before each step, CUDA graph"}
+            "mode": "chunk-local buffers, one halo-exchange kernel before each step, launches overlapped, CUDA graph"}
 
 
 def measure_wave3d(q, stream, dtype: str = "f32", radius: int = 1) -> dict:

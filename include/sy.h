@@ -380,8 +380,10 @@ sy_status sy_split_layout(int64_t ny, const sy_chunk* chunks, int n_chunks, int 
 
 /* One step with every chunk's fields in buffers of its own (the layout above), as
  * chunks on separate devices would hold them: first the inferred halo rows of
- * u_cur are copied between the chunks' buffers (device to device), then each
- * chunk's rows are stepped.  local_prev / local_cur / local_next: arrays of n_chunks
+ * u_cur are copied between the chunks' buffers (one halo-exchange kernel for all
+ * transfers), then each chunk's rows are stepped; consecutive launches overlap
+ * (programmatic dependent launch, SY_PDL=0 turns it off), each waiting for its
+ * predecessor's writes before it reads.  local_prev / local_cur / local_next: arrays of n_chunks
  * device pointers; p describes the global grid.  Aliasing rules per chunk as in
  * sy_stencil_step.  Bit-identical to sy_stencil_step on one shared buffer. */
 sy_status sy_stencil_step_split(sy_queue_t q, const sy_stencil_params* p, void* const* local_prev,

@@ -13,7 +13,9 @@
 // clipped to the domain; the rows of that region it does not write belong to
 // other chunks and are copied from their owners' buffers before the step (each
 // run of rows with one owner is one transfer; a chunk shorter than h makes a
-// region span several owners).
+// region span several owners).  One halo-exchange kernel does all of a step's
+// transfers; it and the chunk kernels overlap their launches (programmatic
+// dependent launch), each waiting for its predecessor before reading.
 #include <vector>
 
 #include "sy_internal.h"
@@ -121,18 +123,20 @@ sy_status split_common(Queue* q, const sy_stencil_params* p, void* const* local_
             return fail(SY_ERR_ALIAS, "chunk %d: u_next partially overlaps u_prev", c);
     }
     SY_TRY(use_device(q));
-    // 1. halo rows of u_cur from their owners (inferred from the range mappers)
+    // 1. halo rows of u_cur from their owners (inferred from the range mappers), all
+    //    of the step's transfers in one kernel
     std::vector<sy_transfer> t;
     SY_TRY(transfers(p->ny, chunks, n_chunks, halo_radius, &t));
+    std::vector<HaloCopy> copies;
+    copies.reserve(t.size());
     for (const sy_transfer& x : t) {
         const int64_t src_row = x.row_begin - chunks[x.src].begin + lay[x.src].halo_lo;
         const int64_t dst_row = x.row_begin - chunks[x.dst].begin + lay[x.dst].halo_lo;
-        const char* src = static_cast<const char*>(local_cur[x.src]) + src_row * pb;
-        char* dst = static_cast<char*>(local_cur[x.dst]) + dst_row * pb;
-        SY_CUDA(cudaMemcpy2DAsync(dst, pb, src, pb, static_cast<size_t>(p->nx) * es,
-                                  static_cast<size_t>(x.row_end - x.row_begin), cudaMemcpyDeviceToDevice,
-                                  q->launch));
+        copies.push_back(HaloCopy{static_cast<const char*>(local_cur[x.src]) + src_row * pb,
+                                  static_cast<char*>(local_cur[x.dst]) + dst_row * pb, x.row_end - x.row_begin});
     }
+    SY_TRY(launch_halo(q, copies.data(), static_cast<int>(copies.size()), static_cast<int64_t>(pb),
+                       p->nx * static_cast<int64_t>(es), true));
     // 2. each chunk steps its own rows of a local grid of halo_lo + len + halo_hi rows
     for (int c = 0; c < n_chunks; ++c) {
         EventRecord* rec = nullptr;
@@ -151,7 +155,9 @@ sy_status split_common(Queue* q, const sy_stencil_params* p, void* const* local_
         w.u_next = local_next[c];
         w.row_begin = lay[c].halo_lo;
         w.row_end = lay[c].halo_lo + (chunks[c].end - chunks[c].begin);
-        w.pdl = 0;  // the halo copies between the launches order them anyway
+        // the first chunk waits for the halo exchange (or, with none, the previous step);
+        // the others start once it has, so both are complete before they read
+        w.pdl = c == 0 ? 1 : 2;
         SY_TRY(launch_wave(q, w));
         SY_TRY(end_event(q, rec));
     }

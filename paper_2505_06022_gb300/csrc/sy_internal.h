@@ -186,6 +186,17 @@ int kernel_occupancy(const void* fn, int threads);
 bool launch_overlap_enabled();
 }  // namespace wave
 
+// Halo exchange of split-buffer execution (halo.cu): copy `rows` rows of
+// width_bytes each, consecutive rows pitch_bytes apart, from src to dst, for every
+// entry, in one launch per 32 entries; pdl = wait for the previous kernel inside the
+// launch and let the next one start early (when programmatic launch is enabled).
+struct HaloCopy {
+    const void* src;
+    void* dst;
+    int64_t rows;
+};
+sy_status launch_halo(Queue* q, const HaloCopy* copies, int n, int64_t pitch_bytes, int64_t width_bytes, bool pdl);
+
 // One chunk of planes of the 3D step (wave3d_*.cu).
 struct WaveLaunch3 {
     int64_t nz, ny, nx, pitch, plane;  // elements

@@ -1,6 +1,8 @@
 """Split-buffer execution on the GPU: every chunk in a buffer of its own, halos
-moved by the transfers the range mappers infer (device-to-device copies).  Must be
-bit-identical to the oracle (and so to the shared-buffer mode)."""
+moved by the transfers the range mappers infer (one halo-exchange kernel per step,
+launches overlapped by programmatic dependent launch).  Must be bit-identical to the
+oracle (and so to the shared-buffer mode), whatever the number of transfers, the
+copy unit the row width allows, and with launch overlap turned off."""
 import numpy as np
 import pytest
 
@@ -37,10 +39,13 @@ def to_local(u, chunks, h, c, pitch, tdt, torch):
     ("f32", 2, 3, 37, 129, [(0, 1), (1, 3), (3, 30), (30, 37)]),     # chunks shorter than the halo
     ("bf16", 4, 4, 50, 520, [(0, 20), (20, 22), (22, 50)]),
     ("f16", 3, 3, 33, 70, [(0, 33)]),
+    ("bf16", 1, 2, 61, 131, None),                                   # odd row width: 2-byte copy unit
+    ("f32", 1, 1, 160, 96, "many"),                                  # 38 transfers: two halo launches
+    ("f16", 2, 3, 48, 200, [(i, i + 2) for i in range(0, 48, 2)]),   # every halo spans two owners
 ])
 def test_split_buffers_bit_exact(q, dtype, r, h, ny, nx, chunks):
     torch = torch_cuda()
-    chunks = chunks or sy.sy_split_rows(ny, 4)
+    chunks = sy.sy_split_rows(ny, 20) if chunks == "many" else (chunks or sy.sy_split_rows(ny, 4))
     u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 6.0) + 0.05 * inputs.random_field(3, ny, nx), dtype)
     tdt = torch.float32 if dtype == "f32" else torch.int16
     pitch = (nx + 7) // 8 * 8
@@ -113,3 +118,51 @@ def test_step_planes_matches_chunked_3d_step(q):
     with pytest.raises(sy.SyError) as e:
         sy.sy_stencil3d_step_planes(q, p, prev, cur, nxt, 3, 15, r)
     assert e.value.name == "SY_ERR_BAD_CHUNKS"
+
+
+_NO_OVERLAP = r"""
+import sys
+import numpy as np
+import torch
+sys.path[:0] = [sys.argv[1], sys.argv[2]]
+import oracle
+import paper_2505_06022_gb300 as sy
+from paper_2505_06022_gb300 import inputs
+ny, nx, r, h = 70, 260, 2, 2
+chunks = sy.sy_split_rows(ny, 5)
+u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 7.0), "f32")
+cur, prev = [], []
+for c, (a, b) in enumerate(chunks):
+    lo, _, rows = sy.sy_split_layout(ny, chunks, h, c)
+    t = torch.zeros(rows, nx, dtype=torch.float32, device="cuda")
+    t[lo: lo + (b - a)] = torch.from_numpy(np.ascontiguousarray(u0[a:b])).cuda()
+    cur.append(t)
+    prev.append(torch.zeros_like(t))
+p = sy.stencil_params(ny, nx, r, 0.25, "f32")
+with sy.Queue(0) as q:
+    sy.sy_stencil_start_split(q.handle, p, cur, prev, chunks, h)
+    for _ in range(6):
+        sy.sy_stencil_step_split(q.handle, p, prev, cur, prev, chunks, h)
+        prev, cur = cur, prev
+    torch.cuda.synchronize()
+got = np.concatenate([cur[c][sy.sy_split_layout(ny, chunks, h, c)[0]:][: b - a].cpu().numpy()
+                      for c, (a, b) in enumerate(chunks)])
+_, want = oracle.wave_run_mirror(oracle.F32, u0, 6, r, 0.25)
+assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+print("ok")
+"""
+
+
+def test_split_without_launch_overlap():
+    """SY_PDL=0: the halo kernel and the chunk kernels run strictly one after another,
+    with the same results (a fresh process: the switch is read once)."""
+    import os
+    import subprocess
+    import sys
+
+    torch_cuda()
+    here = os.path.dirname(os.path.abspath(__file__))
+    env = dict(os.environ, SY_PDL="0")
+    out = subprocess.run([sys.executable, "-c", _NO_OVERLAP, os.path.dirname(here), here], env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stderr[-2000:]
