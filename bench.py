@@ -142,14 +142,25 @@ def kernel_source_sha() -> str:
 
 def kernel_label(dtype: str, variant: int = 0) -> str:
     """The dominant kernel of the timed step: the 2D step's variant for this storage type
-    (the default unless one is asked for; 16-bit radius-1 4-row tiles run the 96-register form)."""
+    (the default unless one is asked for; 16-bit radius-1 4-row tiles run the 96-register form,
+    16-bit radius 3-4 8-row tiles of 128 threads the 168-register form)."""
     import paper_2505_06022_gb300 as sy
 
     code = sy.DTYPE_CODES[dtype]
     v = variant or sy.sy_stencil_default_variant(RADIUS, code)
     rows, _, threads = sy.sy_stencil_variant_info(RADIUS, code, v)
-    name = "wave_hln_kernel" if v >= 13 else "wave_hl_kernel" if v >= 9 else \
-        ("wave_vec_kernel_r96" if dtype != "f32" and RADIUS == 1 and rows == 4 else "wave_vec_kernel")
+    if dtype != "f32" and v == 15:
+        return f"wave_march_kernel<{dtype},{RADIUS}> x {threads} threads, one 2048x8192 chunk per launch"
+    if v >= 13:
+        name = "wave_hln_kernel"
+    elif v >= 9:
+        name = "wave_hl_kernel"
+    elif dtype != "f32" and RADIUS == 1 and rows == 4:
+        name = "wave_vec_kernel_r96"
+    elif dtype != "f32" and RADIUS >= 3 and rows == 8 and threads == 128:
+        name = "wave_vec_kernel_b3"
+    else:
+        name = "wave_vec_kernel"
     return f"{name}<{dtype},{RADIUS},{rows},false> x {threads} threads, one 2048x8192 chunk per launch"
 
 

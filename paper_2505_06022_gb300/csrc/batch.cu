@@ -31,6 +31,7 @@ struct BatchGridDev {
     int64_t tiles_x;
     int32_t radius;
     float c2;
+    float neg0;  // -0.0f (the packed products' addend, a run-time value)
 };
 
 // A group of grids stepped by one persistent launch: every grid of the plan
@@ -97,6 +98,7 @@ __device__ __forceinline__ void batch_tile(const BatchGridDev& G, int parity, in
     a.c2 = START ? 0.5f * G.c2 : G.c2;
     a.stamp = nullptr;
     a.pdl = 0;
+    a.neg0 = G.neg0;
     wave::wave_tile<S, R, RY, START, false, CG>(a, tx, ty, lane);
 }
 
@@ -394,6 +396,7 @@ sy_status sy_stencil_batch_plan(sy_queue_t qh, const sy_batch_grid* grids, int n
             D.tiles_x = (G.nx + 32 * V - 1) / (32 * V);
             D.radius = G.radius;
             D.c2 = G.c2;
+            D.neg0 = -0.0f;
             const int rows = rows_for(tile_rows, G.radius, esize);
             const int64_t tiles_y = (G.ny + rows - 1) / rows;
             if (D.tiles_x >= (int64_t(1) << kTileXBits) || tiles_y >= (int64_t(1) << kTileYBits))

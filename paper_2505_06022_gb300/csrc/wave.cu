@@ -66,6 +66,7 @@ sy_status launch_typed(Queue* q, const WaveLaunch& w, KernelFn vec_fn, KernelFn 
     a.c2 = w.c2;
     a.stamp = q->cur_stamp;
     a.pdl = 0;
+    a.neg0 = -0.0f;
     if (!aligned(w.u_cur, esize) || !aligned(w.u_next, esize) || (!w.start && !aligned(w.u_prev, esize)))
         return fail(SY_ERR_INVALID_ARGUMENT, "field pointers must be aligned to the element size (%zu bytes)", esize);
     const bool vec_ok = aligned(w.u_cur, 16) && aligned(w.u_next, 16) && (w.start || aligned(w.u_prev, 16)) &&
@@ -141,10 +142,14 @@ bool wave_variant_info(int radius, int dtype, int variant, int* tile_rows, int* 
         rows = wave::kHlRows[(variant - 9) % 2];
         thr = wave::kBlockThreads[(variant - 9) / 2];
         cols = 30 * V;
-    } else {  // narrow halo lanes (16-bit): 30 vectors of 4 elements
+    } else if (variant < wave::kMarchVariant) {  // narrow halo lanes (16-bit): 30 vectors of 4 elements
         rows = wave::kHlRows[variant - 13];
         thr = 128;
         cols = 30 * 4;
+    } else {  // march (16-bit): strips of 30 vectors, segments sized per launch (nominal rows)
+        rows = 32;
+        thr = 128;
+        cols = 30 * V;
     }
     if (tile_rows) *tile_rows = rows;
     if (threads) *threads = thr;
@@ -157,7 +162,10 @@ sy_status launch_wave(Queue* q, const WaveLaunch& w) {
     if (!wave_variant_info(w.radius, w.dtype, w.variant, &tile_rows, nullptr, &threads))
         return fail(SY_ERR_INVALID_ARGUMENT, "bad stencil variant %d", w.variant);
     const int v = w.variant == 0 ? wave_default_variant(w.radius, w.dtype) : w.variant;
-    const wave::Form form = v >= 13 ? wave::Form::Narrow : v >= 9 ? wave::Form::Halo : wave::Form::Tile;
+    const wave::Form form = v == wave::kMarchVariant && w.dtype != SY_F32 ? wave::Form::March
+                            : v >= 13                                     ? wave::Form::Narrow
+                            : v >= 9                                      ? wave::Form::Halo
+                                                                          : wave::Form::Tile;
     switch (w.dtype) {
         case SY_F32: return wave::launch_f32(q, w, tile_rows, threads, form);
         case SY_BF16: return wave::launch_bf16(q, w, tile_rows, threads, form);

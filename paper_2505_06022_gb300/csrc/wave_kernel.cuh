@@ -263,6 +263,9 @@ struct Args {
     // With 1 or 2 the block's first thread also waits at exit, so that a launch's
     // completion implies its predecessor's and the chain is transitive.
     int pdl;
+    // -0.0f, set by the host: the addend that turns a packed FMA into a packed
+    // product (see mul2_rn); a run-time value, so the code generator cannot fold it.
+    float neg0;
 };
 
 // One output point from its neighbourhood, in the canonical operation order.
@@ -302,13 +305,26 @@ __device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
     return d;
 }
 
-// The multiplications stay scalar.  Two packed forms were tried and measured to
-// change results at radius 2-4 (whose weights make inexact products; radius 1,
-// whose products are exact, still matched): mul.rn.f32x2 feeding a packed add, and
-// fma.rn.f32x2 with a -0 addend (which rounds the product exactly once): both came
-// out fused with the following addition despite the explicit rounding modes.
+// Scalar products of two points (the form the 3D and temporally blocked kernels use).
 __device__ __forceinline__ float2 mul2_scalar(float w, float2 x) {
     return make_float2(__fmul_rn(w, x.x), __fmul_rn(w, x.y));
+}
+
+// w * x for two points as one packed FMA, fma.rn.f32x2(w, x, neg0) with neg0 = -0.0:
+// each half is the exact product plus -0 rounded once, which is the rounded product
+// for every input (x + -0 = x for x != 0, +0 + -0 = +0, -0 + -0 = -0), so it is
+// bit-identical to __fmul_rn.  The addend is a run-time argument: a packed multiply
+// (mul.rn.f32x2), or an FMA with a literal -0 addend, was measured to change results
+// at radius 2-4 (the product came out fused with the addition that follows it),
+// while an addend whose value is unknown at compile time leaves nothing to fold.
+__device__ __forceinline__ float2 mul2_rn(float w, float2 x, float neg0) {
+    float2 d;
+    asm("{\n\t.reg .b64 pw, px, pz, pd;\n\t"
+        "mov.b64 pw, {%2, %2};\n\tmov.b64 px, {%3, %4};\n\tmov.b64 pz, {%5, %5};\n\t"
+        "fma.rn.f32x2 pd, pw, px, pz;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(w), "f"(x.x), "f"(x.y), "f"(neg0));
+    return d;
 }
 
 // Horizontal pair sums (u_{j-d} + u_{j+d}) of the points j = e, e+1 from a row held as
@@ -327,14 +343,22 @@ __device__ __forceinline__ float2 horz2(const float (&ext)[N], int e, int d) {
 // subtraction as in update(); bit-identical to (2 * u) - up evaluated per point.
 __device__ __forceinline__ float2 inertia2(float2 u, float2 up) { return sub2_rn(add2_rn(u, u), up); }
 
-template <int R, bool START>
+// PMUL: the products as packed FMAs with the run-time -0 addend neg0 (mul2_rn);
+// otherwise scalar (neg0 unused).  Bit-identical either way.
+template <bool PMUL>
+__device__ __forceinline__ float2 mul2(float w, float2 x, float neg0) {
+    if constexpr (PMUL) return mul2_rn(w, x, neg0);
+    else return mul2_scalar(w, x);
+}
+
+template <int R, bool START, bool PMUL = false>
 __device__ __forceinline__ float2 update2(float2 u, float2 up, const float2 (&vert)[R], const float2 (&horz)[R],
-                                          float c2) {
-    float2 acc = mul2_scalar(c0x2<R>(), u);
+                                          float c2, float neg0 = 0.0f) {
+    float2 acc = mul2<PMUL>(c0x2<R>(), u, neg0);
 #pragma unroll
-    for (int d = 1; d <= R; ++d) acc = add2_rn(acc, mul2_scalar(wk<R>(d), add2_rn(vert[d - 1], horz[d - 1])));
-    if (START) return add2_rn(u, mul2_scalar(c2, acc));
-    return add2_rn(inertia2(u, up), mul2_scalar(c2, acc));
+    for (int d = 1; d <= R; ++d) acc = add2_rn(acc, mul2<PMUL>(wk<R>(d), add2_rn(vert[d - 1], horz[d - 1]), neg0));
+    if (START) return add2_rn(u, mul2<PMUL>(c2, acc, neg0));
+    return add2_rn(inertia2(u, up), mul2<PMUL>(c2, acc, neg0));
 }
 
 // Loads of a tile's vectors.  Within one launch u^n is never written, so it is read
@@ -491,7 +515,7 @@ __device__ __forceinline__ void wave_tile_impl(const Args& a, int64_t tx, int64_
                 }
                 const float2 up = START ? make_float2(0.0f, 0.0f)
                                         : make_float2(T::elem(prev[START ? 0 : k], e), T::elem(prev[START ? 0 : k], e + 1));
-                const float2 o = update2<R, START>(make_float2(ext[R + e], ext[R + e + 1]), up, vert, horz, a.c2);
+                const float2 o = update2<R, START, true>(make_float2(ext[R + e], ext[R + e + 1]), up, vert, horz, a.c2, a.neg0);
                 out[e] = o.x;
                 out[e + 1] = o.y;
             }
@@ -635,15 +659,17 @@ __global__ void __launch_bounds__(256) wave_scalar_kernel(Args a) {
 // Row heights of the vector kernel's tiles; variant v (1-based) = (kTileRows[(v-1) % 4],
 // kBlockThreads[(v-1) / 4]) for v <= 8; variants 9-12 are the halo-lane form with
 // (kHlRows[(v-9) % 2], kBlockThreads[(v-9) / 2]); 16-bit storage adds variants 13-14,
-// the narrow halo-lane form with kHlRows[v-13] rows and 128 threads.
+// the narrow halo-lane form with kHlRows[v-13] rows and 128 threads, and variant 15,
+// the march form (wave_march.cuh: TMA-fed row streams, one segment per warp).
 constexpr int kTileRows[4] = {2, 4, 8, 16};
 constexpr int kBlockThreads[2] = {128, 256};
 constexpr int kHlRows[2] = {4, 8};
 constexpr int kVariants32 = 12;  // FP32 storage
-constexpr int kVariants16 = 14;  // 16-bit storage
+constexpr int kVariants16 = 15;  // 16-bit storage
+constexpr int kMarchVariant = 15;
 
 // How a variant covers a chunk.
-enum class Form { Tile, Halo, Narrow };
+enum class Form { Tile, Halo, Narrow, March };
 
 using KernelFn = void (*)(Args);
 

@@ -127,10 +127,11 @@ def test_binding_refuses_strided_views():
 
 
 def test_stencil_variant_table_and_default():
-    """Host-side variant table: 12 tile forms for FP32 storage, 14 for 16-bit (the narrow forms);
-    variant 0 stands for a listed variant with the same description; tile widths are 32 vectors
-    (register tiles) or 30 (halo-lane and narrow tiles); out-of-range ids are refused."""
-    for dtype, count in ((sy.SY_F32, 12), (sy.SY_BF16, 14), (sy.SY_F16, 14)):
+    """Host-side variant table: 12 tile forms for FP32 storage, 15 for 16-bit (the narrow forms
+    and the march form); variant 0 stands for a listed variant with the same description; tile
+    widths are 32 vectors (register tiles) or 30 (halo-lane, narrow and march strips); the march
+    form reports its nominal 32-row segment; out-of-range ids are refused."""
+    for dtype, count in ((sy.SY_F32, 12), (sy.SY_BF16, 15), (sy.SY_F16, 15)):
         es = 4 if dtype == sy.SY_F32 else 2
         V = 16 // es
         for r in (1, 2, 3, 4):
@@ -140,13 +141,15 @@ def test_stencil_variant_table_and_default():
             assert sy.sy_stencil_variant_info(r, dtype, 0) == sy.sy_stencil_variant_info(r, dtype, d)
             for v in range(1, count + 1):
                 rows, cols, thr = sy.sy_stencil_variant_info(r, dtype, v)
-                assert rows in (2, 4, 8, 16) and thr in (128, 256)
+                assert rows in (2, 4, 8, 16, 32) and thr in (128, 256)
                 if v <= 8:
                     assert cols == 32 * V
                 elif v <= 12:
                     assert cols == 30 * V and rows in (4, 8)
-                else:
+                elif v <= 14:
                     assert cols == 30 * 4 and thr == 128
+                else:
+                    assert (rows, cols, thr) == (32, 30 * V, 128)
             with pytest.raises(sy.SyError):
                 sy.sy_stencil_variant_info(r, dtype, count + 1)
     with pytest.raises(sy.SyError):

@@ -162,6 +162,66 @@ def test_halo_lane_and_march_forms_bit_exact(q, dtype, r, shape):
             assert np.array_equal(bits(c), bits(oc)), f"variant {v} chunks {chunks}"
 
 
+MARCH_SHAPES = [(1, 1), (2, 8), (3, 241), (17, 257), (70, 1030), (129, 64), (40, 480), (9, 2000), (300, 300),
+                (600, 1000)]
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", MARCH_SHAPES)
+def test_march_form_bit_exact(q, dtype, r, shape):
+    """Variant 15, the march form (rows streamed into shared memory by TMA, a rolling
+    window of 2r+1 rows a lane): rows padded to a 16-byte pitch so that the form runs;
+    grids narrower than a strip and wider, ragged at nx, shorter than the radius, chunks of
+    one row, and segments shorter than the 2r warm-up rows.  The Taylor start and every
+    step are bit-identical to the precision mirror."""
+    ny, nx = shape
+    pitch = (nx + 7) // 8 * 8
+    u0 = field(ny, nx, dtype, seed=r + 3)
+    steps = 5
+    _, oc = oracle.wave_run_mirror(DT[dtype], u0, steps, r, 0.25)
+    chunkings = [[(0, ny)], sy.sy_split_rows(ny, min(4, ny))]
+    if ny >= 5:
+        chunkings.append([(0, 1), (1, 2), (2, ny - 1), (ny - 1, ny)])
+    for chunks in chunkings:
+        _, c = wave_run(q, u0, steps, r, 0.25, dtype, chunks, variant=15, pitch=pitch)
+        assert np.array_equal(bits(c), bits(oc)), f"chunks {chunks}"
+    # an unaligned pitch takes the tile launcher's scalar kernel, with the same results
+    if nx % 8:
+        _, c = wave_run(q, u0, steps, r, 0.25, dtype, chunkings[-1], variant=15)
+        assert np.array_equal(bits(c), bits(oc))
+
+
+def test_march_bounded_wait_times_out_and_context_survives(q):
+    """A host-injected fault (SY_FAULT=march_timeout: each warp's first row copy is never
+    issued) makes the march kernel's waits run out: the queue reports SY_ERR_TIMEOUT once,
+    and the context then runs the same step correctly."""
+    import os
+
+    torch = torch_cuda()
+    ny, nx, r = 64, 512, 2
+    u0 = field(ny, nx, "bf16", seed=2)
+    p = sy.stencil_params(ny, nx, r, 0.25, "bf16", variant=15)
+    old = os.environ.get("SY_FAULT")
+    os.environ["SY_FAULT"] = "march_timeout"
+    try:
+        cur = to_device(u0)
+        prev = torch.empty_like(cur)
+        sy.sy_stencil_start(q, p, cur, prev, [(0, ny)], r)
+        with pytest.raises(sy.SyError) as e:
+            sy.sy_queue_sync(q)
+        assert e.value.name == "SY_ERR_TIMEOUT"
+    finally:
+        if old is None:
+            del os.environ["SY_FAULT"]
+        else:
+            os.environ["SY_FAULT"] = old
+    sy.sy_queue_sync(q)  # reported once and cleared
+    _, c = wave_run(q, u0, 3, r, 0.25, "bf16", [(0, ny)], variant=15)
+    _, oc = oracle.wave_run_mirror(oracle.BF16, u0, 3, r, 0.25)
+    assert np.array_equal(bits(c), bits(oc))
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("pitch_extra", [4, 8, 3, 1])
 def test_padded_and_unaligned_pitch(q, dtype, pitch_extra):
@@ -364,11 +424,12 @@ def test_full_size_sampled_through_wave_run(q, dtype):
         assert bits(gc)[pt] == bits(m)[pt[0] - y0, pt[1] - x0], pt
 
 
-@pytest.mark.parametrize("dtype,variant", [("bf16", 0), ("bf16", 10), ("f16", 14), ("f32", 9)])
+@pytest.mark.parametrize("dtype,variant", [("bf16", 0), ("bf16", 10), ("f16", 14), ("f32", 9), ("bf16", 15),
+                                           ("f16", 15)])
 def test_full_size_radius4_forms_sampled(q, dtype, variant):
-    """8192^2, radius 4, 40 steps in 4 chunks through sy_wave_run, with the 16-bit default
-    (the 8-row tile held to 168 registers), a halo-lane tile, a narrow tile and the FP32
-    halo-lane tile: sampled points (corners, chunk and tile boundaries, the centre) equal the
+    """8192^2, radius 4, 40 steps in 4 chunks through sy_wave_run, with the 16-bit default,
+    a halo-lane tile, a narrow tile, the FP32 halo-lane tile and the 16-bit march form
+    (segment boundaries every few dozen rows): sampled points (corners, chunk and tile boundaries, the centre) equal the
     precision mirror on the box of their light cone, bit for bit."""
     torch = torch_cuda()
     ny = nx = 8192
