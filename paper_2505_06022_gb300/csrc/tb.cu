@@ -50,6 +50,7 @@ struct TBArgs {
     unsigned long long* stamp;   // timestamp slot or null
     int fault;                   // host-injected fault for tests: 1 = never issue the first copy
     int pdl;                     // as in wave::Args
+    float neg0;                  // -0.0f, set by the host: the packed products' addend (wave::mul2_rn)
 };
 
 template <typename S, int R, int T>
@@ -103,7 +104,7 @@ __device__ __forceinline__ __half to_s<__half>(float v) { return __float2half_rn
 // are set to zero (interior tiles skip the test).
 template <typename S, int R, int T>
 __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_buf0, int x_buf0, bool interior,
-                                        int64_t ny, int64_t nx, float c2) {
+                                        int64_t ny, int64_t nx, float c2, float neg0) {
     using G = Geo<S, R, T>;
     using Tr = wave::Traits<S>;
     constexpr int V = Tr::V;
@@ -144,7 +145,7 @@ __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_b
                 ext[R + V - 1 + d] = g == 31 ? 0.0f : from_right;
             }
             float out[V];
-            if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions (packed FP32 adds)
+            if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions and the products
 #pragma unroll
                 for (int e = 0; e < V; e += 2) {
                     float2 vert[R], horz[R];
@@ -156,9 +157,9 @@ __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_b
                                                     make_float2(Tr::elem(wd, e), Tr::elem(wd, e + 1)));
                         horz[d - 1] = wave::horz2<R>(ext, e, d);
                     }
-                    const float2 o = wave::update2<R, false>(make_float2(ext[R + e], ext[R + e + 1]),
-                                                             make_float2(Tr::elem(pv, e), Tr::elem(pv, e + 1)), vert,
-                                                             horz, c2);
+                    const float2 o = wave::update2<R, false, true>(make_float2(ext[R + e], ext[R + e + 1]),
+                                                                   make_float2(Tr::elem(pv, e), Tr::elem(pv, e + 1)),
+                                                                   vert, horz, c2, neg0);
                     out[e] = o.x;
                     out[e + 1] = o.y;
                 }
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, TbMinBlocks<R>::value) wave_tb_kerne
 
 #pragma unroll 1
         for (int k = 1; k <= T; ++k) {
-            tb_step<S, R, T>(X, Y, k, y_buf0, x_buf0, interior, a.ny, a.nx, a.c2);
+            tb_step<S, R, T>(X, Y, k, y_buf0, x_buf0, interior, a.ny, a.nx, a.c2, a.neg0);
             __syncthreads();
             uint4* tmp = X;  // u^{m+1} is now in Y
             X = Y;
@@ -350,6 +351,7 @@ sy_status launch_tb(Queue* q, const TBLaunch& w) {
     a.stamp = q->cur_stamp;
     a.fault = w.fault;
     a.pdl = w.pdl;
+    a.neg0 = -0.0f;
     if (a.tiles == 0) return SY_OK;
     int occ = 0;
     SY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, G::SMEM));

@@ -50,6 +50,7 @@ sy_status launch3_typed(Queue* q, const WaveLaunch3& w, KernelFn3 vec_fn, Kernel
     a.c2 = w.c2;
     a.stamp = q->cur_stamp;
     a.pdl = 0;
+    a.neg0 = -0.0f;
     if (!aligned(w.u_cur, esize) || !aligned(w.u_next, esize) || (!w.start && !aligned(w.u_prev, esize)))
         return fail(SY_ERR_INVALID_ARGUMENT, "field pointers must be aligned to the element size (%zu bytes)", esize);
     const bool vec_ok = aligned(w.u_cur, 16) && aligned(w.u_next, 16) && (w.start || aligned(w.u_prev, 16)) &&

@@ -59,6 +59,7 @@ struct Args3 {
     float c2;                  // coefficient of L u
     unsigned long long* stamp;
     int pdl;  // as in the 2D kernel: 0 none, 1 wait for the predecessor first, 2 independent chunk
+    float neg0;  // -0.0f, set by the host: the packed products' addend (wave::mul2_rn)
 };
 
 template <int R, bool START>
@@ -72,19 +73,20 @@ __device__ __forceinline__ float update3(float u, float up, const float (&vert)[
     return __fadd_rn(__fsub_rn(__fmul_rn(2.0f, u), up), __fmul_rn(c2, acc));
 }
 
-// update3 for two neighbouring points, additions paired (wave::add2_rn; the
-// multiplications stay scalar, see wave_kernel.cuh): bit-identical to update3.
+// update3 for two neighbouring points, additions paired (wave::add2_rn) and products
+// paired as FMAs with the run-time -0 addend neg0 (wave::mul2_rn): bit-identical to
+// update3.
 template <int R, bool START>
 __device__ __forceinline__ float2 update3_2(float2 u, float2 up, const float2 (&vert)[R], const float2 (&horz)[R],
-                                            const float2 (&depth)[R], float c2) {
+                                            const float2 (&depth)[R], float c2, float neg0) {
     using wave::add2_rn;
-    using wave::mul2_scalar;
-    float2 acc = mul2_scalar(c0x3<R>(), u);
+    using wave::mul2_rn;
+    float2 acc = mul2_rn(c0x3<R>(), u, neg0);
 #pragma unroll
     for (int d = 1; d <= R; ++d)
-        acc = add2_rn(acc, mul2_scalar(wk<R>(d), add2_rn(add2_rn(vert[d - 1], horz[d - 1]), depth[d - 1])));
-    if (START) return add2_rn(u, mul2_scalar(c2, acc));
-    return add2_rn(wave::inertia2(u, up), mul2_scalar(c2, acc));
+        acc = add2_rn(acc, mul2_rn(wk<R>(d), add2_rn(add2_rn(vert[d - 1], horz[d - 1]), depth[d - 1]), neg0));
+    if (START) return add2_rn(u, mul2_rn(c2, acc, neg0));
+    return add2_rn(wave::inertia2(u, up), mul2_rn(c2, acc, neg0));
 }
 
 // One row of a lane's V points: c is the row itself, up[d-1] / dn[d-1] the rows d
@@ -94,7 +96,7 @@ __device__ __forceinline__ float2 update3_2(float2 u, float2 up, const float2 (&
 template <typename S, int R, bool START>
 __device__ __forceinline__ void row_update(const uint4& c, const uint4 (&up)[R], const uint4 (&dn)[R],
                                            const uint4 (&zm)[R], const uint4 (&zp)[R], const uint4& pv,
-                                           const float (&edge)[R], int lane, float c2,
+                                           const float (&edge)[R], int lane, float c2, float neg0,
                                            float (&out)[Traits<S>::V]) {
     using T = Traits<S>;
     constexpr int V = T::V;
@@ -108,7 +110,7 @@ __device__ __forceinline__ void row_update(const uint4& c, const uint4 (&up)[R],
         ext[R - d] = lane == 0 ? edge[d - 1] : from_left;
         ext[R + V - 1 + d] = lane == 31 ? edge[d - 1] : from_right;
     }
-    if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions
+    if constexpr (sizeof(S) == 2) {  // 16-bit storage: pair the additions and the products
 #pragma unroll
         for (int e = 0; e < V; e += 2) {
             float2 vert[R], horz[R], depth[R];
@@ -121,7 +123,7 @@ __device__ __forceinline__ void row_update(const uint4& c, const uint4 (&up)[R],
                                              make_float2(T::elem(zp[d - 1], e), T::elem(zp[d - 1], e + 1)));
             }
             const float2 u2 = START ? make_float2(0.0f, 0.0f) : make_float2(T::elem(pv, e), T::elem(pv, e + 1));
-            const float2 o = update3_2<R, START>(make_float2(ext[R + e], ext[R + e + 1]), u2, vert, horz, depth, c2);
+            const float2 o = update3_2<R, START>(make_float2(ext[R + e], ext[R + e + 1]), u2, vert, horz, depth, c2, neg0);
             out[e] = o.x;
             out[e + 1] = o.y;
         }
@@ -229,7 +231,7 @@ __device__ __forceinline__ void column_impl(const Args3& a, int64_t tx, int64_t 
                 zp[d - 1] = q[R + d][k];
             }
             float out[V];
-            row_update<S, R, START>(q[R][k], up, dn, zm, zp, prev[START ? 0 : k], edge[k], lane, a.c2, out);
+            row_update<S, R, START>(q[R][k], up, dn, zm, zp, prev[START ? 0 : k], edge[k], lane, a.c2, a.neg0, out);
             if (col_in && row_in(y0 + k)) {
                 char* dst = nbase + k * pb;
                 if (!CHECK || nvalid == V) {
@@ -399,7 +401,7 @@ __device__ __forceinline__ void strip_impl(const Args3& a, int64_t tx, int64_t t
                 zp[d - 1] = q[R + d][k];
             }
             float out[V];
-            row_update<S, R, START>(q[R][k], up, dn, zm, zp, prev[START ? 0 : k], edge[k], lane, a.c2, out);
+            row_update<S, R, START>(q[R][k], up, dn, zm, zp, prev[START ? 0 : k], edge[k], lane, a.c2, a.neg0, out);
             if (col_in && row_in(y0 + k)) {
                 char* dst = nbase + k * pb;
                 if (!CHECK || nvalid == V) {

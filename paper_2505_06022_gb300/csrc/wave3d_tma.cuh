@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) wave3d_tma_kernel(const __grid
                 const float no_edge[R] = {};
                 float out[V];
                 row_update<S, R, START>(cz[row * G::ROW_U4 + lane], up, dn, zm, zp, cur_pv[k], no_edge, lane, a.c2,
-                                        out);
+                                        a.neg0, out);
                 if (useful && y0 + k < a.ny) {
                     char* dst = nbase + (y0 + k) * pb + x0 * ES;
                     if (nvalid == V) {
@@ -232,6 +232,7 @@ sy_status launch_tma(Queue* q, const WaveLaunch3& w) {
     a.c2 = w.c2;
     a.stamp = q->cur_stamp;
     a.pdl = 0;
+    a.neg0 = -0.0f;
     const int64_t planes = w.z_end - w.z_begin;
     a.tiles_x = (w.nx + G::BX - 1) / G::BX;
     a.tiles_y = (w.ny + G::RB - 1) / G::RB;

@@ -1,22 +1,24 @@
 // Streaming ("march") form of the wave step for 16-bit storage.
 //
 // A warp owns a strip of 30*V output columns (V = 8 elements a lane) and a segment of
-// rows of the chunk, and walks down the segment one row at a time.  The rows arrive
-// in shared memory by TMA (cp.async.bulk.tensor.2d, completion counted on one
-// mbarrier per ring slot): each step copies one row of u^n, 32*V columns wide (the
-// strip and V columns on each side: lanes 0 and 31 hold the neighbouring columns and
-// store nothing), and one row of u^{n-1}, the strip only.  kDepth slots per warp keep
-// that many rows in flight ahead of the arithmetic.  Points outside the grid arrive
-// as zeros (the copy's out-of-bounds fill): those are the Dirichlet ghosts, so no
-// lane tests a bound before it reads.
+// rows of the chunk, and walks down the segment two rows a step.  The rows arrive in
+// shared memory by TMA (cp.async.bulk.tensor.2d, completion counted on one mbarrier
+// per ring slot): a step copies two rows of u^n, 32*V columns wide (the strip and V
+// columns on each side: lanes 0 and 31 hold the neighbouring columns and store
+// nothing), and the two rows of u^{n-1} it writes, the strip only.  kDepth slots per
+// warp keep that many steps in flight ahead of the arithmetic.  Points outside the
+// grid arrive as zeros (the copy's out-of-bounds fill): those are the Dirichlet
+// ghosts, so no lane tests a bound before it reads.
 //
-// Each lane widens its 8 elements of every u^n row once, into a rolling window of
-// the 2r+1 rows around the output row (FP32, in registers; the loop is unrolled by
-// 2r+1 rows so that every window slot is a compile-time register): the vertical
-// neighbours come from the window, the horizontal ones from the adjacent lanes by
-// shuffles.  Against the register-tile kernel this reads the r halo rows above and
-// below a tile once per segment instead of once per tile, and widens every element
-// once instead of once per use.
+// Each lane widens its 8 elements of every u^n row once, into a rolling window of the
+// 2r+2 rows around the step's two output rows (FP32, in registers; the loop is
+// unrolled over a whole turn of the window so that every window slot is a
+// compile-time register): the vertical neighbours come from the window, the
+// horizontal ones from the adjacent lanes by shuffles.  Against the register-tile
+// kernel this reads the r halo rows above and below a tile once per segment instead
+// of once per tile, and widens every element once instead of once per use.  Measured
+// slower than the tiles all the same (more control instructions per row and a
+// dependency chain along the walk); it is kept as a tuner candidate.
 //
 // Arithmetic: the canonical operation order of the tile kernel (update2 with packed
 // additions and packed products), so results are bit-identical to it.
