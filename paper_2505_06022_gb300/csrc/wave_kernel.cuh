@@ -628,6 +628,13 @@ __global__ void __launch_bounds__(128, 3) wave_vec_kernel_b3(Args a) {
     wave_vec_body<S, R, RY, START, REV>(a);
 }
 
+// The halo-lane form held to 168 registers (3 blocks of 128 threads an SM instead of
+// 2): 16-bit storage, radius 3-4, 8-row tiles.
+template <typename S, int R, int RY, bool START, bool REV>
+__global__ void __launch_bounds__(128, 3) wave_hl_kernel_b3(Args a) {
+    wave_vec_body<S, R, RY, START, REV, true>(a);
+}
+
 // One point per thread; any element-aligned layout.
 template <typename S, int R, bool START>
 __global__ void __launch_bounds__(256) wave_scalar_kernel(Args a) {
@@ -684,8 +691,12 @@ KernelFn pick_vec(int tile_rows, Form form, int threads) {
         if (form == Form::Narrow)
             return tile_rows == 4 ? wave_hln_kernel<S, R, 4, START, REV> : wave_hln_kernel<S, R, 8, START, REV>;
     }
-    if (form == Form::Halo)
+    if (form == Form::Halo) {
+        if constexpr (sizeof(S) == 2 && R >= 3) {
+            if (tile_rows == 8 && threads == 128) return wave_hl_kernel_b3<S, R, 8, START, REV>;
+        }
         return tile_rows == 4 ? wave_hl_kernel<S, R, 4, START, REV> : wave_hl_kernel<S, R, 8, START, REV>;
+    }
     switch (tile_rows) {
         case 2: return wave_vec_kernel<S, R, 2, START, REV>;
         case 4:
