@@ -102,6 +102,80 @@ __device__ __forceinline__ __half to_s<__half>(float v) { return __float2half_rn
 // needed region of step k, [PAD - (T-k)R, PAD + BX + (T-k)R), lies inside
 // [k R, W - k R) where every value is exact (PAD >= T R).  Points outside the grid
 // are set to zero (interior tiles skip the test).
+// The 16-bit rows of tb_step: the same walk, but the window holds the 2R+1 rows
+// widened to FP32 (each element widened once, when its row enters the window,
+// instead of once per use), and the products as well as the additions are paired.
+template <typename S, int R>
+__device__ __forceinline__ void tb_rows16(const uint4* X, uint4* Y, int r0, int r1, int y_buf0, int x_buf0,
+                                          bool interior, int64_t ny, int64_t nx, float c2, float neg0) {
+    using Tr = wave::Traits<S>;
+    constexpr int V = Tr::V;
+    constexpr int NG = 32;
+    constexpr int W = 2 * R + 1;
+    const int g = threadIdx.x & 31;
+    float win[W][V];  // win[i % W] = row r0 - R + i, widened
+#pragma unroll
+    for (int d = 0; d < 2 * R; ++d) {
+        const uint4 v = X[(r0 - R + d) * NG + g];
+#pragma unroll
+        for (int e = 0; e < V; ++e) win[d][e] = Tr::elem(v, e);
+    }
+    const uint4* xrow = X + (r0 + R) * NG + g;  // row r + R of group g
+    const uint4* yrow = Y + r0 * NG + g;
+    uint4* orow = Y + r0 * NG + g;
+    for (int rb = r0; rb < r1; rb += W) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int r = rb + j;
+            if (r >= r1) break;
+            {
+                const uint4 v = xrow[(r - r0) * NG];
+#pragma unroll
+                for (int e = 0; e < V; ++e) win[(j + 2 * R) % W][e] = Tr::elem(v, e);
+            }
+            const uint4 pv = yrow[(r - r0) * NG];
+            const float(&cen)[V] = win[(j + R) % W];
+            float ext[V + 2 * R];  // columns g*V - R .. g*V + V + R - 1
+#pragma unroll
+            for (int e = 0; e < V; ++e) ext[R + e] = cen[e];
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                const float from_left = __shfl_up_sync(wave::kFull, cen[V - d], 1);
+                const float from_right = __shfl_down_sync(wave::kFull, cen[d - 1], 1);
+                ext[R - d] = g == 0 ? 0.0f : from_left;
+                ext[R + V - 1 + d] = g == 31 ? 0.0f : from_right;
+            }
+            float out[V];
+#pragma unroll
+            for (int e = 0; e < V; e += 2) {
+                float2 vert[R], horz[R];
+#pragma unroll
+                for (int d = 1; d <= R; ++d) {
+                    const float(&wu)[V] = win[(j + R - d) % W];
+                    const float(&wd)[V] = win[(j + R + d) % W];
+                    vert[d - 1] = wave::add2_rn(make_float2(wu[e], wu[e + 1]), make_float2(wd[e], wd[e + 1]));
+                    horz[d - 1] = wave::horz2<R>(ext, e, d);
+                }
+                const float2 o = wave::update2<R, false, true>(make_float2(cen[e], cen[e + 1]),
+                                                               make_float2(Tr::elem(pv, e), Tr::elem(pv, e + 1)), vert,
+                                                               horz, c2, neg0);
+                out[e] = o.x;
+                out[e + 1] = o.y;
+            }
+            if (!interior) {  // ghosts outside the grid stay zero
+                const int64_t gy = static_cast<int64_t>(y_buf0) + r;
+                const bool row_in = gy >= 0 && gy < ny;
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const int64_t gx = static_cast<int64_t>(x_buf0) + g * V + e;
+                    if (!row_in || gx < 0 || gx >= nx) out[e] = 0.0f;
+                }
+            }
+            orow[(r - r0) * NG] = Tr::pack(out);
+        }
+    }
+}
+
 template <typename S, int R, int T>
 __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_buf0, int x_buf0, bool interior,
                                         int64_t ny, int64_t nx, float c2, float neg0) {
@@ -116,6 +190,10 @@ __device__ __forceinline__ void tb_step(const uint4* X, uint4* Y, int k, int y_b
     const int r0 = r_lo + rl * per;
     const int r1 = r0 + per < r_hi ? r0 + per : r_hi;
     if (r0 >= r1) return;  // warp-uniform
+    if constexpr (sizeof(S) == 2) {
+        tb_rows16<S, R>(X, Y, r0, r1, y_buf0, x_buf0, interior, ny, nx, c2, neg0);
+        return;
+    }
     // rolling window of the 2R+1 rows around the current one: row r0 - R + i lives in
     // win[i % W]; the loop is unrolled by W rows so that every slot index is a
     // compile-time constant and the window moves without register copies
