@@ -130,21 +130,25 @@ def test_chunk_invariance(q, dtype, r):
     assert np.array_equal(bits(ref), bits(oc))
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
 def test_every_variant_identical(q, dtype, r):
+    """Every variant on a ragged width (700 columns) in rows padded to a 16-byte pitch, so
+    that each runs its vector (or TMA) form, and on unpadded rows (the scalar fallback
+    where a row is not 16-byte aligned)."""
     ny, nx = 75, 700
     u0 = field(ny, nx, dtype)
     _, oc = oracle.wave_run_mirror(DT[dtype], u0, 5, r, 0.25)
     for v in range(0, sy.sy_stencil_variant_count(r, DT[dtype]) + 1):
-        _, c = wave_run(q, u0, 5, r, 0.25, dtype, sy.sy_split_rows(ny, 4), variant=v)
-        assert np.array_equal(bits(c), bits(oc)), f"variant {v}"
+        for pitch in (704, None):
+            _, c = wave_run(q, u0, 5, r, 0.25, dtype, sy.sy_split_rows(ny, 4), variant=v, pitch=pitch)
+            assert np.array_equal(bits(c), bits(oc)), f"variant {v} pitch {pitch}"
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
 @pytest.mark.parametrize("shape", [(1, 1), (3, 241), (17, 257), (70, 1030), (129, 64), (40, 480), (9, 2000)])
-def test_halo_lane_and_march_forms_bit_exact(q, dtype, r, shape):
+def test_halo_lane_and_narrow_forms_bit_exact(q, dtype, r, shape):
     """The halo-lane tiles (variants 9-12: 30 of 32 lanes store) and, for 16-bit storage,
     the narrow halo-lane tiles (variants 13-14: 8-byte vectors): tiles narrower than the
     grid, wider than it, ragged at nx, grids shorter than a tile or than the radius, and
@@ -156,7 +160,7 @@ def test_halo_lane_and_march_forms_bit_exact(q, dtype, r, shape):
     chunkings = [sy.sy_split_rows(ny, min(3, ny))]
     if ny >= 5:
         chunkings.append([(0, 1), (1, 2), (2, ny)])
-    for v in ((9, 12, 13, 14) if dtype != "f32" else (9, 12)):
+    for v in ((9, 10, 11, 12, 13, 14) if dtype != "f32" else (9, 10, 11, 12)):
         for chunks in chunkings:
             _, c = wave_run(q, u0, steps, r, 0.25, dtype, chunks, variant=v)
             assert np.array_equal(bits(c), bits(oc)), f"variant {v} chunks {chunks}"
