@@ -154,7 +154,8 @@ def kernel_label(dtype: str, variant: int = 0) -> str:
     if v >= 13:
         name = "wave_hln_kernel"
     elif v >= 9:
-        name = "wave_hl_kernel"
+        name = "wave_hl_kernel_b3" if dtype != "f32" and RADIUS >= 3 and rows == 8 and threads == 128 \
+            else "wave_hl_kernel"
     elif dtype != "f32" and RADIUS == 1 and rows == 4:
         name = "wave_vec_kernel_r96"
     elif dtype != "f32" and RADIUS >= 3 and rows == 8 and threads == 128:
