@@ -335,7 +335,10 @@ sy_status sy_stencil_multistep(sy_queue_t q, const sy_stencil_params* p, int T, 
  * Variants 1-8: register tiles of 2/4/8/16 rows x 128/256 threads; 9-12:
  * halo-lane tiles of 4/8 rows x 128/256 threads; for 16-bit storage also 13-14:
  * narrow halo-lane tiles (4 elements, 8 bytes, a lane: tile_cols = 120) of 4/8
- * rows x 128 threads, which hold half the registers per tile row. */
+ * rows x 128 threads, which hold half the registers per tile row, and 15: the march
+ * form (each warp walks a strip of tile_cols columns down a segment of rows, rows
+ * copied into shared memory by TMA; tile_rows = 32 is nominal: the segment length
+ * is chosen per launch so that every resident warp takes one segment). */
 sy_status sy_stencil_variant_count(int radius, int dtype, int* count);
 /* The variant (1..count) that variant 0 stands for at this radius and storage. */
 sy_status sy_stencil_default_variant(int radius, int dtype, int* variant);
