@@ -320,7 +320,8 @@ sy_status sy_wave_run_host(sy_queue_t q, const sy_stencil_params* p, const void*
  * bit-identical to T calls of sy_stencil_step.  The outputs must not overlap the
  * inputs or each other (chunks read each other's input rows while writing).
  * The kernel's waits are bounded: if one gives up, the next sy_queue_sync returns
- * SY_ERR_TIMEOUT and the outputs are invalid. */
+ * SY_ERR_TIMEOUT and the outputs are invalid.  Fields of 2^31 rows or columns or
+ * more (the copies' coordinates are 32-bit) are refused with SY_ERR_UNSUPPORTED. */
 sy_status sy_stencil_multistep(sy_queue_t q, const sy_stencil_params* p, int T, const void* u_prev,
                                const void* u_cur, void* out_prev, void* out_cur, const sy_chunk* chunks, int n_chunks,
                                int halo_radius, sy_event* chunk_events);

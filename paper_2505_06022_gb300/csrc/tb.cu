@@ -403,6 +403,9 @@ sy_status make_map(const void* base, int64_t ny, int64_t nx, int64_t pitch_bytes
 template <typename S, int R, int T>
 sy_status launch_tb(Queue* q, const TBLaunch& w) {
     using G = Geo<S, R, T>;
+    // the tile copies' coordinates are 32-bit
+    if (w.ny + BY + 2 * T * R >= (int64_t{1} << 31) || w.nx + G::W >= (int64_t{1} << 31))
+        return fail(SY_ERR_UNSUPPORTED, "temporal blocking supports fields of fewer than 2^31 rows and columns");
     auto kern = wave_tb_kernel<S, R, T>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;

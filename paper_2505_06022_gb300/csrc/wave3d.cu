@@ -263,7 +263,10 @@ sy_status launch_wave3d(Queue* q, const WaveLaunch3& w) {
         const size_t es = dtype_size(w.dtype);
         const bool tma_ok = wave3::aligned(w.u_cur, 16) && wave3::aligned(w.u_next, 16) &&
                             (w.start || wave3::aligned(w.u_prev, 16)) &&
-                            (w.pitch * es) % 16 == 0 && (w.plane * es) % 16 == 0;
+                            (w.pitch * es) % 16 == 0 && (w.plane * es) % 16 == 0 &&
+                            // TMA coordinates are 32-bit
+                            w.nz + 64 < (int64_t{1} << 31) && w.ny + 64 < (int64_t{1} << 31) &&
+                            w.nx + 64 < (int64_t{1} << 31);
         const int64_t planes = w.z_end - w.z_begin;
         if (planes <= 0 || w.ny == 0 || w.nx == 0) return SY_OK;
         if (tma_ok) {
@@ -273,7 +276,7 @@ sy_status launch_wave3d(Queue* q, const WaveLaunch3& w) {
                 case SY_F16: return wave3::launch3_tma_f16(q, w, rows);
             }
         }
-        rows = 1;  // unaligned layouts: the one-point-per-thread kernel of the column family
+        rows = 1;  // unaligned layouts and fields of 2^31 planes, rows or columns: the column family
         threads = 128;
         form = Form3::column;
     }

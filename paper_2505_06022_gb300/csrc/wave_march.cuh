@@ -352,15 +352,18 @@ sy_status launch_march_r(Queue* q, const WaveLaunch& w) {
     return w.reverse ? launch_march_k<S, R, false, true>(q, w) : launch_march_k<S, R, false, false>(q, w);
 }
 
-// Layouts whose rows are not 16-byte aligned go to the tile kernel's launcher (which
-// takes the scalar kernel for them).
+// Layouts whose rows are not 16-byte aligned, and fields of 2^31 rows or columns or
+// more, go to the tile kernel's launcher (which takes the scalar kernel for the
+// unaligned ones).
 template <typename S>
 sy_status launch_march(Queue* q, const WaveLaunch& w) {
     if (w.row_end <= w.row_begin || w.nx == 0) return SY_OK;
     auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     const bool vec_ok = a16(w.u_cur) && a16(w.u_next) && (w.start || a16(w.u_prev)) &&
                         (w.pitch * static_cast<int64_t>(sizeof(S))) % 16 == 0;
-    if (!vec_ok) return launch_dtype<S>(q, w, 4, 128, Form::Tile);
+    // TMA coordinates are 32-bit: taller or wider fields take the tile kernel too
+    const bool coords_ok = w.ny + 64 < (int64_t{1} << 31) && w.nx + 64 < (int64_t{1} << 31);
+    if (!vec_ok || !coords_ok) return launch_dtype<S>(q, w, 4, 128, Form::Tile);
     switch (w.radius) {
         case 1: return launch_march_r<S, 1>(q, w);
         case 2: return launch_march_r<S, 2>(q, w);
