@@ -34,16 +34,18 @@ def to_local(u, chunks, h, c, pitch, tdt, torch):
     return buf
 
 
-@pytest.mark.parametrize("dtype,r,h,ny,nx,chunks", [
-    ("f32", 1, 1, 64, 300, None),
-    ("f32", 2, 3, 37, 129, [(0, 1), (1, 3), (3, 30), (30, 37)]),     # chunks shorter than the halo
-    ("bf16", 4, 4, 50, 520, [(0, 20), (20, 22), (22, 50)]),
-    ("f16", 3, 3, 33, 70, [(0, 33)]),
-    ("bf16", 1, 2, 61, 131, None),                                   # odd row width: 2-byte copy unit
-    ("f32", 1, 1, 160, 96, "many"),                                  # 38 transfers: two halo launches
-    ("f16", 2, 3, 48, 200, [(i, i + 2) for i in range(0, 48, 2)]),   # every halo spans two owners
+@pytest.mark.parametrize("dtype,r,h,ny,nx,chunks,variant", [
+    ("f32", 1, 1, 64, 300, None, 0),
+    ("f32", 2, 3, 37, 129, [(0, 1), (1, 3), (3, 30), (30, 37)], 0),     # chunks shorter than the halo
+    ("bf16", 4, 4, 50, 520, [(0, 20), (20, 22), (22, 50)], 0),
+    ("f16", 3, 3, 33, 70, [(0, 33)], 0),
+    ("bf16", 1, 2, 61, 131, None, 0),                                   # odd row width: 2-byte copy unit
+    ("f32", 1, 1, 160, 96, "many", 0),                                  # 38 transfers: two halo launches
+    ("f16", 2, 3, 48, 200, [(i, i + 2) for i in range(0, 48, 2)], 0),   # every halo spans two owners
+    ("bf16", 4, 4, 50, 520, [(0, 20), (20, 22), (22, 50)], 15),         # the march form in local buffers
+    ("f16", 2, 3, 48, 200, [(i, i + 2) for i in range(0, 48, 2)], 15),
 ])
-def test_split_buffers_bit_exact(q, dtype, r, h, ny, nx, chunks):
+def test_split_buffers_bit_exact(q, dtype, r, h, ny, nx, chunks, variant):
     torch = torch_cuda()
     chunks = sy.sy_split_rows(ny, 20) if chunks == "many" else (chunks or sy.sy_split_rows(ny, 4))
     u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 6.0) + 0.05 * inputs.random_field(3, ny, nx), dtype)
@@ -51,7 +53,7 @@ def test_split_buffers_bit_exact(q, dtype, r, h, ny, nx, chunks):
     pitch = (nx + 7) // 8 * 8
     cur = [to_local(u0, chunks, h, c, pitch, tdt, torch) for c in range(len(chunks))]
     prev = [torch.zeros_like(t) for t in cur]
-    p = sy.stencil_params(ny, nx, r, 0.25, dtype, pitch=pitch)
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype, pitch=pitch, variant=variant)
     sy.sy_stencil_start_split(q, p, cur, prev, chunks, h)
     steps = 8
     for _ in range(steps):

@@ -39,14 +39,15 @@ def as_torch_host(a, pinned):
     return t.pin_memory() if pinned else t
 
 
-@pytest.mark.parametrize("dtype,r", [("f32", 1), ("bf16", 2), ("f16", 4), ("f32", 3)])
+@pytest.mark.parametrize("dtype,r,variant", [("f32", 1, 0), ("bf16", 2, 0), ("f16", 4, 0), ("f32", 3, 0),
+                                             ("bf16", 3, 15)])
 @pytest.mark.parametrize("pinned", [True, False])
-def test_host_run_equals_device_run_and_mirror(q, dtype, r, pinned):
+def test_host_run_equals_device_run_and_mirror(q, dtype, r, pinned, variant):
     torch = torch_cuda()
-    ny, nx, steps = 77, 300, 9
+    ny, nx, steps = 77, 304, 9
     u0 = field(ny, nx, dtype, seed=r)
     chunks = sy.sy_split_rows(ny, 3)
-    p = sy.stencil_params(ny, nx, r, 0.25, dtype)
+    p = sy.stencil_params(ny, nx, r, 0.25, dtype, variant=variant)
     h_in = as_torch_host(u0, pinned)
     h_out, h_prev = torch.empty_like(h_in), torch.empty_like(h_in)
     if pinned:
