@@ -168,3 +168,34 @@ def test_split_without_launch_overlap():
     out = subprocess.run([sys.executable, "-c", _NO_OVERLAP, os.path.dirname(here), here], env=env,
                          capture_output=True, text=True, timeout=600)
     assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stderr[-2000:]
+
+
+def test_split_full_size_sampled(q):
+    """The benchmark's split-buffer form at full size: 8192^2 FP32 with 0.01 noise on the
+    Gaussian, 4 chunks in buffers of their own, halo 1, the Taylor start and 30 steps (one
+    halo-exchange kernel and 4 chunk kernels a step); sampled points (corners, chunk
+    boundaries on both sides, the centre) equal the precision mirror on the box of their
+    light cone, bit for bit."""
+    torch = torch_cuda()
+    ny = nx = 8192
+    steps, r, h = 30, 1, 1
+    chunks = sy.sy_split_rows(ny, 4)
+    u0 = inputs.to_storage(inputs.gaussian_pulse(ny, nx, 64.0) + 0.01 * inputs.random_field(5, ny, nx), "f32")
+    cur = [to_local(u0, chunks, h, c, nx, torch.float32, torch) for c in range(len(chunks))]
+    prev = [torch.zeros_like(t) for t in cur]
+    p = sy.stencil_params(ny, nx, r, 0.25, "f32")
+    sy.sy_stencil_start_split(q, p, cur, prev, chunks, h)
+    for _ in range(steps):
+        sy.sy_stencil_step_split(q, p, prev, cur, prev, chunks, h)
+        prev, cur = cur, prev
+    torch.cuda.synchronize()
+    samples = [(0, 0), (0, 8191), (8191, 0), (8191, 8191), (2047, 4096), (2048, 4096), (2047, 0),
+               (2048, 8191), (4095, 4100), (4096, 4100), (6143, 17), (6144, 17), (4096, 4096), (1000, 7000)]
+    for (i, j) in samples:
+        c = next(k for k, (a, b) in enumerate(chunks) if a <= i < b)
+        lo, _, _ = sy.sy_split_layout(ny, chunks, h, c)
+        got = cur[c][lo + i - chunks[c][0], j].item()
+        y0, y1 = max(0, i - (steps + 1) * r - 1), min(ny, i + (steps + 1) * r + 2)
+        x0, x1 = max(0, j - (steps + 1) * r - 1), min(nx, j + (steps + 1) * r + 2)
+        _, m = oracle.wave_run_mirror(oracle.F32, np.ascontiguousarray(u0[y0:y1, x0:x1]), steps, r, 0.25)
+        assert np.float32(got).view(np.uint32) == m[i - y0, j - x0].view(np.uint32), (i, j)
