@@ -296,13 +296,14 @@ sy_status sy_wave_run(sy_queue_t q, const sy_stencil_params* p, const void* u0, 
  *     sy_queue_sync(q) returns.  With pinned host memory (cudaHostAlloc or
  *     cudaHostRegister) the copies are asynchronous; pageable memory works, but
  *     its copies synchronise with the host.
- *   - Consecutive calls overlap: alternate calls use two device work sets of three
- *     fields each (allocated on the first call and when a larger grid arrives,
- *     freed by sy_queue_destroy), and the copies run on one stream per direction,
- *     so a call's input copy overlaps the previous call's simulation and its
- *     output copy the next call's.  A call whose host_u0 overlaps the previous
- *     call's outputs waits for those copies first, so feeding a result back in is
- *     safe.
+ *   - Consecutive calls overlap: calls rotate through three device work sets of
+ *     three fields each (allocated on the first call and when a larger grid
+ *     arrives, freed by sy_queue_destroy), and the copies run on one stream per
+ *     direction, so a call's input copy overlaps the earlier calls' simulations and
+ *     its output copy the later calls', and an input copy waits only for the
+ *     output copy of the call three back.  A call whose host_u0 overlaps an
+ *     earlier call's outputs waits for those copies first, so feeding a result
+ *     back in is safe.
  *   - host_out and host_prev_out must not overlap each other (SY_ERR_ALIAS);
  *     host_u0 may equal host_out (it is read before the result is written).
  *   - events as in sy_wave_run (valid until the next whole run on this queue);

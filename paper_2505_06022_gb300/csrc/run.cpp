@@ -210,7 +210,7 @@ void host_run_release(Queue* q) {
     HostRun& h = q->host;
     if (h.h2d) cudaStreamSynchronize(h.h2d);
     if (h.d2h) cudaStreamSynchronize(h.d2h);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < kHostSets; ++s) {
         if (h.graph[s].exec) cudaGraphExecDestroy(h.graph[s].exec);
         h.graph[s] = RunGraph();
         for (cudaEvent_t* e : {&h.in_done[s], &h.sim_done[s], &h.out_done[s]})
@@ -235,10 +235,11 @@ sy_status host_run_prepare(Queue* q, size_t field) {
     if (!h.h2d) {
         // all or nothing: a partial failure leaves no half-made stream or event behind
         cudaStream_t s2[2] = {nullptr, nullptr};
-        cudaEvent_t ev[6] = {};
+        cudaEvent_t ev[3 * kHostSets] = {};
         cudaError_t e = cudaStreamCreateWithFlags(&s2[0], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s2[1], cudaStreamNonBlocking);
-        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        for (int i = 0; i < 3 * kHostSets && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             for (cudaEvent_t x : ev)
                 if (x) cudaEventDestroy(x);
@@ -248,7 +249,7 @@ sy_status host_run_prepare(Queue* q, size_t field) {
         }
         h.h2d = s2[0];
         h.d2h = s2[1];
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kHostSets; ++s) {
             h.in_done[s] = ev[3 * s];
             h.sim_done[s] = ev[3 * s + 1];
             h.out_done[s] = ev[3 * s + 2];
@@ -258,7 +259,7 @@ sy_status host_run_prepare(Queue* q, size_t field) {
         // the old sets may still be read or written: wait for every stream that uses them
         SY_CUDA(cudaStreamSynchronize(q->stream));
         SY_TRY(host_run_sync(q));
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kHostSets; ++s) {
             if (h.graph[s].exec) cudaGraphExecDestroy(h.graph[s].exec);
             h.graph[s] = RunGraph();
         }
@@ -266,10 +267,10 @@ sy_status host_run_prepare(Queue* q, size_t field) {
         h.ws = nullptr;
         h.ws_bytes = h.field = 0;
         void* ws = nullptr;
-        cudaError_t e = cudaMalloc(&ws, 6 * field);
+        cudaError_t e = cudaMalloc(&ws, 3 * kHostSets * field);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(host-run work sets)");
         h.ws = ws;
-        h.ws_bytes = 6 * field;
+        h.ws_bytes = 3 * kHostSets * field;
         h.field = field;
     }
     return SY_OK;
@@ -303,19 +304,24 @@ extern "C" sy_status sy_wave_run_host(sy_queue_t qh, const sy_stencil_params* p,
     const size_t field = (bytes + 255) / 256 * 256;
     SY_TRY(host_run_prepare(q, field));
     HostRun& h = q->host;
-    const int s = static_cast<int>(h.calls % 2);
+    const int s = static_cast<int>(h.calls % kHostSets);
     char* set = static_cast<char*>(h.ws) + 3 * static_cast<size_t>(s) * field;
     void* u0 = set;
     void* ua = set + field;
     void* ub = set + 2 * field;
 
-    // host -> device: this set's u0 is free once the call two back has finished
-    // simulating and copying out (with steps = 0 its result is u0 itself); if this
-    // input is the previous call's output, wait for that copy too.
+    // host -> device: this set's u0 is free once the call kHostSets back has finished
+    // simulating and copying out (with steps = 0 its result is u0 itself; the copy-outs
+    // run in call order on one stream, so every older call's copy-out is done too); if
+    // this input is one of the more recent calls' outputs, wait for that copy as well.
     SY_CUDA(cudaStreamWaitEvent(h.h2d, h.out_done[s], 0));
-    const bool reads_last = (h.last_out[0] && ranges_overlap(host_u0, bytes, h.last_out[0], h.last_out_bytes)) ||
-                            (h.last_out[1] && ranges_overlap(host_u0, bytes, h.last_out[1], h.last_out_bytes));
-    if (reads_last) SY_CUDA(cudaStreamWaitEvent(h.h2d, h.out_done[1 - s], 0));
+    for (int t = 0; t < kHostSets; ++t) {
+        if (t == s) continue;
+        bool reads = false;
+        for (const void* o : h.last_out[t])
+            reads = reads || (o && ranges_overlap(host_u0, bytes, o, h.last_out_bytes[t]));
+        if (reads) SY_CUDA(cudaStreamWaitEvent(h.h2d, h.out_done[t], 0));
+    }
     SY_CUDA(cudaMemcpyAsync(u0, host_u0, bytes, cudaMemcpyHostToDevice, h.h2d));
     SY_CUDA(cudaEventRecord(h.in_done[s], h.h2d));
 
@@ -333,9 +339,9 @@ extern "C" sy_status sy_wave_run_host(sy_queue_t qh, const sy_stencil_params* p,
     SY_CUDA(cudaMemcpyAsync(host_out, cv, bytes, cudaMemcpyDeviceToHost, h.d2h));
     if (host_prev_out) SY_CUDA(cudaMemcpyAsync(host_prev_out, pv, bytes, cudaMemcpyDeviceToHost, h.d2h));
     SY_CUDA(cudaEventRecord(h.out_done[s], h.d2h));
-    h.last_out[0] = host_out;
-    h.last_out[1] = host_prev_out;
-    h.last_out_bytes = bytes;
+    h.last_out[s][0] = host_out;
+    h.last_out[s][1] = host_prev_out;
+    h.last_out_bytes[s] = bytes;
     ++h.calls;
     return SY_OK;
 }

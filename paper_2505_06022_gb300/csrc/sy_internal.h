@@ -75,20 +75,24 @@ struct RunGraph {
     const void* cur_out = nullptr;
 };
 
+// Work sets of sy_wave_run_host: call k uses set k mod kHostSets, so a call's input
+// copy waits only for the copy-out of the call kHostSets back.
+constexpr int kHostSets = 3;
+
 struct HostRun {
-    void* ws = nullptr;  // 2 sets x 3 fields of `field` bytes (owned)
+    void* ws = nullptr;  // kHostSets sets x 3 fields of `field` bytes (owned)
     size_t ws_bytes = 0;
     size_t field = 0;
     cudaStream_t h2d = nullptr, d2h = nullptr;  // owned copy streams
     // per set: host->device copy done, simulation done, device->host copies done
-    cudaEvent_t in_done[2] = {nullptr, nullptr};
-    cudaEvent_t sim_done[2] = {nullptr, nullptr};
-    cudaEvent_t out_done[2] = {nullptr, nullptr};
-    RunGraph graph[2];
+    cudaEvent_t in_done[kHostSets] = {};
+    cudaEvent_t sim_done[kHostSets] = {};
+    cudaEvent_t out_done[kHostSets] = {};
+    RunGraph graph[kHostSets];
     uint64_t calls = 0;
-    // host ranges the latest call writes (its u^{steps}, u^{steps-1})
-    const void* last_out[2] = {nullptr, nullptr};
-    size_t last_out_bytes = 0;
+    // per set: the host ranges its latest call writes (u^{steps}, u^{steps-1})
+    const void* last_out[kHostSets][2] = {};
+    size_t last_out_bytes[kHostSets] = {};
 };
 
 struct Queue {

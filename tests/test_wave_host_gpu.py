@@ -68,7 +68,7 @@ def test_host_run_equals_device_run_and_mirror(q, dtype, r, pinned, variant):
 
 
 def test_consecutive_calls_each_give_their_own_result(q):
-    """Four calls in a row (alternating work sets, copies overlapping the neighbouring
+    """Four calls in a row (rotating work sets, copies overlapping the neighbouring
     simulations), a padded pitch, numpy host arrays, one sync at the end."""
     torch_cuda()
     ny, nx, pitch, steps, r = 64, 250, 264, 6, 1
@@ -155,3 +155,26 @@ def test_host_run_zero_steps_growing_grids_and_events(q):
     # the last call's events are still valid: every chunk launch timed
     ms = sy.sy_events_elapsed(q, results[-1][4])
     assert all(m > 0 for m in ms)
+
+
+def test_results_fed_back_two_and_three_calls_later(q):
+    """Interleaved chains: every call's input is the output of the call two back (chains
+    A and B alternate) or three back (chains A, B, C rotate), so the input copy must wait
+    for a copy-out of a call that used another work set."""
+    torch_cuda()
+    ny, nx, steps, r = 48, 256, 4, 1
+    p = sy.stencil_params(ny, nx, r, 0.25, "f32")
+    chunks = sy.sy_split_rows(ny, 2)
+    for n_chains in (2, 3):
+        starts = [field(ny, nx, "f32", seed=20 + c) for c in range(n_chains)]
+        bufs = [as_torch_host(u, pinned=True) for u in starts]
+        rounds = 4
+        for _ in range(rounds):
+            for c in range(n_chains):
+                sy.sy_wave_run_host(q, p, bufs[c], bufs[c], steps, chunks, r)
+        sy.sy_queue_sync(q)
+        for c in range(n_chains):
+            want = starts[c]
+            for _ in range(rounds):
+                _, want = oracle.wave_run_mirror(oracle.F32, want, steps, r, 0.25)
+            assert np.array_equal(bits(bufs[c].numpy()), bits(want)), (n_chains, c)
