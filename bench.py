@@ -77,9 +77,10 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock, power and throttle reasons; stop(window) keeps the
+    samples taken inside the timed region (host wall-clock window), where there are any."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -91,7 +92,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                          "-lms", "50", "-i", str(self.gpu)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -102,7 +103,36 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self) -> dict:
+    @staticmethod
+    def parse(lines, window=None) -> dict:
+        """Summary of nvidia-smi CSV lines (FIELDS order); with window = (t0, t1) in host
+        epoch seconds, only the samples inside it count, unless none falls inside."""
+        import datetime
+
+        rows = []
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                t = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                t = None
+            try:
+                rows.append((t, float(parts[2]), float(parts[3]), float(parts[4]), parts[6:10]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if window and r[0] is not None and window[0] <= r[0] <= window[1]]
+        used = inside or rows
+        if not used:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in used for n, v in zip(names, r[4]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in used), "sm_max_mhz": max(r[2] for r in used),
+                "reasons": reasons, "samples": len(used), "samples_in_timed_region": len(inside),
+                "power_w_median": statistics.median(r[3] for r in used)}
+
+    def stop(self, window=None) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -111,25 +141,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self._t.join(timeout=2)
-        sm, smax, power, reasons = [], [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-                power.append(float(parts[3]))
-            except ValueError:
-                continue
-            for name, val in zip(names, parts[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm), "power_w_median": statistics.median(power)}
+        return self.parse(self.lines, window)
 
 
 def kernel_source_sha() -> str:
@@ -850,12 +862,14 @@ def run_gpu(args) -> None:
         have_energy = False
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
     t_start.record(stream)
     events = []
     for _ in range(args.steps):
         _, _, events = simulate(u0, True)  # per-chunk ids of the latest run
     t_end.record(stream)
     torch.cuda.synchronize()
+    wall1 = time.time()
     joules = seconds = None
     if have_energy:
         try:
@@ -864,7 +878,7 @@ def run_gpu(args) -> None:
             have_energy = False
     if dist:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop((wall0, wall1))
     ms_total = t_start.elapsed_time(t_end)
     launches = q.launches - launches0
     if dist:
