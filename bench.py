@@ -80,7 +80,9 @@ class ClockSampler:
     """nvidia-smi samples of SM clock, power and throttle reasons; stop(window) keeps the
     samples taken inside the timed region (host wall-clock window), where there are any."""
 
-    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    # power.draw.instant: the instantaneous reading (power.draw averages over about a second,
+    # longer than the benchmark's timed region)
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw.instant,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
