@@ -217,12 +217,13 @@ def test_3d_full_size_sampled_light_cone(q):
         assert np.float32(got).view(np.uint32) == want.view(np.uint32), pt
 
 
-@pytest.mark.parametrize("dtype,r,steps", [("bf16", 1, 100), ("f32", 2, 30)])
+@pytest.mark.parametrize("dtype,r,steps", [("bf16", 1, 100), ("f32", 2, 30), ("f32", 4, 12), ("bf16", 4, 12)])
 def test_3d_full_size_other_forms_sampled(q, dtype, r, steps):
     """512^3 in 4 chunks of planes through sy_wave3d_run with the default variant -- the
-    benchmark's BF16 radius-1 and FP32 radius-2 forms (radius 2 over 30 of its 100 steps, so
-    that the light cones stay small; the launches are the same): sampled points equal the
-    oracle's precision mirror on the box of their light cone, bit for bit."""
+    benchmark's BF16 radius-1, FP32 radius-2 and FP32 / BF16 radius-4 forms (radius 2 over 30
+    and radius 4 over 12 of their 100 steps, so that the light cones stay small; the launches
+    are the same): sampled points equal the oracle's precision mirror on the box of their
+    light cone, bit for bit."""
     torch = torch_cuda()
     n = 512
     u0 = inputs.to_storage(inputs.gaussian_pulse_3d(n, n, n, 16.0), dtype)
