@@ -47,8 +47,7 @@ constexpr int kDepth = 4;                // ring slots per warp: kDepth * kRowsP
 constexpr int kRowBytes = 512;           // one u^n row copy (32 x 8 elements); a u^{n-1} row takes 480
 constexpr int kSlot = 2 * kRowsPerStep * kRowBytes;  // u^n rows, then u^{n-1} rows
 constexpr int kPrevOff = kRowsPerStep * kRowBytes;
-constexpr int kNominalRows = 32;         // rows per segment, as reported to the tuner
-constexpr int kMinSegment = 8;
+constexpr int kMinSegment = 8;           // rows; the segment length is otherwise chosen per launch
 
 template <typename S>
 struct Geo {
